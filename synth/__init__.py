@@ -1,0 +1,308 @@
+"""Seeded synthetic LiDAR inputs shared by the oracle tests, the GPU tests and bench.py.
+
+This module only generates inputs: scenes made of walls, poles, boxes and a
+ground plane, spinning-LiDAR scans ray-cast against them, and sensor poses.
+It contains none of the registration method's arithmetic.
+
+Sensors and scenes are shaped like the paper's setups (Table I and Sec. IV-A):
+single 32/64-beam spinning LiDARs (<100k points per scan) and a dense
+128 x 2048 sensor (~260k points per scan, the size of the merged racing
+scans). The datasets themselves are not available; these inputs stand in
+for them.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_libsynth.so")
+_lib = None
+
+PRIM_SEG, PRIM_ARC, PRIM_CYL, PRIM_BOX = 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the ray caster into an in-tree shared library."""
+    src = os.path.join(_HERE, "raycast.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-std=c11", src, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.synth_raycast.restype = ctypes.c_int64
+        lib.synth_raycast.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+            ctypes.c_void_p, ctypes.c_int32]
+        _lib = lib
+    return _lib
+
+
+# --------------------------------------------------------------------------------------
+# sensors
+# --------------------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Lidar:
+    beams: int
+    az_bins: int
+    el_min_deg: float
+    el_max_deg: float
+    r_min: float
+    r_max: float
+    sigma: float
+
+    @property
+    def n_rays(self) -> int:
+        return self.beams * self.az_bins
+
+
+LIDAR_32 = Lidar(32, 1024, -15.0, 15.0, 1.0, 120.0, 0.02)     # single-scan setup
+LIDAR_128 = Lidar(128, 2048, -25.0, 5.0, 1.0, 200.0, 0.03)    # dense high-speed setup
+LIDAR_64 = Lidar(64, 1024, -22.5, 22.5, 1.0, 120.0, 0.02)
+LIDAR_16 = Lidar(16, 1024, -15.0, 15.0, 1.0, 100.0, 0.02)
+
+
+def lidar_beams(beams: int, az_bins: int | None = None) -> Lidar:
+    base = {16: LIDAR_16, 32: LIDAR_32, 64: LIDAR_64, 128: LIDAR_128}[beams]
+    if az_bins is None:
+        return base
+    return Lidar(base.beams, az_bins, base.el_min_deg, base.el_max_deg, base.r_min, base.r_max, base.sigma)
+
+
+# --------------------------------------------------------------------------------------
+# poses
+# --------------------------------------------------------------------------------------
+def rot_z(yaw: float) -> np.ndarray:
+    c, s = math.cos(yaw), math.sin(yaw)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def axis_angle(axis: np.ndarray, angle: float) -> np.ndarray:
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    k = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * k + (1.0 - math.cos(angle)) * (k @ k)
+
+
+def make_pose(R: np.ndarray, t) -> np.ndarray:
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = t
+    return T
+
+
+def random_offset(rng: np.random.Generator, max_rot_deg: float, max_trans: float) -> np.ndarray:
+    """Uniform rotation angle <= max_rot_deg about a random axis, translation <= max_trans."""
+    axis = rng.normal(size=3)
+    ang = math.radians(max_rot_deg) * rng.uniform()
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    return make_pose(axis_angle(axis, ang), d * max_trans * rng.uniform())
+
+
+# --------------------------------------------------------------------------------------
+# scenes
+# --------------------------------------------------------------------------------------
+class Scene:
+    def __init__(self):
+        self._rows: list[list[float]] = []
+
+    def wall(self, x0, y0, x1, y1, zlo, zhi):
+        self._rows.append([PRIM_SEG, x0, y0, x1, y1, zlo, zhi, 0, 0, 0])
+
+    def arc(self, cx, cy, r, a0, a1, zlo, zhi):
+        self._rows.append([PRIM_ARC, cx, cy, r, a0, a1, zlo, zhi, 0, 0])
+
+    def pole(self, cx, cy, r, zlo, zhi):
+        self._rows.append([PRIM_CYL, cx, cy, r, zlo, zhi, 0, 0, 0, 0])
+
+    def box(self, cx, cy, cz, hx, hy, hz, yaw=0.0):
+        self._rows.append([PRIM_BOX, cx, cy, cz, hx, hy, hz, yaw, 0, 0])
+
+    @property
+    def prims(self) -> np.ndarray:
+        return np.ascontiguousarray(np.asarray(self._rows, dtype=np.float64).reshape(-1, 10))
+
+
+def raycast(scene: Scene, lidar: Lidar, pose: np.ndarray, seed: int, scan_id: int,
+            nthreads: int | None = None) -> np.ndarray:
+    """One scan as an (n, 3) float32 array in the sensor frame."""
+    lib = _load()
+    prims = scene.prims
+    pose = np.ascontiguousarray(pose, dtype=np.float64)
+    out = np.empty((lidar.n_rays, 3), dtype=np.float32)
+    nth = nthreads or min(16, os.cpu_count() or 1)
+    n = lib.synth_raycast(prims.ctypes.data, prims.shape[0], pose.ctypes.data,
+                          lidar.beams, lidar.az_bins, lidar.el_min_deg, lidar.el_max_deg,
+                          lidar.r_min, lidar.r_max, lidar.sigma, seed & (2**64 - 1), scan_id,
+                          out.ctypes.data, nth)
+    return np.ascontiguousarray(out[:n])
+
+
+def walls_scene(seed: int, n_walls: int = 20, radius: float = 80.0, keep_clear=((-7.0, 7.0), 3.0)) -> Scene:
+    """Ground plane plus n_walls random vertical walls with centres within `radius`.
+
+    Wall length 5-30 m, height 2-6 m, random yaw. Walls that would come within
+    keep_clear[1] m of the sensor path (x in keep_clear[0], y = 0) are redrawn.
+    """
+    rng = np.random.default_rng(seed)
+    sc = Scene()
+    (xlo, xhi), clear = keep_clear
+    made = 0
+    while made < n_walls:
+        r = radius * math.sqrt(rng.uniform())
+        phi = rng.uniform(0, 2 * math.pi)
+        cx, cy = r * math.cos(phi), r * math.sin(phi)
+        length = rng.uniform(5.0, 30.0)
+        height = rng.uniform(2.0, 6.0)
+        yaw = rng.uniform(0, math.pi)
+        dx, dy = 0.5 * length * math.cos(yaw), 0.5 * length * math.sin(yaw)
+        u = np.linspace(-1, 1, 64)
+        xs, ys = cx + u * dx, cy + u * dy
+        if np.any((xs > xlo - clear) & (xs < xhi + clear) & (np.abs(ys) < clear)):
+            continue
+        sc.wall(cx - dx, cy - dy, cx + dx, cy + dy, 0.0, height)
+        made += 1
+    return sc
+
+
+# ---- walled oval track ---------------------------------------------------------------
+TRACK_STRAIGHT = 700.0
+TRACK_RADIUS = 120.0
+TRACK_LENGTH = 2 * TRACK_STRAIGHT + 2 * math.pi * TRACK_RADIUS
+SENSOR_HEIGHT = 1.8
+
+
+def track_centreline(s: float):
+    """(x, y, heading) of the oval centreline at arclength s (counter-clockwise)."""
+    L, R = TRACK_STRAIGHT, TRACK_RADIUS
+    s = s % TRACK_LENGTH
+    half = 0.5 * L
+    if s < L:                                   # bottom straight, heading +x
+        return -half + s, -R, 0.0
+    s -= L
+    if s < math.pi * R:                         # right semicircle
+        a = -0.5 * math.pi + s / R
+        return half + R * math.cos(a), R * math.sin(a), a + 0.5 * math.pi
+    s -= math.pi * R
+    if s < L:                                   # top straight, heading -x
+        return half - s, R, math.pi
+    s -= L
+    a = 0.5 * math.pi + s / R                   # left semicircle
+    return -half + R * math.cos(a), R * math.sin(a), a + 0.5 * math.pi
+
+
+def track_pose(s: float, weave: float = 1.5, weave_len: float = 400.0) -> np.ndarray:
+    """Sensor pose at arclength s: centreline plus a gentle lateral weave."""
+    x, y, h = track_centreline(s)
+    lat = weave * math.sin(2 * math.pi * s / weave_len)
+    dlat = weave * 2 * math.pi / weave_len * math.cos(2 * math.pi * s / weave_len)
+    nx, ny = -math.sin(h), math.cos(h)
+    yaw = h + math.atan(dlat)
+    return make_pose(rot_z(yaw), [x + lat * nx, y + lat * ny, SENSOR_HEIGHT])
+
+
+def oval_track_scene(seed: int) -> Scene:
+    """Walled oval: straights of 700 m, radius 120 m, walls at +-10 m.
+
+    Each side has a 1.5 m barrier and a fence from 1.5 m to 6 m just behind it,
+    0.3 m poles every 25 m in front of the barriers, grandstands outside the
+    straights and a few buildings in the infield.
+    """
+    rng = np.random.default_rng(seed)
+    sc = Scene()
+    L, R = TRACK_STRAIGHT, TRACK_RADIUS
+    half = 0.5 * L
+    for off, fence_off in ((-10.0, -10.3), (10.0, 10.3)):   # inner (-) and outer (+) side
+        for o, zlo, zhi in ((off, 0.0, 1.5), (fence_off, 1.5, 6.0)):
+            rr = R + o
+            sc.wall(-half, -rr, half, -rr, zlo, zhi)
+            sc.wall(half, rr, -half, rr, zlo, zhi)
+            sc.arc(half, 0.0, rr, -0.5 * math.pi, 0.5 * math.pi, zlo, zhi)
+            sc.arc(-half, 0.0, rr, 0.5 * math.pi, 1.5 * math.pi, zlo, zhi)
+    s = 0.0
+    while s < TRACK_LENGTH - 1e-6:
+        x, y, h = track_centreline(s)
+        nx, ny = -math.sin(h), math.cos(h)
+        for side in (-9.5, 9.5):
+            sc.pole(x + side * nx, y + side * ny, 0.15, 0.0, 8.0)
+        s += 25.0
+    for xc in (-220.0, 0.0, 220.0):
+        for sgn in (-1.0, 1.0):
+            h = rng.uniform(14.0, 22.0)
+            sc.box(xc + rng.uniform(-20, 20), sgn * (R + 30.0), 0.5 * h, 45.0, 9.0, 0.5 * h, 0.0)
+    for _ in range(8):
+        bx, by = rng.uniform(-300, 300), rng.uniform(-70, 70)
+        hx, hy, hz = rng.uniform(5, 15), rng.uniform(5, 15), rng.uniform(3, 8)
+        sc.box(bx, by, hz, hx, hy, hz, rng.uniform(0, math.pi))
+    return sc
+
+
+# --------------------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------------------
+@dataclass
+class SingleScanProblem:
+    """Single scan-to-map registration: map scans + query scan + poses."""
+    map_scans: list
+    map_poses: list
+    query: np.ndarray
+    truth: np.ndarray
+    init: np.ndarray
+
+
+def single_scan_problem(seed: int, lidar: Lidar = LIDAR_32, n_prior: int = 10,
+                        max_rot_deg: float = 2.0, max_trans: float = 0.5) -> SingleScanProblem:
+    """Ground plane + 20 random walls within 80 m; 10 prior scans 1 m apart along x
+    with +-5 deg yaw jitter form the map; the query is taken at a nearby true pose and
+    the initial guess is truth * offset (rotation <= 2 deg, translation <= 0.5 m)."""
+    scene = walls_scene(seed)
+    rng = np.random.default_rng(seed + 1_000_003)
+    poses = []
+    for i in range(n_prior):
+        yaw = math.radians(rng.uniform(-5.0, 5.0))
+        poses.append(make_pose(rot_z(yaw), [i - n_prior // 2, 0.0, SENSOR_HEIGHT]))
+    scans = [raycast(scene, lidar, p, seed, i) for i, p in enumerate(poses)]
+    yaw = math.radians(rng.uniform(-5.0, 5.0))
+    truth = make_pose(rot_z(yaw), [0.5 + rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), SENSOR_HEIGHT])
+    query = raycast(scene, lidar, truth, seed, 1000)
+    init = truth @ random_offset(rng, max_rot_deg, max_trans)
+    return SingleScanProblem(scans, poses, query, truth, init)
+
+
+class TrackSequence:
+    """High-speed sequence on the walled oval: the sensor moves `step` metres per
+    frame (70 m/s at 10 Hz = 7 m). Scans are generated on demand and cached."""
+
+    def __init__(self, seed: int = 42, lidar: Lidar = LIDAR_128, step: float = 7.0, s0: float = 0.0):
+        self.seed, self.lidar, self.step, self.s0 = seed, lidar, step, s0
+        self.scene = oval_track_scene(seed)
+        self._cache: dict[int, np.ndarray] = {}
+
+    def pose(self, t: int) -> np.ndarray:
+        return track_pose(self.s0 + self.step * t)
+
+    def scan(self, t: int) -> np.ndarray:
+        if t not in self._cache:
+            self._cache[t] = raycast(self.scene, self.lidar, self.pose(t), self.seed, t)
+        return self._cache[t]
+
+
+def constant_velocity_guess(prev2: np.ndarray, prev1: np.ndarray) -> np.ndarray:
+    """T_{t} ~= T_{t-1} (T_{t-2}^-1 T_{t-1})."""
+    return prev1 @ (np.linalg.inv(prev2) @ prev1)
