@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the scan-to-map registration hot path on one GB300.
+
+Workload: the high-speed sequence - a 128-beam x 2048-azimuth spinning LiDAR
+(~260k points per scan, 0.03 m range noise) moving at 70 m/s, 10 Hz (7 m per
+frame) around a walled oval track. One step = one scan through the whole path:
+ingest, scan-local downsampling and Eq. 1 covariances, Gauss-Newton GICP
+registration (at most 10 iterations, ||xi|| <= 5e-3), adaptive threshold update,
+ASMD-capped insert at the registered pose with added-point covariances, and
+eviction beyond 150 m. v = 0.5 m, N_max = 20, k = 5.
+
+Inputs are synthetic (seeded ray casting) and resident in HBM before timing;
+the e2e pass feeds the same scans from pinned host memory through the public
+API. L2 (129 MB) is flushed between timed steps by writing a 256 MiB buffer.
+
+`--impl reference` times the CPU oracle (plain FP64 C++) on the host instead.
+Multi-GPU: one independent vehicle per rank (replicas, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Mpoints/s at 128x2048 beams (high-speed sequence, per-scan register+map update)"
+UNIT = "Mpoints/s"
+V, NMAX, K_COV = 0.5, 20, 5
+R_NEAR, R_MAX, EVICT_R = 10.0, 200.0, 150.0
+MAX_ITERS, CONV_EPS = 10, 5e-3
+SIGMA0, MIN_MOTION = 2.0, 0.1
+MAX_SCAN = 300_000
+MAX_VOXELS = 1 << 21
+PRIOR_NOISE = (0.05, 0.1)   # IMU-like prior: metres, degrees per frame
+
+
+def workload_config(steps, warmup, n_gpus):
+    return {
+        "workload": "high-speed sequence: 128x2048 LiDAR (~260k pts/scan, sigma 0.03 m), 70 m/s at 10 Hz "
+                    "on a walled oval (700 m straights, R 120 m), per-scan register + ASMD insert + evict",
+        "voxel_m": V, "n_max": NMAX, "k_cov": K_COV, "gn_max_iters": MAX_ITERS, "conv_eps": CONV_EPS,
+        "asmd": {"r_near_m": R_NEAR, "r_max_m": R_MAX}, "evict_radius_m": EVICT_R,
+        "threshold": {"sigma0_m": SIGMA0, "min_motion_m": MIN_MOTION},
+        "init_prior": "true inter-frame motion + seeded noise (%.2f m, %.1f deg)" % PRIOR_NOISE,
+        "scans_timed": steps, "scans_warmup": warmup, "first_scan": "inserted at its true pose (setup)",
+        "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident before timing",
+        "parallelism": "replicas" if n_gpus > 1 else "single GPU",
+    }
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def rank_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --------------------------------------------------------------------------------------- inputs
+class Vehicle:
+    """One simulated vehicle on the oval: scans, true poses and the motion prior."""
+
+    def __init__(self, rank: int):
+        self.seq = synth.TrackSequence(seed=42 + rank, s0=300.0 * rank)
+        self.rng = np.random.default_rng(1000 + rank)
+
+    def prior(self, t: int, prev_est: np.ndarray) -> np.ndarray:
+        """IMU-like prediction: previous estimate times the true motion, with seeded noise."""
+        d = np.linalg.inv(self.seq.pose(t - 1)) @ self.seq.pose(t)
+        return prev_est @ d @ synth.random_offset(self.rng, PRIOR_NOISE[1], PRIOR_NOISE[0])
+
+
+def rot_angle(R):
+    return math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2)))
+
+
+# --------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = ""
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out)) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gicp.cu", "search.cuh", "far_internal.cuh", "gicp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_26010_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per k_gn_iter launch from the committed ncu summary, if it matches the source."""
+    p = os.path.join(ROOT, "profiles", "k_gn_iter_hbm_128x2048.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# --------------------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2606_26010_gb300 import build as far_build
+    from paper_2606_26010_gb300 import far
+
+    rank, world, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    far_build.build()
+    stream = torch.cuda.Stream()
+    veh = Vehicle(rank)
+    n_total = 1 + args.warmup + args.steps
+    scans = [veh.seq.scan(t) for t in range(n_total)]
+    dev = [torch.from_numpy(s).cuda() for s in scans]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def make_map():
+        with torch.cuda.stream(stream):
+            m = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=MAX_VOXELS, load_factor=0.5,
+                             max_scan_points=MAX_SCAN, stream=stream.cuda_stream)
+            m.insert(dev[0], veh.seq.pose(0), asmd=True, r_near=R_NEAR, r_max=R_MAX)
+        return m
+
+    def step(m, thr, t, est, inp):
+        init = veh.prior(t, est)
+        tau, kappa = thr.get()
+        pose, _, res = m.process_scan(inp, init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau, kappa=kappa,
+                                      asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R)
+        thr.update(init, pose)
+        return pose, res
+
+    # ---- device-resident pass (value)
+    m = make_map()
+    m.set_profiling(True)
+    thr = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
+    est = veh.seq.pose(0)
+    with torch.cuda.stream(stream):
+        for t in range(1, 1 + args.warmup):
+            est, _ = step(m, thr, t, est, dev[t])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms, gn_ms, gn_bytes, gn_launches, stage_acc, results = [], [], [], [], {}, []
+    launches0 = far.launch_count()
+    launches_in_steps = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for t in range(1 + args.warmup, n_total):
+                flush.zero_()
+                l0 = far.launch_count()
+                ev0.record(stream)
+                est, res = step(m, thr, t, est, dev[t])
+                ev1.record(stream)
+                ev1.synchronize()
+                launches_in_steps += far.launch_count() - l0
+                step_ms.append(ev0.elapsed_time(ev1))
+                st = m.stage_times()
+                for k_, v_ in st.items():
+                    stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
+                n_src, u_v, p_touched = m.gn_footprint()
+                nblk = min((scans[t].shape[0] + 255) // 256, 152 * 8)
+                # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B),
+                # each probed voxel's slot (16 B), its points (12 B xyz + 4 B id + 24 B covariance),
+                # and the FP64 block partials (28 doubles per block)
+                gn_bytes.append(36.0 * n_src + 16.0 * u_v + 40.0 * p_touched + 224.0 * nblk)
+                gn_ms.append(st["gn_launch_ms"])
+                gn_launches.append(st["gn_launches"])
+                results.append(res)
+                err = np.linalg.inv(veh.seq.pose(t)) @ est
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    pts = float(sum(scans[t].shape[0] for t in range(1 + args.warmup, n_total)))
+    dev_s = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([dev_s, pts], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        dev_s_all, pts_all = float(mx[0]), float(sm[1])
+    else:
+        dev_s_all, pts_all = dev_s, pts
+    value = pts_all / dev_s_all / 1e6
+    lat = np.array(step_ms)
+
+    # roofline of the dominant kernel (k_gn_iter)
+    peak, peak_kind = measured_peaks()
+    tot_b = sum(b * n for b, n in zip(gn_bytes, gn_launches))
+    tot_t = sum(ms * n for ms, n in zip(gn_ms, gn_launches)) / 1e3
+    achieved = tot_b / tot_t / 1e9 if tot_t > 0 else 0.0
+    per_launch_bytes = tot_b / max(1, sum(gn_launches))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 5), "traffic": ncu_traffic(), "kernel": "k_gn_iter",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": round(per_launch_bytes),
+                "mean_launch_us": round(1e3 * tot_t / max(1, sum(gn_launches)) * 1e3, 2),
+                "launches": int(sum(gn_launches))}
+
+    # ---- end-to-end pass through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(s).pin_memory() for s in scans]
+        m2 = make_map()
+        thr2 = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
+        est2 = veh.seq.pose(0)
+        with torch.cuda.stream(stream):
+            for t in range(1, 1 + args.warmup):
+                est2, _ = step(m2, thr2, t, est2, pinned[t])
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e2e_s = 0.0
+            for t in range(1 + args.warmup, n_total):
+                flush.zero_()
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                est2, _ = step(m2, thr2, t, est2, pinned[t])
+                e2e_s += time.perf_counter() - w0
+        if world > 1:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt[0])
+        h2d = pts / args.steps * 12.0
+        # pose (128 B) + registration state (~700 B) + map counters (96 B) read back per step
+        d2h = 128 + 704 + 96
+        e2e = {"value": round(pts_all / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": round(h2d),
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
+               "api": "far_process_scan with pinned host points"}
+        m2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_steps)
+
+    n_iter = np.mean([r["iters"] for r in results])
+    st_mean = {k_: round(v_ / args.steps, 4) for k_, v_ in stage_acc.items()}
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s_all / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ray-cast LiDAR; the paper's datasets are not available)",
+        "config": workload_config(args.steps, args.warmup, world),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                       "p99": round(float(np.percentile(lat, 99)), 4),
+                       "max": round(float(lat.max()), 4), "mean": round(float(lat.mean()), 4)},
+        "stages_ms_mean": st_mean,
+        "gn_iters_mean": round(float(n_iter), 3),
+        "points_per_scan": round(pts / args.steps),
+        "n_src_mean": round(float(np.mean([r["n_src"] for r in results]))),
+        "map_points_end": int(results[-1]["n_points"]),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches_in_steps),
+        "clocks": clk.summary(),
+        "wall_s_timed_region": round(wall, 3),
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------------------- CPU oracle
+def oracle_steps(n_steps: int, rank: int = 0, time_cap_s: float = 1e9):
+    """Run the oracle over the same workload: first scan at its true pose (untimed),
+    then n_steps scans of register + threshold update + ASMD insert + eviction (timed)."""
+    import oracle
+    veh = Vehicle(rank)
+    m = oracle.OracleMap(V, NMAX, K_COV)
+    m.insert(veh.seq.scan(0), veh.seq.pose(0), asmd=True, r_c=R_NEAR, r_max=R_MAX)
+    thr = oracle.Threshold(SIGMA0, MIN_MOTION, R_MAX)
+    est = veh.seq.pose(0)
+    times, pts = [], []
+    for t in range(1, n_steps + 1):
+        scan = veh.seq.scan(t)
+        init = veh.prior(t, est)
+        t0 = time.perf_counter()
+        tau, kappa = thr.get()
+        est, _, _ = m.register(scan, init, MAX_ITERS, CONV_EPS, tau, kappa)
+        thr.update(init, est)
+        m.insert(scan, est, asmd=True, r_c=R_NEAR, r_max=R_MAX)
+        m.evict(est[:3, 3], EVICT_R)
+        times.append(time.perf_counter() - t0)
+        pts.append(scan.shape[0])
+        if sum(times) > time_cap_s:
+            break
+    return times, pts
+
+
+def cpu_baseline(n_steps: int):
+    times, pts = oracle_steps(n_steps)
+    v = sum(pts) / sum(times) / 1e6
+    return {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "ms_per_scan": round(1e3 * sum(times) / len(times), 2),
+            "sample": f"first {len(times)} scans of the same sequence (register + ASMD insert + evict), "
+                      f"single-threaded FP64 oracle on the host"}
+
+
+def run_reference(args):
+    rank, world, local = rank_env()
+    if rank != 0:
+        return
+    # warm-up: build the oracle library and touch the generator
+    import oracle
+    oracle.build()
+    if args.warmup > 0:
+        oracle_steps(min(args.warmup, 1))
+    times, pts = oracle_steps(args.steps, time_cap_s=150.0)
+    v = sum(pts) / sum(times) / 1e6
+    lat = np.array(times) * 1e3
+    out = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": len(times),
+           "warmup": args.warmup, "ms_per_step": round(float(lat.mean()), 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+           "data": "synthetic (seeded ray-cast LiDAR)", "config": workload_config(len(times), args.warmup, world),
+           "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                          "p99": round(float(np.percentile(lat, 99)), 3)},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{len(times)} consecutive scans of the sequence (capped at 150 s)"},
+           "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

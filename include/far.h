@@ -1,0 +1,264 @@
+/*
+ * far.h - C ABI of the GB300 (sm_103a) scan-to-map registration library.
+ *
+ * The library implements the data-parallel hot path of FAR-LIO (Sec. III-A):
+ * the voxel hashmap with batched insert, adaptive-density cap and eviction
+ * (Sec. III-A.2 "cuVoxelMap", Sec. III-A.3), the 27-voxel neighbour search,
+ * per-point covariances (Eq. 1), and the sparsity-aware GICP Gauss-Newton
+ * loop (Eq. 2-6). All arithmetic runs in the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *  - Status: every function returns far_status and never aborts. On error the
+ *    outputs are left untouched and far_last_error() describes the cause
+ *    (a thread-local string).
+ *  - Points: `xyz` is an array of n records of `stride_bytes` bytes whose first
+ *    12 bytes are float x, y, z (stride_bytes >= 12, a multiple of 4). The
+ *    pointer may be host memory (pageable or pinned) or device memory; the
+ *    library detects which and copies host data on the map's stream. The caller
+ *    keeps ownership of every input and output buffer.
+ *  - Poses: row-major 4x4 double, sensor-to-map. Only the top 3x4 is read.
+ *  - Covariances: 6x6 row-major double, ordered [rotation; translation].
+ *  - Streams: each map is bound to the CUDA stream given at creation; all work
+ *    of that map is ordered on it. Calls on one map must not overlap in time
+ *    from several host threads. Functions that return host results synchronise
+ *    that stream before returning.
+ *  - Point ids: every point admitted to a map gets a 32-bit id, assigned
+ *    consecutively in (call, input index) order; ids break distance ties.
+ */
+#ifndef FAR_H
+#define FAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum far_status {
+    FAR_OK = 0,
+    FAR_ERR_INVALID = 1,     /* bad argument (null pointer, size, parameter) */
+    FAR_ERR_OOM = 2,         /* device allocation failed or HBM budget exceeded */
+    FAR_ERR_CAPACITY = 3,    /* table, bucket pool or id space full; excess points dropped */
+    FAR_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    FAR_ERR_DEGENERATE = 5,  /* fewer than 6 correspondences or H not positive definite */
+    FAR_ERR_TIMEOUT = 6      /* registration exceeded its time budget */
+} far_status;
+
+/* Opaque map: owns all device memory of one voxel map and its scratch. */
+typedef struct far_map far_map;
+
+/*
+ * Map parameters (Sec. III-A.2: voxel size v, at most N points per voxel,
+ * "regularly spaced"; Eq. 1: k nearest neighbours for covariances).
+ */
+typedef struct far_map_params {
+    float voxel_size;           /* v in metres, > 0 */
+    uint32_t max_pts_per_voxel; /* N_max, 1..64 */
+    uint32_t k_cov;             /* k for Eq. 1, 1..16 */
+    float min_spacing;          /* d_min between points of a voxel; < 0 => v / sqrt(N_max); 0 => off */
+    uint64_t max_voxels;        /* size of the bucket pool (live voxels) */
+    float load_factor;          /* hash slots = next_pow2(max_voxels / load_factor), 0.05..0.95 */
+    uint32_t max_scan_points;   /* largest scan accepted by insert / register */
+    uint32_t precision_mode;    /* 0: FP32 map coordinates (only mode of this version) */
+} far_map_params;
+
+/* Adaptive Submap Density cap of an insert (Sec. III-A.3). */
+typedef struct far_insert_params {
+    int32_t asmd;     /* 0: cap = N_max for every voxel; 1: adaptive cap */
+    double r_near;    /* close-range radius r_c (m) over which the mean occupancy is taken */
+    double r_max;     /* range (m) at which the cap has decayed to k */
+} far_insert_params;
+
+/* Registration parameters (Sec. III-A.2, Eq. 4-6 and the termination rule). */
+typedef struct far_reg_params {
+    uint32_t max_iters;         /* Gauss-Newton iterations at most */
+    double conv_eps;            /* stop when ||xi||_2 <= conv_eps (paper: 5e-3); 0 => run max_iters */
+    float tau;                  /* correspondence distance threshold (m) */
+    float kappa;                /* Cauchy kernel scale (Eq. 5) */
+    double time_budget_s;       /* wall-clock cap of one registration; <= 0 => none */
+    uint32_t threads_per_point; /* 1 (default); other values are tuning hints */
+} far_reg_params;
+
+typedef struct far_reg_stats {
+    uint32_t iters;      /* Gauss-Newton updates applied */
+    uint32_t n_src;      /* source points after scan-local downsampling */
+    uint32_t n_corr;     /* correspondences of the last linearisation */
+    uint32_t n_p2p;      /* of which point-to-point (SA GICP special case) */
+    int32_t converged;   /* 1 if ||xi|| <= conv_eps was reached */
+    int32_t status;      /* far_status of the registration */
+    double chi2;         /* sum of the Cauchy cost of the last linearisation */
+} far_reg_stats;
+
+/* Human-readable name of a status code (static string). */
+const char* far_status_string(far_status s);
+/* Description of the last error raised on the calling thread (static per thread). */
+const char* far_last_error(void);
+/* Library version string. */
+const char* far_version(void);
+
+/* Device bytes a map with these parameters preallocates (for HBM budgeting). */
+far_status far_map_bytes(const far_map_params* params, uint64_t* out_bytes);
+
+/*
+ * Create a map and preallocate all its device memory (the paper preallocates
+ * its VRAM, Sec. IV-B). `cuda_stream` is a cudaStream_t (NULL = legacy default).
+ */
+far_status far_map_create(const far_map_params* params, void* cuda_stream, far_map** out);
+far_status far_map_destroy(far_map* map);
+/* Remove every voxel; ids restart at 0. */
+far_status far_map_clear(far_map* map);
+
+/*
+ * Insert a scan (Sec. III-A.3): points are transformed by `pose`
+ * (x_w = fp32(R p + t), evaluated in FP64), keyed by voxel, and admitted in input
+ * order while their voxel holds fewer than its cap and every point already in it
+ * is at least d_min away. The cap is N_max, or with ASMD
+ *   N_ASMD(r) = clamp(round(N_near + (k - N_near) * min(r / r_max, 1)), k, N_max),
+ * N_near = mean point count of this scan's voxels within r_near of the sensor,
+ * r = distance from the voxel centre to the sensor. Then the Eq. 1 covariance of
+ * every added point is computed against the updated map. `params` may be NULL
+ * (cap = N_max). `n_inserted` (may be NULL) receives the number of added points.
+ * Points with non-finite coordinates or keys beyond +-2^20 voxels are skipped.
+ */
+far_status far_map_insert(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                          const double pose[16], const far_insert_params* params, uint64_t* n_inserted);
+
+/*
+ * Evict (Sec. III-A.3): remove every voxel whose centre ((key + 0.5) v) is
+ * farther than `radius` from `center` (distance computed in FP64).
+ */
+far_status far_map_evict(far_map* map, const double center[3], double radius, uint64_t* n_removed);
+
+/* Live voxels and points of the map. */
+far_status far_map_size(const far_map* map, uint64_t* n_voxels, uint64_t* n_points);
+
+/*
+ * Sorted dump of the map (parity checks): voxels in ascending (x, y, z) key
+ * order, points of a voxel in insertion order. Host output arrays:
+ * keys[3 * voxels], counts[voxels], ids[points], xyz[3 * points],
+ * cov[6 * points] (xx xy xz yy yz zz), valid[points]. Capacities are checked
+ * against far_map_size(); any pointer except keys/counts may be NULL.
+ */
+far_status far_map_export(const far_map* map, int32_t* keys, uint32_t* counts, uint32_t* ids, float* xyz,
+                          float* cov, uint8_t* valid, uint64_t cap_voxels, uint64_t cap_points);
+
+/*
+ * 1-NN over the 27 voxels around each query point's voxel (Sec. III-A.2):
+ * smallest FP32 d^2 = ((dx*dx + dy*dy) + dz*dz), ties to the smaller id.
+ * out_ids[i] = id, or -1 when there is no candidate or d^2 > fp32(tau)^2.
+ * out_d2 (may be NULL) receives d^2 (+inf without a candidate).
+ * Outputs may be host or device pointers.
+ */
+far_status far_map_nearest(far_map* map, const float* q, uint64_t n, uint32_t stride_bytes, float tau,
+                           int64_t* out_ids, float* out_d2);
+
+/*
+ * k nearest map points (k <= 16) over the 27 voxels, ordered by (d^2, id).
+ * out_ids[n * k] (0xFFFFFFFF padding), out_found[n]. Host or device outputs.
+ */
+far_status far_map_knn(far_map* map, const float* q, uint64_t n, uint32_t stride_bytes, uint32_t k,
+                       uint32_t* out_ids, int32_t* out_found);
+
+/*
+ * Source side of a registration (Sec. III-A.2 Cov-Calc): build a scan-local
+ * voxel map with the map's v, N_max and d_min (no ASMD), keep the admitted
+ * points (the downsampling), and compute their Eq. 1 covariances from k
+ * neighbours in that local map. Outputs (host or device, room for n entries):
+ * index[n_src] (input index of each admitted point, ascending), cov[6 n_src],
+ * valid[n_src], knn_ids[k n_src] (local admission ranks; may be NULL).
+ */
+far_status far_scan_sources(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, int64_t* out_index,
+                            float* out_cov, uint8_t* out_valid, uint32_t* out_knn_ids, uint64_t* n_src);
+
+/*
+ * One Gauss-Newton linearisation of Eq. 4 at `pose` without the update:
+ * H (36, row-major) and g (6) as defined by J = [[q]x, -I], IRLS Cauchy weights
+ * w = 1 / (1 + e^2 / kappa^2), e^2 = d^T M d, M = (Sigma_r + R Sigma_s R^T)^-1
+ * or I when either covariance is invalid. out_corr[n_src] (may be NULL) receives
+ * the map id matched by each source point or -1. Host outputs.
+ */
+far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, const double pose[16],
+                         float tau, float kappa, double out_H[36], double out_g[6], int32_t* out_corr,
+                         far_reg_stats* stats);
+
+/*
+ * Register a scan against the map (Sec. III-A.2): scan-local downsampling and
+ * covariances, then Gauss-Newton iterations from `init_pose`, each solving
+ * H xi = -g by FP64 Cholesky and applying T <- exp(xi) T (Eq. 6), until
+ * ||xi|| <= conv_eps or max_iters. out_cov (may be NULL) receives H^-1 of the
+ * last linearisation. Returns FAR_ERR_DEGENERATE (pose = last good estimate)
+ * when fewer than 6 correspondences remain or H is not positive definite.
+ */
+far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                             const double init_pose[16], const far_reg_params* params, double out_pose[16],
+                             double out_cov[36], far_reg_stats* stats);
+
+typedef struct far_step_result {
+    far_reg_stats reg;    /* registration of the scan */
+    uint64_t n_inserted;  /* points added to the map */
+    uint64_t n_removed;   /* points evicted */
+    uint64_t n_voxels;    /* map size after the step */
+    uint64_t n_points;
+} far_step_result;
+
+/*
+ * One scan of the LiDAR pipeline on the device (Sec. III-A.2 then III-A.3):
+ * far_register_scan from `init_pose`, then - when the registration succeeded -
+ * the insert of the same scan at the registered pose with the cap of `ins`
+ * (NULL: N_max), then eviction of the voxels farther than `evict_radius` from the
+ * registered position (0 or +inf: no eviction). The registered pose never leaves
+ * the device between the stages; the call synchronises once at the end.
+ * Returns the registration status (a degenerate or timed-out scan is discarded,
+ * the map is left unchanged except for eviction), or FAR_ERR_CAPACITY.
+ */
+far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                            const double init_pose[16], const far_reg_params* reg, const far_insert_params* ins,
+                            double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Kernel launches issued by the library since it was loaded (all maps). */
+unsigned long long far_launch_count(void);
+
+/*
+ * Per-stage device timeline of the last far_process_scan / far_register_scan
+ * (CUDA events on the map's stream; the paper reports the same split per frame,
+ * Sec. IV-B, Fig. 4a). Stages: ingest (a copy of host points and packing),
+ * sources (scan-local map and Eq. 1 covariances), Gauss-Newton (all launches),
+ * insert (ASMD cap, admission, added-point covariances), evict.
+ * gn_launch_ms is the mean duration of the launches that did work.
+ */
+typedef struct far_stage_times {
+    double ingest_ms, sources_ms, gauss_newton_ms, gn_launch_ms;
+    uint32_t gn_launches;
+    double insert_ms, evict_ms, total_ms;
+} far_stage_times;
+far_status far_set_profiling(far_map* map, int enable);
+far_status far_get_stage_times(const far_map* map, far_stage_times* out);
+
+/*
+ * Footprint of one Gauss-Newton launch at the last registration's final pose:
+ * out[0] = source points, out[1] = distinct map voxels probed by their
+ * 27-neighbourhoods, out[2] = points held by those voxels. Diagnostic only.
+ */
+far_status far_gn_footprint(far_map* map, uint64_t out[3]);
+
+/*
+ * Adaptive correspondence threshold (the scheme the paper adopts from
+ * Vizzo et al., Sec. III-A.2), pure host code: sigma = sqrt(mean delta^2) over
+ * recorded frames (sigma0 before any), tau = 3 sigma, kappa = sigma / 3. A frame
+ * is recorded when the translation of init^-1 * result exceeds min_motion;
+ * delta = 2 r_max sin(theta / 2) + ||dt||.
+ */
+typedef struct far_threshold {
+    double sigma0, min_motion, r_max, sse;
+    int64_t n;
+} far_threshold;
+far_status far_threshold_init(far_threshold* t, double sigma0, double min_motion, double r_max);
+far_status far_threshold_get(const far_threshold* t, double* tau, double* kappa);
+far_status far_threshold_update(far_threshold* t, const double init_pose[16], const double result_pose[16]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FAR_H */

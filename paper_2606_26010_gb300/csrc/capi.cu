@@ -1,0 +1,896 @@
+// C ABI of the registration library (declarations and contracts in include/far.h).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "far.h"
+#include "gicp.cuh"
+#include "map.cuh"
+#include "primitives.cuh"
+
+using namespace far;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void far::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Events of the per-stage timeline (Sec. IV-B reports per-stage runtimes per frame).
+enum { EV_INGEST = 0, EV_SOURCES, EV_INSERT, EV_EVICT, EV_END, EV_GN0, EV_COUNT_FIXED = EV_GN0 };
+constexpr int MAX_ITERS = 1000;
+
+far_status fail(far_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e__ = (call);                                                                    \
+        if (e__ != cudaSuccess)                                                                      \
+            return fail(FAR_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, \
+                        __LINE__);                                                                   \
+    } while (0)
+
+u32 next_pow2(uint64_t x) {
+    uint64_t p = 64;
+    while (p < x) p <<= 1;
+    return (u32)p;
+}
+
+int log2_u32(u32 x) {
+    int b = 0;
+    while ((1u << b) < x) ++b;
+    return b;
+}
+
+// Planned device allocations of one map (sizes in bytes), shared by create and far_map_bytes.
+struct Plan {
+    u32 cap, local_cap, max_buckets, local_buckets, max_n, nmax;
+    std::vector<std::pair<void**, size_t>> items;
+    size_t total = 0;
+};
+
+}  // namespace
+
+struct far_map {
+    far_map_params p{};
+    cudaStream_t stream = nullptr;
+    DeviceMap map;
+    DeviceMap local;
+    Scratch s;
+    double* d_cov36 = nullptr;
+    MapCounters* h_ctr = nullptr;  // pinned mirrors
+    RegState* h_st = nullptr;
+    u32* h_scal = nullptr;
+    double* h_cov36 = nullptr;
+    std::vector<void*> allocs;
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;     // EV_COUNT_FIXED + MAX_ITERS + 1
+    bool ev_used[EV_COUNT_FIXED] = {};
+    u32 gn_launched = 0;
+    far_stage_times last{};
+};
+
+namespace {
+
+far_status validate_params(const far_map_params* p) {
+    if (!p) return fail(FAR_ERR_INVALID, "params is NULL");
+    if (!(p->voxel_size > 0.0f) || !std::isfinite(p->voxel_size))
+        return fail(FAR_ERR_INVALID, "voxel_size must be finite and > 0");
+    if (p->max_pts_per_voxel < 1 || p->max_pts_per_voxel > (u32)NMAX_LIMIT)
+        return fail(FAR_ERR_INVALID, "max_pts_per_voxel must be in 1..%d", NMAX_LIMIT);
+    if (p->k_cov < 1 || p->k_cov > (u32)KMAX) return fail(FAR_ERR_INVALID, "k_cov must be in 1..%d", KMAX);
+    if (p->max_voxels < 1) return fail(FAR_ERR_INVALID, "max_voxels must be >= 1");
+    if (!(p->load_factor >= 0.05f && p->load_factor <= 0.95f))
+        return fail(FAR_ERR_INVALID, "load_factor must be in [0.05, 0.95]");
+    if (p->max_scan_points < 1 || p->max_scan_points > (1u << 26))
+        return fail(FAR_ERR_INVALID, "max_scan_points must be in 1..2^26");
+    if (p->precision_mode != 0) return fail(FAR_ERR_INVALID, "precision_mode %u is not supported", p->precision_mode);
+    if ((double)p->max_voxels * p->max_pts_per_voxel >= 4294967295.0)
+        return fail(FAR_ERR_INVALID, "max_voxels * max_pts_per_voxel must stay below 2^32");
+    if ((double)p->max_voxels / p->load_factor > 2147483648.0)
+        return fail(FAR_ERR_INVALID, "hash table would exceed 2^31 slots");
+    if (!std::isfinite(p->min_spacing)) return fail(FAR_ERR_INVALID, "min_spacing must be finite");
+    return FAR_OK;
+}
+
+Plan make_plan(const far_map_params& p, far_map* m) {
+    Plan pl;
+    pl.max_n = p.max_scan_points;
+    pl.nmax = p.max_pts_per_voxel;
+    pl.max_buckets = (u32)p.max_voxels;
+    pl.cap = next_pow2((uint64_t)std::ceil((double)p.max_voxels / p.load_factor));
+    pl.local_buckets = pl.max_n;
+    pl.local_cap = next_pow2((uint64_t)pl.max_n * 2);
+    const size_t n = pl.max_n;
+    const u32 rblk = radix_blocks(pl.max_n);
+    const size_t partials = std::max<size_t>(scan_blocks(pl.max_n), scan_blocks(256u * rblk)) + 2;
+    static far_map dummy;
+    far_map* t = m ? m : &dummy;
+    auto add = [&](void** ptr, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        pl.items.push_back({ptr, bytes});
+        pl.total += bytes;
+    };
+    // registration map
+    add((void**)&t->map.slots, (size_t)pl.cap * sizeof(Slot));
+    add((void**)&t->map.slots_alt, (size_t)pl.cap * sizeof(Slot));
+    add((void**)&t->map.pts, (size_t)pl.max_buckets * pl.nmax * sizeof(float4));
+    add((void**)&t->map.cov, (size_t)pl.max_buckets * pl.nmax * 2 * sizeof(float4));
+    add((void**)&t->map.ring, (size_t)pl.max_buckets * sizeof(u32));
+    add((void**)&t->map.ctr, sizeof(MapCounters));
+    // scan-local map
+    add((void**)&t->local.slots, (size_t)pl.local_cap * sizeof(Slot));
+    add((void**)&t->local.pts, (size_t)pl.local_buckets * pl.nmax * sizeof(float4));
+    add((void**)&t->local.ring, (size_t)pl.local_buckets * sizeof(u32));
+    add((void**)&t->local.ctr, sizeof(MapCounters));
+    // scratch
+    add(&t->s.staging, n * 32);
+    add((void**)&t->s.in4, n * sizeof(float4));
+    add((void**)&t->s.world, n * sizeof(float4));
+    add((void**)&t->s.keys, n * sizeof(u64));
+    for (u32** a : {&t->s.sk, &t->s.sv, &t->s.sk_alt, &t->s.sv_alt, &t->s.flags, &t->s.gidx, &t->s.admitted,
+                    &t->s.rank, &t->s.pos, &t->s.added, &t->s.src_index})
+        add((void**)a, (n + 1) * sizeof(u32));
+    add((void**)&t->s.gstart, (n + 2) * sizeof(u32));
+    add((void**)&t->s.hist, (size_t)256 * rblk * sizeof(u32));
+    add((void**)&t->s.partials, partials * sizeof(u32));
+    add((void**)&t->s.scal, SCAL_COUNT * sizeof(u32));
+    add((void**)&t->s.src, n * sizeof(float4));
+    add((void**)&t->s.src_cov, n * 2 * sizeof(float4));
+    add((void**)&t->s.knn_ids, n * KMAX * sizeof(u32));
+    add((void**)&t->s.i32_out, n * sizeof(int32_t));
+    add((void**)&t->s.f32_out, n * 6 * sizeof(float));
+    add((void**)&t->s.i64_out, n * sizeof(int64_t));
+    add((void**)&t->s.gn_partials, gn_partials_doubles(pl.max_n) * sizeof(double));
+    add((void**)&t->s.st, sizeof(RegState));
+    add((void**)&t->d_cov36, 36 * sizeof(double));
+    add((void**)&t->s.touched, (size_t)pl.cap * sizeof(u32));
+    add((void**)&t->s.foot, 2 * sizeof(unsigned long long));
+    return pl;
+}
+
+void release(far_map* m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    m->ev.clear();
+    for (void* p : m->allocs) cudaFree(p);
+    m->allocs.clear();
+    if (m->h_ctr) cudaFreeHost(m->h_ctr);
+    if (m->h_st) cudaFreeHost(m->h_st);
+    if (m->h_scal) cudaFreeHost(m->h_scal);
+    if (m->h_cov36) cudaFreeHost(m->h_cov36);
+    m->h_ctr = nullptr;
+    m->h_st = nullptr;
+    m->h_scal = nullptr;
+    m->h_cov36 = nullptr;
+}
+
+bool finite_pose(const double* T) {
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(T[i])) return false;
+    return true;
+}
+
+far_status check_points(const far_map* m, const float* xyz, uint64_t n, uint32_t stride) {
+    if (!m) return fail(FAR_ERR_INVALID, "map is NULL");
+    if (n > 0 && !xyz) return fail(FAR_ERR_INVALID, "xyz is NULL");
+    if (stride < 12 || stride % 4 != 0) return fail(FAR_ERR_INVALID, "stride_bytes must be >= 12 and a multiple of 4");
+    if (n > m->p.max_scan_points)
+        return fail(FAR_ERR_INVALID, "n = %llu exceeds max_scan_points = %u", (unsigned long long)n,
+                    m->p.max_scan_points);
+    return FAR_OK;
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// a1: bring the caller's points (host or device, AoS with stride) into s.in4.
+far_status ingest(far_map* m, const float* xyz, u32 n, u32 stride) {
+    if (n == 0) return FAR_OK;
+    const void* src = xyz;
+    u32 eff = stride;
+    if (!is_device_pointer(xyz)) {
+        if (stride <= 32) {
+            CK(cudaMemcpyAsync(m->s.staging, xyz, (size_t)n * stride, cudaMemcpyHostToDevice, m->stream));
+        } else {
+            CK(cudaMemcpy2DAsync(m->s.staging, 16, xyz, stride, 12, n, cudaMemcpyHostToDevice, m->stream));
+            eff = 16;
+        }
+        src = m->s.staging;
+    }
+    CK(pack_points(src, n, eff, m->s.in4, m->stream));
+    return FAR_OK;
+}
+
+far_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (!dst || bytes == 0) return FAR_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return FAR_OK;
+}
+
+far_status check_device_errors(far_map* m, const char* what) {
+    const u32 err = m->h_ctr->err;
+    if (!err) return FAR_OK;
+    CK(cudaMemsetAsync(&m->map.ctr->err, 0, sizeof(u32), m->stream));
+    CK(cudaMemsetAsync(&m->map.ctr->n_dropped, 0, sizeof(u32), m->stream));
+    return fail(FAR_ERR_CAPACITY, "%s: %s%s%s(%u points dropped)", what, (err & ERR_TABLE_FULL) ? "hash table full; " : "",
+                (err & ERR_BUCKETS_FULL) ? "bucket pool exhausted; " : "",
+                (err & ERR_ID_OVERFLOW) ? "point ids exhausted; " : "", m->h_ctr->n_dropped);
+}
+
+void mark(far_map* m, int e) {
+    if (!m->profiling) return;
+    cudaEventRecord(m->ev[e], m->stream);
+    if (e < EV_COUNT_FIXED) m->ev_used[e] = true;
+}
+
+void reset_marks(far_map* m) {
+    for (bool& u : m->ev_used) u = false;
+    m->gn_launched = 0;
+}
+
+float span_ms(far_map* m, int a, int b) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m->ev[a], m->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return t;
+}
+
+// Fill m->last from the recorded events (after the stream has been synchronised).
+void collect_times(far_map* m, u32 iters_done, u32 status) {
+    if (!m->profiling) return;
+    far_stage_times t{};
+    if (m->ev_used[EV_INGEST] && m->ev_used[EV_SOURCES]) t.ingest_ms = span_ms(m, EV_INGEST, EV_SOURCES);
+    if (m->ev_used[EV_SOURCES] && m->gn_launched) t.sources_ms = span_ms(m, EV_SOURCES, EV_GN0);
+    if (m->gn_launched) {
+        t.gauss_newton_ms = span_ms(m, EV_GN0, EV_GN0 + m->gn_launched);
+        u32 working = std::min(m->gn_launched, iters_done + (status != 0 ? 1u : 0u));
+        t.gn_launches = working;
+        if (working) t.gn_launch_ms = span_ms(m, EV_GN0, EV_GN0 + working) / working;
+    }
+    if (m->ev_used[EV_INSERT] && m->ev_used[EV_EVICT]) t.insert_ms = span_ms(m, EV_INSERT, EV_EVICT);
+    if (m->ev_used[EV_EVICT] && m->ev_used[EV_END]) t.evict_ms = span_ms(m, EV_EVICT, EV_END);
+    if (m->ev_used[EV_END]) {
+        const int first = m->ev_used[EV_INGEST] ? EV_INGEST : (m->gn_launched ? EV_GN0 : EV_INSERT);
+        t.total_ms = span_ms(m, first, EV_END);
+    }
+    m->last = t;
+}
+
+// Launch the Gauss-Newton chain (max_iters launches), marking each launch when profiling.
+far_status run_gn(far_map* m, const GnArgs& a, u32 n_upper, u32 iters) {
+    mark(m, EV_GN0);
+    for (u32 it = 0; it < iters; ++it) {
+        CK(gn_iteration(a, n_upper, m->stream));
+        mark(m, EV_GN0 + 1 + (int)it);
+    }
+    m->gn_launched = iters;
+    return FAR_OK;
+}
+
+Pose12 pose12(const double* T) {
+    Pose12 p;
+    for (int i = 0; i < 12; ++i) p.m[i] = T[i];
+    return p;
+}
+
+// Scan-local map + Eq. 1 source covariances (a2, a3) from s.in4[0..n).
+far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
+    CK(map_clear(m->local, m->stream));
+    InsertCfg cfg;
+    CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream));
+    CK(make_sources(m->local, m->s, n, knn_ids, m->stream));
+    return FAR_OK;
+}
+
+GnArgs gn_args(far_map* m, u32 n, float tau, float kappa, double conv_eps, int update, int32_t* corr,
+               double budget_s) {
+    GnArgs a;
+    a.map = m->map.view();
+    a.src = m->s.src;
+    a.src_cov = m->s.src_cov;
+    a.n_src = m->s.scal + SCAL_NADMIT;
+    a.n_max = n;
+    a.st = m->s.st;
+    a.partials = m->s.gn_partials;
+    a.tau2 = tau * tau;
+    a.kappa2 = kappa * kappa;
+    a.conv_eps = conv_eps;
+    a.update = update;
+    a.corr_out = corr;
+    a.budget_ns = budget_s > 0 ? (unsigned long long)(budget_s * 1e9) : 0ull;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* far_status_string(far_status s) {
+    switch (s) {
+        case FAR_OK: return "FAR_OK";
+        case FAR_ERR_INVALID: return "FAR_ERR_INVALID";
+        case FAR_ERR_OOM: return "FAR_ERR_OOM";
+        case FAR_ERR_CAPACITY: return "FAR_ERR_CAPACITY";
+        case FAR_ERR_CUDA: return "FAR_ERR_CUDA";
+        case FAR_ERR_DEGENERATE: return "FAR_ERR_DEGENERATE";
+        case FAR_ERR_TIMEOUT: return "FAR_ERR_TIMEOUT";
+    }
+    return "FAR_ERR_UNKNOWN";
+}
+
+const char* far_last_error(void) { return g_last_error.c_str(); }
+
+const char* far_version(void) { return "far-gb300 0.1 (sm_103a)"; }
+
+far_status far_map_bytes(const far_map_params* params, uint64_t* out_bytes) {
+    far_status st = validate_params(params);
+    if (st != FAR_OK) return st;
+    if (!out_bytes) return fail(FAR_ERR_INVALID, "out_bytes is NULL");
+    Plan pl = make_plan(*params, nullptr);
+    *out_bytes = pl.total;
+    return FAR_OK;
+}
+
+far_status far_map_create(const far_map_params* params, void* cuda_stream, far_map** out) {
+    far_status st = validate_params(params);
+    if (st != FAR_OK) return st;
+    if (!out) return fail(FAR_ERR_INVALID, "out is NULL");
+    int ndev = 0;
+    cudaError_t de = cudaGetDeviceCount(&ndev);
+    if (de != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(FAR_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(de));
+    }
+    far_map* m = new far_map();
+    m->p = *params;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    Plan pl = make_plan(*params, m);
+    for (auto& it : pl.items) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, it.second);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            release(m);
+            delete m;
+            return fail(FAR_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", it.second, cudaGetErrorString(e));
+        }
+        *it.first = p;
+        m->allocs.push_back(p);
+    }
+    if (cudaMallocHost((void**)&m->h_ctr, sizeof(MapCounters)) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_st, sizeof(RegState)) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_scal, SCAL_COUNT * sizeof(u32)) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_cov36, 36 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        release(m);
+        delete m;
+        return fail(FAR_ERR_OOM, "pinned host allocation failed");
+    }
+    const float v = params->voxel_size;
+    const u32 nmax = params->max_pts_per_voxel;
+    float dmin = params->min_spacing < 0.0f ? (float)((double)v / std::sqrt((double)nmax)) : params->min_spacing;
+    for (DeviceMap* d : {&m->map, &m->local}) {
+        d->nmax = nmax;
+        d->k = params->k_cov;
+        d->v = v;
+        d->inv_v = 1.0f / v;
+        d->dmin2 = dmin * dmin;
+    }
+    m->map.cap = pl.cap;
+    m->map.mask = pl.cap - 1;
+    m->map.key_bits = log2_u32(pl.cap) + 1;
+    m->map.max_buckets = pl.max_buckets;
+    m->local.cap = pl.local_cap;
+    m->local.mask = pl.local_cap - 1;
+    m->local.key_bits = log2_u32(pl.local_cap) + 1;
+    m->local.max_buckets = pl.local_buckets;
+    m->local.cov = nullptr;
+    m->local.slots_alt = nullptr;
+    m->s.max_n = pl.max_n;
+    m->s.staging_bytes = (size_t)pl.max_n * 32;
+    m->s.max_gn_blocks = gn_grid(pl.max_n);
+    cudaError_t e = map_clear(m->map, m->stream);
+    if (e == cudaSuccess) e = map_clear(m->local, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        release(m);
+        delete m;
+        return fail(FAR_ERR_CUDA, "map initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return FAR_OK;
+}
+
+far_status far_map_destroy(far_map* map) {
+    if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
+    release(map);
+    delete map;
+    return FAR_OK;
+}
+
+far_status far_map_clear(far_map* map) {
+    if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
+    CK(map_clear(map->map, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    return FAR_OK;
+}
+
+far_status far_map_insert(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, const double pose[16],
+                          const far_insert_params* params, uint64_t* n_inserted) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (!pose || !finite_pose(pose)) return fail(FAR_ERR_INVALID, "pose is NULL or not finite");
+    InsertCfg cfg;
+    if (params && params->asmd) {
+        if (!(params->r_max > 0.0) || !(params->r_near >= 0.0) || !std::isfinite(params->r_max))
+            return fail(FAR_ERR_INVALID, "ASMD needs r_near >= 0 and finite r_max > 0");
+        cfg.asmd = 1;
+        cfg.rc2 = params->r_near * params->r_near;
+        cfg.r_max = params->r_max;
+    }
+    cfg.sx = pose[3];
+    cfg.sy = pose[7];
+    cfg.sz = pose[11];
+    if ((st = ingest(map, xyz, (u32)n, stride_bytes)) != FAR_OK) return st;
+    Pose12 T = pose12(pose);
+    CK(map_insert_batch(map->map, map->s, (u32)n, &T, cfg, true, map->stream));
+    CK(cudaMemcpyAsync(map->h_ctr, map->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    if (n_inserted) *n_inserted = map->h_ctr->n_added;
+    return check_device_errors(map, "far_map_insert");
+}
+
+far_status far_map_evict(far_map* map, const double center[3], double radius, uint64_t* n_removed) {
+    if (!map || !center) return fail(FAR_ERR_INVALID, "map or center is NULL");
+    if (!(radius >= 0.0) || !std::isfinite(center[0]) || !std::isfinite(center[1]) || !std::isfinite(center[2]))
+        return fail(FAR_ERR_INVALID, "radius must be >= 0 and center finite");
+    CK(map_evict(map->map, center, radius, map->stream));
+    CK(cudaMemcpyAsync(map->h_ctr, map->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    if (n_removed) *n_removed = map->h_ctr->removed;
+    if (map->h_ctr->n_tomb > map->map.cap / 4) {
+        CK(map_rebuild(map->map, map->stream));
+        CK(cudaStreamSynchronize(map->stream));
+    }
+    return FAR_OK;
+}
+
+far_status far_map_size(const far_map* map, uint64_t* n_voxels, uint64_t* n_points) {
+    if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
+    CK(cudaMemcpyAsync(map->h_ctr, map->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    if (n_voxels) *n_voxels = map->h_ctr->n_voxels;
+    if (n_points) *n_points = map->h_ctr->n_points;
+    return FAR_OK;
+}
+
+far_status far_map_export(const far_map* cmap, int32_t* keys, uint32_t* counts, uint32_t* ids, float* xyz,
+                          float* cov, uint8_t* valid, uint64_t cap_voxels, uint64_t cap_points) {
+    far_map* map = const_cast<far_map*>(cmap);
+    if (!map || !keys || !counts) return fail(FAR_ERR_INVALID, "map, keys or counts is NULL");
+    uint64_t nv = 0, np = 0;
+    far_status st = far_map_size(map, &nv, &np);
+    if (st != FAR_OK) return st;
+    if (nv > cap_voxels || np > cap_points) return fail(FAR_ERR_INVALID, "export buffers too small");
+    if (nv == 0) return FAR_OK;
+    u64* d_keys = nullptr;
+    u32 *d_buckets = nullptr, *d_counts = nullptr, *d_n = nullptr, *d_off = nullptr;
+    float4 *d_pts = nullptr, *d_cov = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_keys); cudaFree(d_buckets); cudaFree(d_counts); cudaFree(d_n); cudaFree(d_off);
+        cudaFree(d_pts); cudaFree(d_cov);
+    };
+    if (cudaMalloc(&d_keys, nv * sizeof(u64)) != cudaSuccess || cudaMalloc(&d_buckets, nv * sizeof(u32)) != cudaSuccess ||
+        cudaMalloc(&d_counts, nv * sizeof(u32)) != cudaSuccess || cudaMalloc(&d_n, sizeof(u32)) != cudaSuccess ||
+        cudaMalloc(&d_off, nv * sizeof(u32)) != cudaSuccess ||
+        cudaMalloc(&d_pts, std::max<uint64_t>(np, 1) * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&d_cov, std::max<uint64_t>(np, 1) * 2 * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(FAR_ERR_OOM, "export scratch allocation failed");
+    }
+    std::vector<u64> hk(nv);
+    std::vector<u32> hb(nv), hc(nv);
+    u32 hn = 0;
+    cudaError_t e = map_list_slots(map->map, d_keys, d_buckets, d_counts, d_n, (u32)nv, map->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, d_n, sizeof(u32), cudaMemcpyDeviceToHost, map->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(map->stream);
+    if (e == cudaSuccess && hn > nv) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMemcpy(hk.data(), d_keys, hn * sizeof(u64), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hb.data(), d_buckets, hn * sizeof(u32), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hc.data(), d_counts, hn * sizeof(u32), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(FAR_ERR_CUDA, "export listing failed: %s", cudaGetErrorString(e));
+    }
+    auto unpack = [](u64 k, int32_t* o) {
+        o[0] = (int32_t)((k >> 42) & 0x1FFFFF) - (1 << 20);
+        o[1] = (int32_t)((k >> 21) & 0x1FFFFF) - (1 << 20);
+        o[2] = (int32_t)(k & 0x1FFFFF) - (1 << 20);
+    };
+    std::vector<u32> order(hn);
+    for (u32 i = 0; i < hn; ++i) order[i] = i;
+    std::vector<int32_t> kk(3 * (size_t)hn);
+    for (u32 i = 0; i < hn; ++i) unpack(hk[i], &kk[3 * (size_t)i]);
+    std::sort(order.begin(), order.end(), [&](u32 a, u32 b) {
+        const int32_t* x = &kk[3 * (size_t)a];
+        const int32_t* y = &kk[3 * (size_t)b];
+        if (x[0] != y[0]) return x[0] < y[0];
+        if (x[1] != y[1]) return x[1] < y[1];
+        return x[2] < y[2];
+    });
+    std::vector<u32> sb(hn), sc(hn), so(hn);
+    u32 total = 0;
+    for (u32 i = 0; i < hn; ++i) {
+        sb[i] = hb[order[i]];
+        sc[i] = hc[order[i]];
+        so[i] = total;
+        total += sc[i];
+        std::memcpy(keys + 3 * (size_t)i, &kk[3 * (size_t)order[i]], 3 * sizeof(int32_t));
+        counts[i] = sc[i];
+    }
+    if (total > np) {
+        cleanup();
+        return fail(FAR_ERR_CUDA, "export: listed %u points but the map counts %llu", total, (unsigned long long)np);
+    }
+    std::vector<float4> hp(total), hcv(2 * (size_t)total);
+    e = cudaMemcpy(d_buckets, sb.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_counts, sc.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_off, so.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = map_gather(map->map, d_buckets, d_counts, d_off, hn, d_pts, d_cov, map->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(map->stream);
+    if (e == cudaSuccess && total) e = cudaMemcpy(hp.data(), d_pts, total * sizeof(float4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && total)
+        e = cudaMemcpy(hcv.data(), d_cov, total * 2 * sizeof(float4), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return fail(FAR_ERR_CUDA, "export gather failed: %s", cudaGetErrorString(e));
+    for (u32 i = 0; i < total; ++i) {
+        const float4 p = hp[i];
+        u32 id;
+        std::memcpy(&id, &p.w, 4);
+        if (ids) ids[i] = id;
+        if (xyz) {
+            xyz[3 * (size_t)i] = p.x;
+            xyz[3 * (size_t)i + 1] = p.y;
+            xyz[3 * (size_t)i + 2] = p.z;
+        }
+        const float4 c0 = hcv[2 * (size_t)i], c1 = hcv[2 * (size_t)i + 1];
+        if (cov) {
+            float* o = cov + 6 * (size_t)i;
+            o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c0.w; o[4] = c1.x; o[5] = c1.y;
+        }
+        if (valid) valid[i] = c1.z > 0.5f ? 1 : 0;
+    }
+    return FAR_OK;
+}
+
+far_status far_map_nearest(far_map* map, const float* q, uint64_t n, uint32_t stride_bytes, float tau,
+                           int64_t* out_ids, float* out_d2) {
+    far_status st = check_points(map, q, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (n > 0 && !out_ids) return fail(FAR_ERR_INVALID, "out_ids is NULL");
+    if (n == 0) return FAR_OK;
+    if ((st = ingest(map, q, (u32)n, stride_bytes)) != FAR_OK) return st;
+    const float tau2 = tau * tau;
+    CK(map_nearest(map->map, map->s.in4, (u32)n, tau2, map->s.i64_out, map->s.f32_out, map->stream));
+    if ((st = copy_out(out_ids, map->s.i64_out, n * sizeof(int64_t), map->stream)) != FAR_OK) return st;
+    if ((st = copy_out(out_d2, map->s.f32_out, n * sizeof(float), map->stream)) != FAR_OK) return st;
+    CK(cudaStreamSynchronize(map->stream));
+    return FAR_OK;
+}
+
+far_status far_map_knn(far_map* map, const float* q, uint64_t n, uint32_t stride_bytes, uint32_t k,
+                       uint32_t* out_ids, int32_t* out_found) {
+    far_status st = check_points(map, q, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (k < 1 || k > (u32)KMAX) return fail(FAR_ERR_INVALID, "k must be in 1..%d", KMAX);
+    if (n > 0 && (!out_ids || !out_found)) return fail(FAR_ERR_INVALID, "outputs are NULL");
+    if (n == 0) return FAR_OK;
+    if ((st = ingest(map, q, (u32)n, stride_bytes)) != FAR_OK) return st;
+    CK(map_knn(map->map, map->s.in4, (u32)n, k, map->s.knn_ids, map->s.i32_out, map->stream));
+    if ((st = copy_out(out_ids, map->s.knn_ids, n * k * sizeof(u32), map->stream)) != FAR_OK) return st;
+    if ((st = copy_out(out_found, map->s.i32_out, n * sizeof(int32_t), map->stream)) != FAR_OK) return st;
+    CK(cudaStreamSynchronize(map->stream));
+    return FAR_OK;
+}
+
+}  // extern "C"
+
+namespace far {
+cudaError_t export_sources(const Scratch& s, u32 n, int64_t* index, float* cov6, uint8_t* valid, cudaStream_t st);
+}
+
+extern "C" {
+
+far_status far_scan_sources(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, int64_t* out_index,
+                            float* out_cov, uint8_t* out_valid, uint32_t* out_knn_ids, uint64_t* n_src) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (n == 0) {
+        if (n_src) *n_src = 0;
+        return FAR_OK;
+    }
+    if ((st = ingest(map, xyz, (u32)n, stride_bytes)) != FAR_OK) return st;
+    if ((st = build_sources(map, (u32)n, map->s.knn_ids)) != FAR_OK) return st;
+    uint8_t* vbuf = reinterpret_cast<uint8_t*>(map->s.i32_out);
+    CK(export_sources(map->s, (u32)n, map->s.i64_out, map->s.f32_out, vbuf, map->stream));
+    CK(cudaMemcpyAsync(map->h_scal, map->s.scal, SCAL_COUNT * sizeof(u32), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    const uint64_t m = map->h_scal[SCAL_NADMIT];
+    if ((st = copy_out(out_index, map->s.i64_out, m * sizeof(int64_t), map->stream)) != FAR_OK) return st;
+    if ((st = copy_out(out_cov, map->s.f32_out, m * 6 * sizeof(float), map->stream)) != FAR_OK) return st;
+    if ((st = copy_out(out_valid, vbuf, m, map->stream)) != FAR_OK) return st;
+    if ((st = copy_out(out_knn_ids, map->s.knn_ids, m * map->p.k_cov * sizeof(u32), map->stream)) != FAR_OK) return st;
+    CK(cudaStreamSynchronize(map->stream));
+    if (n_src) *n_src = m;
+    return FAR_OK;
+}
+
+far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, const double pose[16],
+                         float tau, float kappa, double out_H[36], double out_g[6], int32_t* out_corr,
+                         far_reg_stats* stats) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (!pose || !finite_pose(pose) || !out_H || !out_g) return fail(FAR_ERR_INVALID, "pose/H/g invalid");
+    if (!(kappa > 0.0f) || !(tau >= 0.0f)) return fail(FAR_ERR_INVALID, "kappa must be > 0 and tau >= 0");
+    const u32 nn = (u32)n;
+    if ((st = ingest(map, xyz, nn, stride_bytes)) != FAR_OK) return st;
+    if (nn) {
+        if ((st = build_sources(map, nn, nullptr)) != FAR_OK) return st;
+    } else {
+        CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
+    }
+    CK(gn_begin(map->s.st, pose, map->s.scal + SCAL_NADMIT, map->stream));
+    GnArgs a = gn_args(map, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0);
+    CK(gn_iteration(a, std::max(nn, 1u), map->stream));
+    CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaMemcpyAsync(map->h_scal, map->s.scal, SCAL_COUNT * sizeof(u32), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    const uint64_t m = map->h_st->n_src;
+    if ((st = copy_out(out_corr, map->s.i32_out, m * sizeof(int32_t), map->stream)) != FAR_OK) return st;
+    CK(cudaStreamSynchronize(map->stream));
+    std::memcpy(out_H, map->h_st->H, 36 * sizeof(double));
+    std::memcpy(out_g, map->h_st->g, 6 * sizeof(double));
+    if (stats) {
+        stats->iters = 0;
+        stats->n_src = (uint32_t)m;
+        stats->n_corr = map->h_st->n_corr;
+        stats->n_p2p = map->h_st->n_p2p;
+        stats->converged = 0;
+        stats->status = FAR_OK;
+        stats->chi2 = map->h_st->chi2;
+    }
+    return FAR_OK;
+}
+
+far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                             const double init_pose[16], const far_reg_params* params, double out_pose[16],
+                             double out_cov[36], far_reg_stats* stats) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (!params || !init_pose || !finite_pose(init_pose) || !out_pose)
+        return fail(FAR_ERR_INVALID, "params, init_pose or out_pose invalid");
+    if (!(params->kappa > 0.0f) || !(params->tau >= 0.0f) || params->max_iters > 1000)
+        return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000");
+    const u32 nn = (u32)n;
+    reset_marks(map);
+    mark(map, EV_INGEST);
+    if ((st = ingest(map, xyz, nn, stride_bytes)) != FAR_OK) return st;
+    mark(map, EV_SOURCES);
+    if (nn) {
+        if ((st = build_sources(map, nn, nullptr)) != FAR_OK) return st;
+    } else {
+        CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
+    }
+    CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
+    GnArgs a = gn_args(map, std::max(nn, 1u), params->tau, params->kappa, params->conv_eps, 1, nullptr,
+                       params->time_budget_s);
+    if ((st = run_gn(map, a, std::max(nn, 1u), params->max_iters)) != FAR_OK) return st;
+    mark(map, EV_END);
+    if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
+    CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaMemcpyAsync(map->h_scal, map->s.scal, SCAL_COUNT * sizeof(u32), cudaMemcpyDeviceToHost, map->stream));
+    if (out_cov) CK(cudaMemcpyAsync(map->h_cov36, map->d_cov36, 36 * sizeof(double), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    const RegState& r = *map->h_st;
+    collect_times(map, r.iters, r.status);
+    std::memcpy(out_pose, r.T, 16 * sizeof(double));
+    if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));
+    far_status result = FAR_OK;
+    if (r.status == 5) result = fail(FAR_ERR_DEGENERATE, "registration degenerate (%u correspondences)", r.n_corr);
+    if (r.status == 6) result = fail(FAR_ERR_TIMEOUT, "registration exceeded its time budget after %u iterations", r.iters);
+    if (stats) {
+        stats->iters = r.iters;
+        stats->n_src = r.n_src;
+        stats->n_corr = r.n_corr;
+        stats->n_p2p = r.n_p2p;
+        stats->converged = (int32_t)r.converged;
+        stats->status = result;
+        stats->chi2 = r.chi2;
+    }
+    return result;
+}
+
+far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                            const double init_pose[16], const far_reg_params* reg, const far_insert_params* ins,
+                            double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (!reg || !init_pose || !finite_pose(init_pose) || !out_pose)
+        return fail(FAR_ERR_INVALID, "reg params, init_pose or out_pose invalid");
+    if (!(reg->kappa > 0.0f) || !(reg->tau >= 0.0f) || reg->max_iters > 1000)
+        return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000");
+    if (!(evict_radius >= 0.0) || std::isnan(evict_radius)) return fail(FAR_ERR_INVALID, "evict_radius must be >= 0");
+    InsertCfg cfg;
+    if (ins && ins->asmd) {
+        if (!(ins->r_max > 0.0) || !(ins->r_near >= 0.0) || !std::isfinite(ins->r_max))
+            return fail(FAR_ERR_INVALID, "ASMD needs r_near >= 0 and finite r_max > 0");
+        cfg.asmd = 1;
+        cfg.rc2 = ins->r_near * ins->r_near;
+        cfg.r_max = ins->r_max;
+    }
+    const u32 nn = (u32)n;
+    reset_marks(map);
+    mark(map, EV_INGEST);
+    if ((st = ingest(map, xyz, nn, stride_bytes)) != FAR_OK) return st;
+    mark(map, EV_SOURCES);
+    if (nn) {
+        if ((st = build_sources(map, nn, nullptr)) != FAR_OK) return st;
+    } else {
+        CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
+    }
+    CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
+    GnArgs a = gn_args(map, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr, reg->time_budget_s);
+    if ((st = run_gn(map, a, std::max(nn, 1u), reg->max_iters)) != FAR_OK) return st;
+    if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
+    mark(map, EV_INSERT);
+    // Sec. III-A.3 submap update at the registered pose, read from the device (skipped unless status == 0)
+    DevicePose dp;
+    dp.T = map->s.st->T;
+    dp.status = &map->s.st->status;
+    CK(map_insert_batch(map->map, map->s, nn, nullptr, cfg, true, map->stream, dp));
+    mark(map, EV_EVICT);
+    if (evict_radius > 0.0 && std::isfinite(evict_radius))
+        CK(map_evict(map->map, nullptr, evict_radius, map->stream, map->s.st->T));
+    else
+        CK(cudaMemsetAsync(&map->map.ctr->removed, 0, sizeof(unsigned long long), map->stream));
+    mark(map, EV_END);
+    CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaMemcpyAsync(map->h_ctr, map->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, map->stream));
+    if (out_cov) CK(cudaMemcpyAsync(map->h_cov36, map->d_cov36, 36 * sizeof(double), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    if (map->h_ctr->n_tomb > map->map.cap / 4) {
+        CK(map_rebuild(map->map, map->stream));
+        CK(cudaStreamSynchronize(map->stream));
+    }
+    const RegState& r = *map->h_st;
+    collect_times(map, r.iters, r.status);
+    std::memcpy(out_pose, r.T, 16 * sizeof(double));
+    if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));
+    far_status res = FAR_OK;
+    if (r.status == 5) res = fail(FAR_ERR_DEGENERATE, "registration degenerate (%u correspondences); scan not inserted",
+                                  r.n_corr);
+    if (r.status == 6) res = fail(FAR_ERR_TIMEOUT, "registration exceeded its time budget; scan not inserted");
+    if (result) {
+        result->reg.iters = r.iters;
+        result->reg.n_src = r.n_src;
+        result->reg.n_corr = r.n_corr;
+        result->reg.n_p2p = r.n_p2p;
+        result->reg.converged = (int32_t)r.converged;
+        result->reg.status = res;
+        result->reg.chi2 = r.chi2;
+        result->n_inserted = map->h_ctr->n_added;
+        result->n_removed = map->h_ctr->removed;
+        result->n_voxels = map->h_ctr->n_voxels;
+        result->n_points = map->h_ctr->n_points;
+    }
+    if (res == FAR_OK) return check_device_errors(map, "far_process_scan");
+    return res;
+}
+
+unsigned long long far_launch_count(void) { return g_launches.load(); }
+
+far_status far_set_profiling(far_map* map, int enable) {
+    if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
+    if (enable && map->ev.empty()) {
+        map->ev.resize(EV_COUNT_FIXED + MAX_ITERS + 1, nullptr);
+        for (cudaEvent_t& e : map->ev) CK(cudaEventCreate(&e));
+    }
+    map->profiling = enable != 0;
+    return FAR_OK;
+}
+
+far_status far_get_stage_times(const far_map* map, far_stage_times* out) {
+    if (!map || !out) return fail(FAR_ERR_INVALID, "NULL argument");
+    if (!map->profiling) return fail(FAR_ERR_INVALID, "profiling is off (far_set_profiling)");
+    *out = map->last;
+    return FAR_OK;
+}
+
+far_status far_gn_footprint(far_map* map, uint64_t out[3]) {
+    if (!map || !out) return fail(FAR_ERR_INVALID, "NULL argument");
+    CK(gn_footprint(map->map.view(), map->s.src, map->s.st, map->s.touched, map->map.cap, map->s.foot,
+                    map->p.max_scan_points, map->stream));
+    unsigned long long f[2];
+    CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaMemcpyAsync(f, map->s.foot, sizeof(f), cudaMemcpyDeviceToHost, map->stream));
+    CK(cudaStreamSynchronize(map->stream));
+    out[0] = map->h_st->n_src;
+    out[1] = f[0];
+    out[2] = f[1];
+    return FAR_OK;
+}
+
+// ---- adaptive threshold (host) ----
+far_status far_threshold_init(far_threshold* t, double sigma0, double min_motion, double r_max) {
+    if (!t || !(sigma0 > 0) || !(r_max > 0) || !(min_motion >= 0)) return fail(FAR_ERR_INVALID, "bad threshold params");
+    t->sigma0 = sigma0;
+    t->min_motion = min_motion;
+    t->r_max = r_max;
+    t->sse = 0.0;
+    t->n = 0;
+    return FAR_OK;
+}
+
+far_status far_threshold_get(const far_threshold* t, double* tau, double* kappa) {
+    if (!t || !tau || !kappa) return fail(FAR_ERR_INVALID, "NULL argument");
+    const double sigma = t->n > 0 ? std::sqrt(t->sse / (double)t->n) : t->sigma0;
+    *tau = 3.0 * sigma;
+    *kappa = sigma / 3.0;
+    return FAR_OK;
+}
+
+far_status far_threshold_update(far_threshold* t, const double a[16], const double b[16]) {
+    if (!t || !a || !b) return fail(FAR_ERR_INVALID, "NULL argument");
+    // D = a^-1 b for rigid a: R_D = R_a^T R_b, t_D = R_a^T (t_b - t_a)
+    double RD[3][3], tD[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int l = 0; l < 3; ++l) s += a[4 * l + i] * b[4 * l + j];
+            RD[i][j] = s;
+        }
+        double s = 0;
+        for (int l = 0; l < 3; ++l) s += a[4 * l + i] * (b[4 * l + 3] - a[4 * l + 3]);
+        tD[i] = s;
+    }
+    const double c = std::max(-1.0, std::min(1.0, 0.5 * (RD[0][0] + RD[1][1] + RD[2][2] - 1.0)));
+    const double theta = std::acos(c);
+    const double dt = std::sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
+    const double delta = 2.0 * t->r_max * std::sin(0.5 * theta) + dt;
+    if (dt > t->min_motion) {
+        t->sse += delta * delta;
+        t->n += 1;
+    }
+    return FAR_OK;
+}
+
+}  // extern "C"

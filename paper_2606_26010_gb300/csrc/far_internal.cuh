@@ -1,0 +1,161 @@
+// Internal device structures and helpers of the FAR registration library (sm_103a).
+//
+// Voxel map layout in HBM (cuVoxelMap analogue, FAR-LIO Sec. III-A.2):
+//   slots[cap]    16 B open-addressing slots {u64 key, u32 bucket, u32 count};
+//                 eight slots per 128 B line, linear probing with step 1, so a
+//                 lookup normally touches one line. Keys pack the 3 voxel
+//                 indices (21 bits each).
+//   pts[B * N]    float4 {x, y, z, id bits} per point, N = max points per voxel,
+//                 bucket b occupies pts[b * N, b * N + N).
+//   cov[2 B N]    two float4 per point {c00 c01 c02 c11} {c12 c22 valid 0}.
+//   ring[B]       free-bucket ring (allocation at head, eviction returns at tail).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace far {
+
+// Host-side count of kernel launches issued by the library (all maps, all threads).
+void note_launch();
+// Launch a kernel and count it.
+#define FAR_LAUNCH(kernel, grid, block, smem, stream, ...)              \
+    do {                                                                \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);     \
+        ::far::note_launch();                                           \
+    } while (0)
+
+typedef unsigned long long u64;
+typedef uint32_t u32;
+
+constexpr u64 KEY_EMPTY = ~0ull;          // memset(0xFF) state of a slot
+constexpr u64 KEY_TOMB = ~0ull - 1ull;    // evicted voxel
+constexpr u64 KEY_INVALID = ~0ull - 2ull; // point without a key (never stored)
+constexpr u32 NO_BUCKET = 0xFFFFFFFFu;
+constexpr u32 NO_ID = 0xFFFFFFFFu;
+constexpr int KEY_BIAS = 1 << 20;         // keys lie in [-2^20, 2^20)
+constexpr float KEY_LIMIT = 1048576.0f;
+constexpr int KMAX = 16;                  // largest k of the kNN kernels
+constexpr int NMAX_LIMIT = 64;            // largest N_max
+
+enum ErrFlag : u32 {
+    ERR_TABLE_FULL = 1u,
+    ERR_BUCKETS_FULL = 2u,
+    ERR_ID_OVERFLOW = 4u,
+    ERR_TIMEOUT = 8u,
+};
+
+struct __align__(16) Slot {
+    u64 key;
+    u32 bucket;
+    u32 count;
+};
+
+// Device-resident counters of one map.
+struct MapCounters {
+    u32 ring_head;       // next free-ring position to allocate from
+    u32 ring_tail;       // next free-ring position to return to
+    u32 n_voxels;        // live voxels (slots holding a key)
+    u32 n_tomb;          // tombstones
+    u32 next_id;         // next point id
+    u32 max_probe;       // longest probe distance of any stored key
+    u32 err;             // ErrFlag bits
+    u32 n_dropped;       // points dropped by capacity errors
+    unsigned long long n_points;      // live points
+    unsigned long long removed;       // points removed by the last eviction
+    unsigned long long near_sum;      // ASMD: sum of near-voxel candidate counts
+    unsigned long long near_cnt;      // ASMD: number of near voxels
+    u32 n_added;         // points admitted by the last insert
+    u32 pad[3];
+};
+
+// Read-only view of a map handed to search kernels.
+struct MapView {
+    const Slot* slots;
+    const float4* pts;
+    const float4* cov;   // may be null (scan-local map)
+    const MapCounters* ctr;
+    u32 mask;
+    u32 nmax;
+    float inv_v;
+};
+
+// Registration state kept on the device between Gauss-Newton launches.
+struct RegState {
+    double T[16];        // current pose
+    double H[36];        // last linearisation
+    double g[6];
+    double xi[6];
+    double chi2;
+    double xi_norm;
+    u32 n_corr, n_p2p;
+    u32 iters;           // updates applied
+    u32 converged;
+    u32 status;          // 0 ok, 5 degenerate
+    u32 done;            // stop flag read at kernel entry
+    u32 block_counter;   // last-block detection
+    u32 n_src;           // source points of this registration
+    unsigned long long t_start_ns;  // %globaltimer at the start of the registration
+};
+
+// ----------------------------------------------------------------------------- keys
+__device__ __forceinline__ bool voxel_key3(float x, float y, float z, float inv_v, int& kx, int& ky, int& kz) {
+    // Key reading: floor(x * fp32(1/v)) with one FP32 rounding of the product.
+    float sx = __fmul_rn(x, inv_v), sy = __fmul_rn(y, inv_v), sz = __fmul_rn(z, inv_v);
+    if (!(sx >= -KEY_LIMIT && sx < KEY_LIMIT && sy >= -KEY_LIMIT && sy < KEY_LIMIT && sz >= -KEY_LIMIT &&
+          sz < KEY_LIMIT))
+        return false;
+    kx = (int)floorf(sx);
+    ky = (int)floorf(sy);
+    kz = (int)floorf(sz);
+    return true;
+}
+
+__device__ __forceinline__ bool key_in_range(int k) { return k >= -KEY_BIAS && k < KEY_BIAS; }
+
+__device__ __forceinline__ u64 pack_key(int kx, int ky, int kz) {
+    return ((u64)(u32)(kx + KEY_BIAS) << 42) | ((u64)(u32)(ky + KEY_BIAS) << 21) | (u64)(u32)(kz + KEY_BIAS);
+}
+
+__device__ __forceinline__ void unpack_key(u64 k, int& kx, int& ky, int& kz) {
+    kx = (int)((k >> 42) & 0x1FFFFF) - KEY_BIAS;
+    ky = (int)((k >> 21) & 0x1FFFFF) - KEY_BIAS;
+    kz = (int)(k & 0x1FFFFF) - KEY_BIAS;
+}
+
+// Spatial hash of Teschner/Niessner (primes 73856093, 19349669, 83492791) on the voxel indices.
+__device__ __forceinline__ u32 hash_key(int kx, int ky, int kz) {
+    return ((u32)kx * 73856093u) ^ ((u32)ky * 19349669u) ^ ((u32)kz * 83492791u);
+}
+
+// Candidate distance reading: ((dx*dx + dy*dy) + dz*dz), FP32 round-to-nearest, no contraction.
+__device__ __forceinline__ float dist2_rn(float ax, float ay, float az, float bx, float by, float bz) {
+    float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Find the slot of a key; returns its contents in `out` (bucket/count) or false.
+__device__ __forceinline__ bool find_slot(const Slot* __restrict__ slots, u32 mask, u32 max_probe, int kx, int ky,
+                                          int kz, u32& bucket, u32& count) {
+    const u64 key = pack_key(kx, ky, kz);
+    u32 h = hash_key(kx, ky, kz) & mask;
+    for (u32 p = 0; p <= max_probe; ++p) {
+        uint4 raw = __ldg(reinterpret_cast<const uint4*>(slots + h));
+        u64 k = ((u64)raw.y << 32) | raw.x;
+        if (k == key) {
+            bucket = raw.z;
+            count = raw.w;
+            return raw.z != NO_BUCKET;
+        }
+        if (k == KEY_EMPTY) return false;
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+// (d2, id) lexicographic "better than"
+__device__ __forceinline__ bool better(float d2, u32 id, float bd2, u32 bid) {
+    return d2 < bd2 || (d2 == bd2 && id < bid);
+}
+
+}  // namespace far

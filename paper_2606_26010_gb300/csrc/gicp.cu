@@ -1,0 +1,418 @@
+// Sparsity-aware GICP Gauss-Newton iteration (FAR-LIO Sec. III-A.2, Eq. 2-6).
+//
+// One launch = one iteration, fully on the device:
+//   per source point (one thread): q = R s + t (FP32), 1-NN over the 27 voxels,
+//   rejection by tau, M = (Sigma_r + R Sigma_s R^T)^-1 or I (SA GICP),
+//   d = r - q, Cauchy IRLS weight w = 1 / (1 + e^2/kappa^2), e^2 = d^T M d,
+//   accumulate w J^T M J (21 values) and w J^T M d (6) with J = [[q]x, -I];
+//   FP32 per thread and per warp (shuffles), FP64 across warps and blocks;
+//   the last block to finish reduces the block partials in a fixed order,
+//   solves H xi = -g by FP64 Cholesky and applies T <- exp(xi) T (Eq. 6).
+// The iteration checks a stop flag at entry, so a fixed-size chain of launches
+// (or a CUDA graph of them) stops doing work once converged.
+#include "gicp.cuh"
+#include "search.cuh"
+
+namespace far {
+
+namespace {
+
+constexpr int GN_THREADS = 256;
+constexpr int NACC = 28;   // 21 H + 6 g + chi2
+constexpr int NPART = 32;  // doubles per block partial: 28 + n_corr + n_p2p + pad
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- FP64 6x6 Cholesky solve and SE(3) exponential (single thread) ----
+__device__ bool chol6_solve(const double* H, const double* b, double* x) {
+    double L[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) L[i][j] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        double s = H[6 * j + j];
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0)) return false;
+        const double d = sqrt(s);
+        L[j][j] = d;
+        for (int i = j + 1; i < 6; ++i) {
+            double t = H[6 * i + j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / d;
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+__device__ void se3_exp_dev(const double* xi, double* E) {
+    const double px = xi[0], py = xi[1], pz = xi[2];
+    const double th2 = px * px + py * py + pz * pz;
+    const double th = sqrt(th2);
+    double A, B, C;
+    if (th < 1e-8) {
+        A = 1.0 - th2 / 6.0;
+        B = 0.5 - th2 / 24.0;
+        C = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        double s, c;
+        sincos(th, &s, &c);
+        A = s / th;
+        B = (1.0 - c) / th2;
+        C = (th - s) / (th2 * th);
+    }
+    const double K[3][3] = {{0, -pz, py}, {pz, 0, -px}, {-py, px, 0}};
+    double K2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K2[i][j] = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
+    for (int i = 0; i < 3; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            const double id = (i == j) ? 1.0 : 0.0;
+            E[4 * i + j] = id + A * K[i][j] + B * K2[i][j];
+            t += (id + B * K[i][j] + C * K2[i][j]) * xi[3 + j];
+        }
+        E[4 * i + 3] = t;
+    }
+    E[12] = E[13] = E[14] = 0.0;
+    E[15] = 1.0;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ u32 warp_sum_u(u32 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(GN_THREADS) k_gn_iter(GnArgs a) {
+    __shared__ float red[GN_THREADS / 32][NACC + 2];
+    __shared__ double tot[NPART];
+    __shared__ float pose_f[12];
+    __shared__ u32 s_flag;
+    RegState* st = a.st;
+    if (threadIdx.x == 0) s_flag = *reinterpret_cast<volatile u32*>(&st->done);
+    if (threadIdx.x < 12) pose_f[threadIdx.x] = (float)st->T[threadIdx.x];
+    __syncthreads();
+    if (s_flag) return;
+
+    const float R00 = pose_f[0], R01 = pose_f[1], R02 = pose_f[2], tx = pose_f[3];
+    const float R10 = pose_f[4], R11 = pose_f[5], R12 = pose_f[6], ty = pose_f[7];
+    const float R20 = pose_f[8], R21 = pose_f[9], R22 = pose_f[10], tz = pose_f[11];
+    const MapView m = a.map;
+    const u32 max_probe = m.ctr->max_probe;
+    const u32 n = min(a.n_max, *a.n_src);
+
+    float acc[NACC];
+#pragma unroll
+    for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
+    u32 n_corr = 0, n_p2p = 0;
+
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 s = a.src[i];
+        // Eq. 2 / Eq. 6: current estimate applied to the source point
+        const float qx = fmaf(R00, s.x, fmaf(R01, s.y, fmaf(R02, s.z, tx)));
+        const float qy = fmaf(R10, s.x, fmaf(R11, s.y, fmaf(R12, s.z, ty)));
+        const float qz = fmaf(R20, s.x, fmaf(R21, s.y, fmaf(R22, s.z, tz)));
+        float bd2;
+        u32 bid, bpos;
+        const bool any = nearest27(m, max_probe, qx, qy, qz, bd2, bid, bpos);
+        const bool ok = any && !(bd2 > a.tau2);
+        if (a.corr_out) a.corr_out[i] = ok ? (int32_t)bid : -1;
+        if (!ok) continue;
+        const float4 r = __ldg(m.pts + bpos);
+        const float4 rc0 = __ldg(m.cov + 2 * (size_t)bpos);
+        const float4 rc1 = __ldg(m.cov + 2 * (size_t)bpos + 1);
+        const float4 sc0 = a.src_cov[2 * (size_t)i];
+        const float4 sc1 = a.src_cov[2 * (size_t)i + 1];
+        // M: (Sigma_r + R Sigma_s R^T)^-1, or I when a covariance is invalid (SA GICP)
+        float M00 = 1.f, M01 = 0.f, M02 = 0.f, M11 = 1.f, M12 = 0.f, M22 = 1.f;
+        const bool p2p = !(rc1.z > 0.5f && sc1.z > 0.5f);
+        if (!p2p) {
+            const float S00 = sc0.x, S01 = sc0.y, S02 = sc0.z, S11 = sc0.w, S12 = sc1.x, S22 = sc1.y;
+            // A = R S
+            const float A00 = R00 * S00 + R01 * S01 + R02 * S02, A01 = R00 * S01 + R01 * S11 + R02 * S12,
+                        A02 = R00 * S02 + R01 * S12 + R02 * S22;
+            const float A10 = R10 * S00 + R11 * S01 + R12 * S02, A11 = R10 * S01 + R11 * S11 + R12 * S12,
+                        A12 = R10 * S02 + R11 * S12 + R12 * S22;
+            const float A20 = R20 * S00 + R21 * S01 + R22 * S02, A21 = R20 * S01 + R21 * S11 + R22 * S12,
+                        A22 = R20 * S02 + R21 * S12 + R22 * S22;
+            // C = Sigma_r + A R^T (symmetric)
+            const float a_ = rc0.x + A00 * R00 + A01 * R01 + A02 * R02;
+            const float b_ = rc0.y + A00 * R10 + A01 * R11 + A02 * R12;
+            const float c_ = rc0.z + A00 * R20 + A01 * R21 + A02 * R22;
+            const float d_ = rc0.w + A10 * R10 + A11 * R11 + A12 * R12;
+            const float e_ = rc1.x + A10 * R20 + A11 * R21 + A12 * R22;
+            const float f_ = rc1.y + A20 * R20 + A21 * R21 + A22 * R22;
+            const float C00 = d_ * f_ - e_ * e_, C01 = c_ * e_ - b_ * f_, C02 = b_ * e_ - c_ * d_;
+            const float C11 = a_ * f_ - c_ * c_, C12 = b_ * c_ - a_ * e_, C22 = a_ * d_ - b_ * b_;
+            const float idet = 1.0f / (a_ * C00 + b_ * C01 + c_ * C02);
+            M00 = C00 * idet; M01 = C01 * idet; M02 = C02 * idet;
+            M11 = C11 * idet; M12 = C12 * idet; M22 = C22 * idet;
+        }
+        // Eq. 3 residual and Eq. 4/5 weight
+        const float dx = r.x - qx, dy = r.y - qy, dz = r.z - qz;
+        const float Mdx = M00 * dx + M01 * dy + M02 * dz;
+        const float Mdy = M01 * dx + M11 * dy + M12 * dz;
+        const float Mdz = M02 * dx + M12 * dy + M22 * dz;
+        const float e2 = dx * Mdx + dy * Mdy + dz * Mdz;
+        const float w = a.kappa2 / (a.kappa2 + e2);
+        // MQ = M [q]x
+        const float MQ00 = M01 * qz - M02 * qy, MQ01 = M02 * qx - M00 * qz, MQ02 = M00 * qy - M01 * qx;
+        const float MQ10 = M11 * qz - M12 * qy, MQ11 = M12 * qx - M01 * qz, MQ12 = M01 * qy - M11 * qx;
+        const float MQ20 = M12 * qz - M22 * qy, MQ21 = M22 * qx - M02 * qz, MQ22 = M02 * qy - M12 * qx;
+        // [q]x^T MQ: row a of [q]x^T is column a of [q]x
+        // [q]x = [[0,-qz,qy],[qz,0,-qx],[-qy,qx,0]]
+        const float T00 = qz * MQ10 - qy * MQ20, T01 = qz * MQ11 - qy * MQ21, T02 = qz * MQ12 - qy * MQ22;
+        const float T11 = -qz * MQ01 + qx * MQ21, T12 = -qz * MQ02 + qx * MQ22;
+        const float T22 = qy * MQ02 - qx * MQ12;
+        float* h = acc;
+        // row 0..2 rotational block, cross block -MQ^T, translational block M
+        h[0] = fmaf(w, T00, h[0]);   h[1] = fmaf(w, T01, h[1]);   h[2] = fmaf(w, T02, h[2]);
+        h[3] = fmaf(w, -MQ00, h[3]); h[4] = fmaf(w, -MQ10, h[4]); h[5] = fmaf(w, -MQ20, h[5]);
+        h[6] = fmaf(w, T11, h[6]);   h[7] = fmaf(w, T12, h[7]);
+        h[8] = fmaf(w, -MQ01, h[8]); h[9] = fmaf(w, -MQ11, h[9]); h[10] = fmaf(w, -MQ21, h[10]);
+        h[11] = fmaf(w, T22, h[11]);
+        h[12] = fmaf(w, -MQ02, h[12]); h[13] = fmaf(w, -MQ12, h[13]); h[14] = fmaf(w, -MQ22, h[14]);
+        h[15] = fmaf(w, M00, h[15]); h[16] = fmaf(w, M01, h[16]); h[17] = fmaf(w, M02, h[17]);
+        h[18] = fmaf(w, M11, h[18]); h[19] = fmaf(w, M12, h[19]);
+        h[20] = fmaf(w, M22, h[20]);
+        // g = w [Md x q; -Md]
+        h[21] = fmaf(w, Mdy * qz - Mdz * qy, h[21]);
+        h[22] = fmaf(w, Mdz * qx - Mdx * qz, h[22]);
+        h[23] = fmaf(w, Mdx * qy - Mdy * qx, h[23]);
+        h[24] = fmaf(w, -Mdx, h[24]);
+        h[25] = fmaf(w, -Mdy, h[25]);
+        h[26] = fmaf(w, -Mdz, h[26]);
+        h[27] += 0.5f * a.kappa2 * log1pf(e2 / a.kappa2);
+        ++n_corr;
+        if (p2p) ++n_p2p;
+    }
+
+    // ---- reduction: FP32 within the warp, FP64 across warps and blocks ----
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NACC; ++j) {
+        const float v = warp_sum(acc[j]);
+        if (lane == 0) red[warp][j] = v;
+    }
+    n_corr = warp_sum_u(n_corr);
+    n_p2p = warp_sum_u(n_p2p);
+    if (lane == 0) {
+        red[warp][NACC] = __uint_as_float(n_corr);
+        red[warp][NACC + 1] = __uint_as_float(n_p2p);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        double s = 0.0;
+        if (threadIdx.x < NACC) {
+            for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
+        } else if (threadIdx.x < NACC + 2) {
+            for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)__float_as_uint(red[w][threadIdx.x]);
+        }
+        a.partials[(size_t)blockIdx.x * NPART + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const u32 ticket = atomicAdd(&st->block_counter, 1u);
+        s_flag = (ticket == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_flag) return;
+
+    // ---- last block: fixed-order FP64 reduction of the block partials ----
+    __threadfence();
+    {
+        const int v = threadIdx.x >> 3, j = threadIdx.x & 7;  // 32 values x 8 lanes
+        double s = 0.0;
+        for (u32 b = j; b < gridDim.x; b += 8) s += __ldcg(a.partials + (size_t)b * NPART + v);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (j == 0) tot[v] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+
+    st->block_counter = 0;
+    double H[36], g[6];
+    {
+        int idx = 0;
+        for (int r = 0; r < 6; ++r)
+            for (int c = r; c < 6; ++c) {
+                H[6 * r + c] = tot[idx];
+                H[6 * c + r] = tot[idx];
+                ++idx;
+            }
+        for (int r = 0; r < 6; ++r) g[r] = tot[21 + r];
+    }
+    for (int j = 0; j < 36; ++j) st->H[j] = H[j];
+    for (int j = 0; j < 6; ++j) st->g[j] = g[j];
+    st->chi2 = tot[27];
+    st->n_corr = (u32)tot[28];
+    st->n_p2p = (u32)tot[29];
+    if (!a.update) {
+        st->done = 1;
+        return;
+    }
+    if (st->n_corr < 6) {
+        st->status = 5;
+        st->done = 1;
+        return;
+    }
+    double mg[6], xi[6];
+    for (int j = 0; j < 6; ++j) mg[j] = -g[j];
+    if (!chol6_solve(H, mg, xi)) {
+        st->status = 5;
+        st->done = 1;
+        return;
+    }
+    double E[16], T[16], Tn[16];
+    se3_exp_dev(xi, E);
+    for (int j = 0; j < 16; ++j) T[j] = st->T[j];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c)
+            Tn[4 * r + c] = E[4 * r + 0] * T[0 + c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c] +
+                            E[4 * r + 3] * T[12 + c];
+    for (int j = 0; j < 16; ++j) st->T[j] = Tn[j];
+    double nx = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        st->xi[j] = xi[j];
+        nx += xi[j] * xi[j];
+    }
+    st->xi_norm = sqrt(nx);
+    st->iters += 1;
+    if (st->xi_norm <= a.conv_eps) {
+        st->converged = 1;
+        st->done = 1;
+    }
+    if (a.budget_ns > 0 && globaltimer_ns() - st->t_start_ns > a.budget_ns) {
+        st->status = 6;
+        st->done = 1;
+    }
+}
+
+__global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
+    st->n_src = n_src ? *n_src : 0u;
+    for (int j = 0; j < 16; ++j) st->T[j] = init.m[j];
+    for (int j = 0; j < 36; ++j) st->H[j] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        st->g[j] = 0.0;
+        st->xi[j] = 0.0;
+    }
+    st->chi2 = 0.0;
+    st->xi_norm = 0.0;
+    st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
+    st->block_counter = 0;
+    st->t_start_ns = globaltimer_ns();
+}
+
+// Output covariance: H^-1 of the last linearisation (FP64, single thread).
+__global__ void k_gn_cov(RegState* st, double* cov) {
+    double e[6], x[6];
+    for (int c = 0; c < 6; ++c) {
+        for (int r = 0; r < 6; ++r) e[r] = (r == c) ? 1.0 : 0.0;
+        if (!chol6_solve(st->H, e, x)) {
+            for (int j = 0; j < 36; ++j) cov[j] = 0.0;
+            return;
+        }
+        for (int r = 0; r < 6; ++r) cov[6 * r + c] = x[r];
+    }
+}
+
+// Map footprint of one Gauss-Newton launch at the current pose: the distinct
+// voxels probed by the 27-neighbourhoods of all source points and the points
+// they hold (the unique data a launch must read at least once).
+__global__ void k_footprint(MapView m, const float4* __restrict__ src, const RegState* __restrict__ st,
+                            u32* __restrict__ touched, unsigned long long* __restrict__ out) {
+    const u32 n = st->n_src;
+    const u32 max_probe = m.ctr->max_probe;
+    float T[12];
+    for (int j = 0; j < 12; ++j) T[j] = (float)st->T[j];
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 s = src[i];
+        const float qx = fmaf(T[0], s.x, fmaf(T[1], s.y, fmaf(T[2], s.z, T[3])));
+        const float qy = fmaf(T[4], s.x, fmaf(T[5], s.y, fmaf(T[6], s.z, T[7])));
+        const float qz = fmaf(T[8], s.x, fmaf(T[9], s.y, fmaf(T[10], s.z, T[11])));
+        int kx, ky, kz;
+        if (!voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz)) continue;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int nx = kx + dx, ny = ky + dy, nz = kz + dz;
+                    if (!key_in_range(nx) || !key_in_range(ny) || !key_in_range(nz)) continue;
+                    const u64 key = pack_key(nx, ny, nz);
+                    u32 h = hash_key(nx, ny, nz) & m.mask;
+                    for (u32 p = 0; p <= max_probe; ++p) {
+                        const Slot sl = m.slots[h];
+                        if (sl.key == key) {
+                            if (sl.bucket != NO_BUCKET && atomicExch(&touched[h], 1u) == 0u) {
+                                atomicAdd(&out[0], 1ull);
+                                atomicAdd(&out[1], (unsigned long long)sl.count);
+                            }
+                            break;
+                        }
+                        if (sl.key == KEY_EMPTY) break;
+                        h = (h + 1) & m.mask;
+                    }
+                }
+    }
+}
+
+}  // namespace
+
+cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st, u32* touched, u32 cap,
+                         unsigned long long* out2, u32 n_upper, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(touched, 0, (size_t)cap * sizeof(u32), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    FAR_LAUNCH(k_footprint, gn_grid(n_upper), GN_THREADS, 0, s, m, src, st, touched, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t gn_covariance(RegState* st, double* cov36, cudaStream_t s) {
+    FAR_LAUNCH(k_gn_cov, 1, 1, 0, s, st, cov36);
+    return cudaGetLastError();
+}
+
+u32 gn_grid(u32 n_upper) {
+    u32 b = (n_upper + GN_THREADS - 1) / GN_THREADS;
+    if (b == 0) b = 1;
+    return b < 152u * 8u ? b : 152u * 8u;
+}
+
+size_t gn_partials_doubles(u32 n_upper) { return (size_t)gn_grid(n_upper) * NPART; }
+
+cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s) {
+    Pose16 p;
+    for (int j = 0; j < 16; ++j) p.m[j] = init[j];
+    FAR_LAUNCH(k_gn_begin, 1, 1, 0, s, st, p, n_src);
+    return cudaGetLastError();
+}
+
+cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s) {
+    FAR_LAUNCH(k_gn_iter, gn_grid(n_upper), GN_THREADS, 0, s, a);
+    return cudaGetLastError();
+}
+
+}  // namespace far

@@ -1,0 +1,36 @@
+#pragma once
+#include "far_internal.cuh"
+
+namespace far {
+
+struct Pose16 {
+    double m[16];
+};
+
+struct GnArgs {
+    MapView map;                 // registration map (points + covariances)
+    const float4* src;           // source points (sensor frame), w = local rank
+    const float4* src_cov;       // two float4 per source point, valid flag in [1].z
+    const u32* n_src;            // device count of source points
+    u32 n_max;                   // upper bound of n_src (grid sizing)
+    RegState* st;
+    double* partials;            // gn_partials_doubles(n_max)
+    float tau2, kappa2;
+    double conv_eps;
+    int update;                  // 0: linearise only (stage entry point)
+    int32_t* corr_out;           // optional per-source correspondence ids
+    unsigned long long budget_ns;  // 0: no time cap
+};
+
+u32 gn_grid(u32 n_upper);
+size_t gn_partials_doubles(u32 n_upper);
+// Reset the registration state to `init`; n_src (device, may be null) is recorded in st->n_src.
+cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s);
+cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s);
+// Distinct map voxels (out2[0]) and their points (out2[1]) probed by the source points at st->T.
+cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st, u32* touched, u32 cap,
+                         unsigned long long* out2, u32 n_upper, cudaStream_t s);
+// cov36 = H^-1 of the last linearisation in st (zeros when H is not positive definite).
+cudaError_t gn_covariance(RegState* st, double* cov36, cudaStream_t s);
+
+}  // namespace far

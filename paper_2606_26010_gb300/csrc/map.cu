@@ -1,0 +1,613 @@
+// Voxel map kernels: batched insert with the spacing rule and the Adaptive
+// Submap Density cap, eviction, rebuild, export helpers and stage searches.
+// FAR-LIO Sec. III-A.2 (cuVoxelMap) and Sec. III-A.3 (submap update).
+//
+// Determinism: admission inside a voxel follows the input order because the
+// points of a batch are grouped by a stable radix sort on their slot index;
+// point ids are an exclusive scan of the admission flags in input order. Slot
+// and bucket placement depend on thread timing, but nothing visible does.
+#include "map.cuh"
+#include "primitives.cuh"
+#include "search.cuh"
+
+namespace far {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline u32 blocks_for(u32 n, u32 tpb = TPB) {
+    u32 b = (n + tpb - 1) / tpb;
+    return b ? b : 1;
+}
+
+__global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* __restrict__ out) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* p = reinterpret_cast<const float*>(src + (size_t)i * stride);
+    out[i] = make_float4(p[0], p[1], p[2], __uint_as_float(i));
+}
+
+// a11: x_w = fp32(((R0 x + R1 y) + R2 z) + t) in FP64 without contraction; then the key.
+__global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
+                             float inv_v, float4* __restrict__ world, u64* __restrict__ keys) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (dp.T) {
+#pragma unroll
+        for (int j = 0; j < 12; ++j) T.m[j] = dp.T[j];
+    }
+    const float4 p = in[i];
+    float w[3] = {p.x, p.y, p.z};
+    const bool finite = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && !(dp.status && *dp.status != 0);
+    if (has_pose && finite) {
+        const double x = p.x, y = p.y, z = p.z;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], x), __dmul_rn(T.m[4 * r + 1], y));
+            s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], z));
+            s = __dadd_rn(s, T.m[4 * r + 3]);
+            w[r] = __double2float_rn(s);
+        }
+    }
+    world[i] = make_float4(w[0], w[1], w[2], p.w);
+    u64 key = KEY_INVALID;
+    int kx, ky, kz;
+    if (finite && voxel_key3(w[0], w[1], w[2], inv_v, kx, ky, kz)) key = pack_key(kx, ky, kz);
+    keys[i] = key;
+}
+
+__global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slots, u32 mask,
+                                 u32* __restrict__ out_slot, u32* __restrict__ out_idx, MapCounters* ctr) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out_idx[i] = i;
+    const u64 key = keys[i];
+    const u32 sentinel = mask + 1u;
+    if (key == KEY_INVALID) {
+        out_slot[i] = sentinel;
+        return;
+    }
+    int kx, ky, kz;
+    unpack_key(key, kx, ky, kz);
+    u32 h = hash_key(kx, ky, kz) & mask;
+    for (u32 p = 0; p <= mask; ++p) {
+        const u64 k = *reinterpret_cast<volatile u64*>(&slots[h].key);
+        if (k == key) {
+            out_slot[i] = h;
+            atomicMax(&ctr->max_probe, p);
+            return;
+        }
+        if (k == KEY_EMPTY) {
+            const u64 old = atomicCAS(&slots[h].key, KEY_EMPTY, key);
+            if (old == KEY_EMPTY || old == key) {
+                out_slot[i] = h;
+                atomicMax(&ctr->max_probe, p);
+                return;
+            }
+        }
+        h = (h + 1u) & mask;
+    }
+    out_slot[i] = sentinel;
+    atomicOr(&ctr->err, (u32)ERR_TABLE_FULL);
+    atomicAdd(&ctr->n_dropped, 1u);
+}
+
+__global__ void k_group_heads(const u32* __restrict__ sk, u32 n, u32 sentinel, u32* __restrict__ flags) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u32 k = sk[i];
+    flags[i] = (k != sentinel && (i == 0 || sk[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void k_group_starts(const u32* __restrict__ sk, const u32* __restrict__ flags,
+                               const u32* __restrict__ gidx, u32 n, u32 sentinel, u32* __restrict__ gstart,
+                               const u32* __restrict__ scal) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flags[i]) gstart[gidx[i]] = i;
+    const u32 k = sk[i];
+    if (k != sentinel && (i + 1 == n || sk[i + 1] == sentinel)) gstart[scal[SCAL_NGROUPS]] = i + 1;
+}
+
+__device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v, double sx, double sy,
+                                               double sz) {
+    const double dx = __dsub_rn(__dmul_rn(__dadd_rn((double)kx, 0.5), v), sx);
+    const double dy = __dsub_rn(__dmul_rn(__dadd_rn((double)ky, 0.5), v), sy);
+    const double dz = __dsub_rn(__dmul_rn(__dadd_rn((double)kz, 0.5), v), sz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// a10: sum and count of the (uncapped) candidate counts of this batch's voxels within r_c.
+__global__ void k_asmd_near(const u32* __restrict__ gstart, const u32* __restrict__ scal,
+                            const u32* __restrict__ sk, const Slot* __restrict__ slots, double v, InsertCfg cfg,
+                            const double* __restrict__ dev_T, MapCounters* ctr) {
+    if (dev_T) {
+        cfg.sx = dev_T[3];
+        cfg.sy = dev_T[7];
+        cfg.sz = dev_T[11];
+    }
+    const u32 ng = scal[SCAL_NGROUPS];
+    unsigned long long sum = 0, cnt = 0;
+    for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const u32 s0 = gstart[g], s1 = gstart[g + 1];
+        int kx, ky, kz;
+        unpack_key(slots[sk[s0]].key, kx, ky, kz);
+        if (centre_dist2(kx, ky, kz, v, cfg.sx, cfg.sy, cfg.sz) <= cfg.rc2) {
+            sum += s1 - s0;
+            cnt += 1;
+        }
+    }
+    if (cnt) {
+        atomicAdd(&ctr->near_sum, sum);
+        atomicAdd(&ctr->near_cnt, cnt);
+    }
+}
+
+// N_ASMD(r) = clamp(round(N_near + (k - N_near) min(r / r_max, 1)), k, N_max), FP64.
+__device__ __forceinline__ u32 asmd_cap(int kx, int ky, int kz, double v, const InsertCfg& cfg, double n_near,
+                                        u32 k, u32 nmax) {
+    const double r = __dsqrt_rn(centre_dist2(kx, ky, kz, v, cfg.sx, cfg.sy, cfg.sz));
+    double f = __ddiv_rn(r, cfg.r_max);
+    if (f > 1.0) f = 1.0;
+    const double val = __dadd_rn(n_near, __dmul_rn(__dsub_rn((double)k, n_near), f));
+    const double c = floor(__dadd_rn(val, 0.5));
+    if (c > (double)nmax) return nmax;
+    if (c < (double)k) return k;
+    return (u32)c;
+}
+
+struct AdmitArgs {
+    const u32* sk;
+    const u32* sv;
+    const u32* gstart;
+    const u32* scal;
+    const float4* world;
+    Slot* slots;
+    float4* pts;
+    const u32* ring;
+    u32 max_buckets;
+    MapCounters* ctr;
+    u32 nmax, k;
+    float dmin2;
+    double v;
+    InsertCfg cfg;
+    const double* dev_T;
+    u32* admitted;
+    u32* pos;
+};
+
+// a11 admission: one warp per voxel group. Candidates are walked in input order;
+// a candidate enters while the voxel holds fewer than its cap and no point of the
+// voxel is closer than d_min (FP32 d^2 >= d_min^2). Lanes hold the voxel's points
+// (lane j: points j and j + 32) and test a candidate against all of them at once;
+// windows of 32 candidates are prefetched one per lane.
+__global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
+    if (a.dev_T) {
+        a.cfg.sx = a.dev_T[3];
+        a.cfg.sy = a.dev_T[7];
+        a.cfg.sz = a.dev_T[11];
+    }
+    const int lane = threadIdx.x & 31;
+    const u32 warps_total = (gridDim.x * blockDim.x) >> 5;
+    const u32 ng = a.scal[SCAL_NGROUPS];
+    double n_near = (double)a.nmax;
+    if (a.cfg.asmd && a.ctr->near_cnt > 0)
+        n_near = __ddiv_rn((double)a.ctr->near_sum, (double)a.ctr->near_cnt);
+    const u32 ring_tail = a.ctr->ring_tail;
+    const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
+    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps_total) {
+        const u32 start = a.gstart[g], end = a.gstart[g + 1];
+        const u32 slot = a.sk[start];
+        Slot* sp = a.slots + slot;
+        u32 bucket = sp->bucket;
+        u32 cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
+        if (bucket == NO_BUCKET) {
+            u32 b = NO_BUCKET;
+            if (lane == 0) {
+                const u32 h = atomicAdd(&a.ctr->ring_head, 1u);
+                if (h < ring_tail) {
+                    b = a.ring[h % a.max_buckets];
+                    sp->bucket = b;
+                    sp->count = 0;
+                    atomicAdd(&a.ctr->n_voxels, 1u);
+                } else {
+                    atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
+                    atomicAdd(&a.ctr->n_dropped, end - start);
+                }
+            }
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b == NO_BUCKET) continue;
+            bucket = b;
+        }
+        int kx, ky, kz;
+        unpack_key(sp->key, kx, ky, kz);
+        const u32 cap = a.cfg.asmd ? asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax) : a.nmax;
+        float4* bp = a.pts + (size_t)bucket * a.nmax;
+        float4 e0 = (lane < (int)cnt) ? bp[lane] : far4;
+        float4 e1 = (lane + 32 < (int)cnt) ? bp[lane + 32] : far4;
+        const u32 cnt0 = cnt;
+        for (u32 w0 = start; w0 < end && cnt < cap; w0 += 32) {
+            const u32 i = w0 + lane;
+            const u32 my_idx = (i < end) ? a.sv[i] : 0u;
+            const float4 my_c = (i < end) ? a.world[my_idx] : far4;
+            const u32 wn = min(32u, end - w0);
+            for (u32 j = 0; j < wn && cnt < cap; ++j) {
+                const float cx = __shfl_sync(0xffffffffu, my_c.x, j);
+                const float cy = __shfl_sync(0xffffffffu, my_c.y, j);
+                const float cz = __shfl_sync(0xffffffffu, my_c.z, j);
+                const u32 cidx = __shfl_sync(0xffffffffu, my_idx, j);
+                bool conflict = false;
+                if (lane < (int)cnt) conflict = !(dist2_rn(cx, cy, cz, e0.x, e0.y, e0.z) >= a.dmin2);
+                if (lane + 32 < (int)cnt) conflict |= !(dist2_rn(cx, cy, cz, e1.x, e1.y, e1.z) >= a.dmin2);
+                if (__any_sync(0xffffffffu, conflict)) continue;
+                const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
+                if (lane == (int)(cnt & 31u)) {
+                    if (cnt < 32) e0 = c;
+                    else e1 = c;
+                }
+                if (lane == 0) {
+                    bp[cnt] = c;
+                    a.pos[cidx] = bucket * a.nmax + cnt;
+                    a.admitted[cidx] = 1u;
+                }
+                ++cnt;
+            }
+        }
+        if (lane == 0 && cnt != cnt0) sp->count = cnt;
+    }
+}
+
+__global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __restrict__ rank,
+                             const u32* __restrict__ pos, u32 n, float4* pts, u32* __restrict__ added,
+                             const u32* __restrict__ scal, MapCounters* ctr) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !admitted[i]) return;
+    const u32 base = ctr->next_id;
+    const u32 r = rank[i];
+    pts[pos[i]].w = __uint_as_float(base + r);
+    added[r] = pos[i];
+    if (i == 0 || r + 1 == scal[SCAL_NADMIT]) {
+        if ((unsigned long long)base + scal[SCAL_NADMIT] > 0xFFFFFFFFull) atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
+    }
+}
+
+__global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal) {
+    const u32 t = scal[SCAL_NADMIT];
+    ctr->next_id += t;
+    ctr->n_points += t;
+    ctr->n_added = t;
+}
+
+// Eq. 1 covariances of query points against map m. Queries are either q[r]
+// (q != null) or m.pts[qpos[r]]; output index is out_pos[r] (map points) or r.
+template <int K>
+__global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __restrict__ q,
+                                                 const u32* __restrict__ qpos, u32 n, const u32* __restrict__ n_dev,
+                                                 int k, float4* __restrict__ cov_out, const u32* __restrict__ out_pos,
+                                                 u32* __restrict__ knn_ids) {
+    const u32 nn = n_dev ? min(n, *n_dev) : n;
+    const u32 max_probe = m.ctr->max_probe;
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
+        const float4 p = q ? q[r] : m.pts[qpos[r]];
+        float bd[K];
+        u32 bid[K], bpos[K];
+        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, k, bd, bid, bpos);
+        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (found >= k) covariance_from_neighbours<K>(m.pts, bpos, k, p.x, p.y, p.z, c0, c1);
+        const u32 o = out_pos ? out_pos[r] : r;
+        cov_out[2 * (size_t)o] = c0;
+        cov_out[2 * (size_t)o + 1] = c1;
+        if (knn_ids) {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < k) knn_ids[(size_t)r * k + j] = (j < found) ? bid[j] : NO_ID;
+        }
+    }
+}
+
+__global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __restrict__ rank,
+                               const float4* __restrict__ in4, u32 n, float4* __restrict__ src,
+                               u32* __restrict__ src_index) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !admitted[i]) return;
+    const u32 r = rank[i];
+    const float4 p = in4[i];
+    src[r] = make_float4(p.x, p.y, p.z, __uint_as_float(r));
+    src_index[r] = i;
+}
+
+__global__ void k_iota(u32* a, u32 n) {
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+__global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, double cz, double r2, u32* ring,
+                        u32 max_buckets, MapCounters* ctr, const double* __restrict__ dev_T) {
+    if (dev_T) {
+        cx = dev_T[3];
+        cy = dev_T[7];
+        cz = dev_T[11];
+    }
+    for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
+        const u64 key = slots[h].key;
+        if (key >> 63) continue;  // empty or tombstone
+        int kx, ky, kz;
+        unpack_key(key, kx, ky, kz);
+        if (!(centre_dist2(kx, ky, kz, v, cx, cy, cz) > r2)) continue;
+        const u32 b = slots[h].bucket;
+        const u32 c = slots[h].count;
+        slots[h].key = KEY_TOMB;
+        slots[h].bucket = NO_BUCKET;
+        slots[h].count = 0;
+        atomicAdd(&ctr->n_tomb, 1u);
+        if (b != NO_BUCKET) {
+            const u32 t = atomicAdd(&ctr->ring_tail, 1u);
+            ring[t % max_buckets] = b;
+            atomicSub(&ctr->n_voxels, 1u);
+            atomicAdd(&ctr->removed, (unsigned long long)c);
+            atomicAdd(&ctr->n_points, (unsigned long long)(0ull - (unsigned long long)c));
+        }
+    }
+}
+
+__global__ void k_rebuild(const Slot* __restrict__ old_slots, u32 old_cap, Slot* new_slots, u32 mask,
+                          MapCounters* ctr) {
+    for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < old_cap; h += gridDim.x * blockDim.x) {
+        const Slot s = old_slots[h];
+        if (s.key >> 63) continue;
+        int kx, ky, kz;
+        unpack_key(s.key, kx, ky, kz);
+        u32 j = hash_key(kx, ky, kz) & mask;
+        for (u32 p = 0; p <= mask; ++p) {
+            if (atomicCAS(&new_slots[j].key, KEY_EMPTY, s.key) == KEY_EMPTY) {
+                new_slots[j].bucket = s.bucket;
+                new_slots[j].count = s.count;
+                atomicMax(&ctr->max_probe, p);
+                break;
+            }
+            j = (j + 1u) & mask;
+        }
+    }
+}
+
+__global__ void k_list_slots(const Slot* __restrict__ slots, u32 cap, u64* keys, u32* buckets, u32* counts,
+                             u32* n_out, u32 cap_out) {
+    for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
+        const Slot s = slots[h];
+        if ((s.key >> 63) || s.bucket == NO_BUCKET || s.count == 0) continue;
+        const u32 o = atomicAdd(n_out, 1u);
+        if (o >= cap_out) continue;  // counted, not written: the caller sees n_out > cap_out
+        keys[o] = s.key;
+        buckets[o] = s.bucket;
+        counts[o] = s.count;
+    }
+}
+
+__global__ void k_gather(const float4* __restrict__ pts, const float4* __restrict__ cov, u32 nmax,
+                         const u32* __restrict__ buckets, const u32* __restrict__ counts,
+                         const u32* __restrict__ offsets, u32 nvox, float4* __restrict__ pts_out,
+                         float4* __restrict__ cov_out) {
+    const int lane = threadIdx.x & 31;
+    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nvox; g += (gridDim.x * blockDim.x) >> 5) {
+        const u32 b = buckets[g], c = counts[g], o = offsets[g];
+        for (u32 j = lane; j < c; j += 32) {
+            pts_out[o + j] = pts[(size_t)b * nmax + j];
+            if (cov) {
+                cov_out[2 * (size_t)(o + j)] = cov[2 * ((size_t)b * nmax + j)];
+                cov_out[2 * (size_t)(o + j) + 1] = cov[2 * ((size_t)b * nmax + j) + 1];
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __restrict__ q, u32 n, int k,
+                                                   u32* __restrict__ ids, int32_t* __restrict__ found_out) {
+    const u32 max_probe = m.ctr->max_probe;
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const float4 p = q[r];
+        float bd[K];
+        u32 bid[K], bpos[K];
+        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, k, bd, bid, bpos);
+        found_out[r] = found;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (j < k) ids[(size_t)r * k + j] = (j < found) ? bid[j] : NO_ID;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_nearest_stage(MapView m, const float4* __restrict__ q, u32 n, float tau2,
+                                                       int64_t* __restrict__ ids, float* __restrict__ d2_out) {
+    const u32 max_probe = m.ctr->max_probe;
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const float4 p = q[r];
+        float bd2;
+        u32 bid, bpos;
+        const bool any = nearest27(m, max_probe, p.x, p.y, p.z, bd2, bid, bpos);
+        d2_out[r] = bd2;
+        ids[r] = (any && !(bd2 > tau2)) ? (int64_t)bid : (int64_t)-1;
+    }
+}
+
+template <int K>
+cudaError_t launch_knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n, const u32* n_dev,
+                           float4* cov_out, const u32* out_pos, u32* knn_ids, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_knn_cov<K>, blocks_for(n), TPB, 0, st, m.view(), q, qpos, n, n_dev, (int)m.k, cov_out, out_pos, knn_ids);
+    return cudaGetLastError();
+}
+
+cudaError_t knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n, const u32* n_dev,
+                    float4* cov_out, const u32* out_pos, u32* knn_ids, cudaStream_t st) {
+    if (m.k <= 8) return launch_knn_cov<8>(m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st);
+    return launch_knn_cov<16>(m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st);
+}
+
+}  // namespace
+
+#define FAR_TRY(x)                                  \
+    do {                                            \
+        cudaError_t e__ = (x);                      \
+        if (e__ != cudaSuccess) return e__;         \
+    } while (0)
+
+cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_pack, blocks_for(n), TPB, 0, st, static_cast<const char*>(src), n, stride, out);
+    return cudaGetLastError();
+}
+
+cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
+                             bool covariances, cudaStream_t st, DevicePose dpose) {
+    FAR_TRY(cudaMemsetAsync(s.scal, 0, SCAL_COUNT * sizeof(u32), st));
+    // zero the per-insert counters (near_sum, near_cnt, n_added)
+    FAR_TRY(cudaMemsetAsync(&m.ctr->near_sum, 0, 2 * sizeof(unsigned long long), st));
+    FAR_TRY(cudaMemsetAsync(&m.ctr->n_added, 0, sizeof(u32), st));
+    if (n == 0) return cudaSuccess;
+    const u32 sentinel = m.cap;
+    Pose12 T{};
+    if (pose) T = *pose;
+    FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
+                                                m.inv_v, s.world, s.keys);
+    FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr);
+    bool alt = false;
+    FAR_TRY(radix_sort_pairs(s.sk, s.sv, s.sk_alt, s.sv_alt, n, m.key_bits, s.hist, s.partials, st, &alt));
+    const u32* sk = alt ? s.sk_alt : s.sk;
+    const u32* sv = alt ? s.sv_alt : s.sv;
+    FAR_LAUNCH(k_group_heads, blocks_for(n), TPB, 0, st, sk, n, sentinel, s.flags);
+    FAR_TRY(scan_exclusive(s.flags, s.gidx, n, nullptr, s.scal + SCAL_NGROUPS, s.partials, st));
+    FAR_LAUNCH(k_group_starts, blocks_for(n), TPB, 0, st, sk, s.flags, s.gidx, n, sentinel, s.gstart, s.scal);
+    if (cfg.asmd)
+        FAR_LAUNCH(k_asmd_near, blocks_for(n), TPB, 0, st, s.gstart, s.scal, sk, m.slots, (double)m.v, cfg, dpose.T,
+                                                   m.ctr);
+    FAR_TRY(cudaMemsetAsync(s.admitted, 0, (size_t)n * sizeof(u32), st));
+    AdmitArgs a;
+    a.sk = sk;
+    a.sv = sv;
+    a.gstart = s.gstart;
+    a.scal = s.scal;
+    a.world = s.world;
+    a.slots = m.slots;
+    a.pts = m.pts;
+    a.ring = m.ring;
+    a.max_buckets = m.max_buckets;
+    a.ctr = m.ctr;
+    a.nmax = m.nmax;
+    a.k = m.k;
+    a.dmin2 = m.dmin2;
+    a.v = (double)m.v;
+    a.cfg = cfg;
+    a.dev_T = dpose.T;
+    a.admitted = s.admitted;
+    a.pos = s.pos;
+    // one warp per group; groups <= n
+    const u32 warps = min(n, 152u * 64u);
+    FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
+    FAR_TRY(scan_exclusive(s.admitted, s.rank, n, nullptr, s.scal + SCAL_NADMIT, s.partials, st));
+    FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.added, s.scal, m.ctr);
+    FAR_LAUNCH(k_finalize_insert, 1, 1, 0, st, m.ctr, s.scal);
+    if (covariances && m.cov)
+        FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));
+    return cudaGetLastError();
+}
+
+cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_make_sources, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.in4, n, s.src, s.src_index);
+    return knn_cov(local, s.src, nullptr, n, s.scal + SCAL_NADMIT, s.src_cov, nullptr, knn_ids_out, st);
+}
+
+__global__ void k_clear_counters(MapCounters* ctr, u32 ring_tail) {
+    MapCounters c{};
+    c.ring_tail = ring_tail;
+    *ctr = c;
+}
+
+cudaError_t map_clear(DeviceMap& m, cudaStream_t st) {
+    FAR_TRY(cudaMemsetAsync(m.slots, 0xFF, (size_t)m.cap * sizeof(Slot), st));
+    // every bucket free: ring = identity, head = 0, tail = number of buckets
+    FAR_LAUNCH(k_iota, min(blocks_for(m.max_buckets), 152u * 8u), TPB, 0, st, m.ring, m.max_buckets);
+    FAR_LAUNCH(k_clear_counters, 1, 1, 0, st, m.ctr, m.max_buckets);
+    return cudaGetLastError();
+}
+
+cudaError_t map_evict(DeviceMap& m, const double center[3], double radius, cudaStream_t st, const double* dev_pose) {
+    FAR_TRY(cudaMemsetAsync(&m.ctr->removed, 0, sizeof(unsigned long long), st));
+    const u32 blocks = min(blocks_for(m.cap), 152u * 16u);
+    const double c0 = center ? center[0] : 0.0, c1 = center ? center[1] : 0.0, c2 = center ? center[2] : 0.0;
+    FAR_LAUNCH(k_evict, blocks, TPB, 0, st, m.slots, m.cap, (double)m.v, c0, c1, c2, radius * radius, m.ring, m.max_buckets,
+                                    m.ctr, dev_pose);
+    return cudaGetLastError();
+}
+
+cudaError_t map_rebuild(DeviceMap& m, cudaStream_t st) {
+    FAR_TRY(cudaMemsetAsync(m.slots_alt, 0xFF, (size_t)m.cap * sizeof(Slot), st));
+    FAR_TRY(cudaMemsetAsync(&m.ctr->max_probe, 0, sizeof(u32), st));
+    FAR_TRY(cudaMemsetAsync(&m.ctr->n_tomb, 0, sizeof(u32), st));
+    const u32 blocks = min(blocks_for(m.cap), 152u * 16u);
+    FAR_LAUNCH(k_rebuild, blocks, TPB, 0, st, m.slots, m.cap, m.slots_alt, m.mask, m.ctr);
+    Slot* t = m.slots;
+    m.slots = m.slots_alt;
+    m.slots_alt = t;
+    return cudaGetLastError();
+}
+
+cudaError_t map_list_slots(const DeviceMap& m, u64* keys, u32* buckets, u32* counts, u32* n_out, u32 cap_out,
+                           cudaStream_t st) {
+    FAR_TRY(cudaMemsetAsync(n_out, 0, sizeof(u32), st));
+    const u32 blocks = min(blocks_for(m.cap), 152u * 16u);
+    FAR_LAUNCH(k_list_slots, blocks, TPB, 0, st, m.slots, m.cap, keys, buckets, counts, n_out, cap_out);
+    return cudaGetLastError();
+}
+
+cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets, u32 nvox,
+                       float4* pts_out, float4* cov_out, cudaStream_t st) {
+    if (nvox == 0) return cudaSuccess;
+    FAR_LAUNCH(k_gather, blocks_for(nvox * 32u), TPB, 0, st, m.pts, m.cov, m.nmax, buckets, counts, offsets, nvox, pts_out,
+                                                     cov_out);
+    return cudaGetLastError();
+}
+
+cudaError_t map_knn(const DeviceMap& m, const float4* q, u32 n, u32 k, u32* ids, int32_t* found, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (k <= 8)
+        FAR_LAUNCH(k_knn_stage<8>, blocks_for(n), TPB, 0, st, m.view(), q, n, (int)k, ids, found);
+    else
+        FAR_LAUNCH(k_knn_stage<16>, blocks_for(n), TPB, 0, st, m.view(), q, n, (int)k, ids, found);
+    return cudaGetLastError();
+}
+
+cudaError_t map_nearest(const DeviceMap& m, const float4* q, u32 n, float tau2, int64_t* ids, float* d2,
+                        cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_nearest_stage, blocks_for(n), TPB, 0, st, m.view(), q, n, tau2, ids, d2);
+    return cudaGetLastError();
+}
+
+}  // namespace far
+
+namespace far {
+
+namespace {
+__global__ void k_export_sources(const u32* __restrict__ src_index, const float4* __restrict__ src_cov,
+                                 const u32* __restrict__ n_dev, u32 n, int64_t* __restrict__ index,
+                                 float* __restrict__ cov6, uint8_t* __restrict__ valid) {
+    const u32 nn = min(n, *n_dev);
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
+        index[r] = (int64_t)src_index[r];
+        const float4 c0 = src_cov[2 * (size_t)r], c1 = src_cov[2 * (size_t)r + 1];
+        float* o = cov6 + 6 * (size_t)r;
+        o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c0.w; o[4] = c1.x; o[5] = c1.y;
+        valid[r] = c1.z > 0.5f ? 1 : 0;
+    }
+}
+}  // namespace
+
+cudaError_t export_sources(const Scratch& s, u32 n, int64_t* index, float* cov6, uint8_t* valid, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_export_sources, blocks_for(n), TPB, 0, st, s.src_index, s.src_cov, s.scal + SCAL_NADMIT, n, index, cov6,
+                                                    valid);
+    return cudaGetLastError();
+}
+
+}  // namespace far

@@ -1,0 +1,121 @@
+#pragma once
+#include "far_internal.cuh"
+
+namespace far {
+
+// One voxel map on the device (the registration map, or the scan-local map
+// used for the source covariances, FAR-LIO Sec. III-A.2 "Cov-Calc").
+struct DeviceMap {
+    Slot* slots = nullptr;
+    Slot* slots_alt = nullptr;   // rebuild target (registration map only)
+    u32 cap = 0, mask = 0;
+    int key_bits = 0;            // bits of a slot index plus one (sort key incl. sentinel)
+    float4* pts = nullptr;
+    float4* cov = nullptr;       // null for the scan-local map
+    u32* ring = nullptr;
+    u32 max_buckets = 0;
+    MapCounters* ctr = nullptr;
+    u32 nmax = 0, k = 0;
+    float v = 0, inv_v = 0, dmin2 = 0;
+
+    MapView view() const {
+        MapView mv;
+        mv.slots = slots;
+        mv.pts = pts;
+        mv.cov = cov;
+        mv.ctr = ctr;
+        mv.mask = mask;
+        mv.nmax = nmax;
+        mv.inv_v = inv_v;
+        return mv;
+    }
+};
+
+// Per-scan scratch, sized once for the largest accepted scan.
+struct Scratch {
+    u32 max_n = 0;
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    float4* in4 = nullptr;     // packed input points, w = input index
+    float4* world = nullptr;   // keyed points (map frame), by input index
+    u64* keys = nullptr;
+    u32 *sk = nullptr, *sv = nullptr, *sk_alt = nullptr, *sv_alt = nullptr;
+    u32 *flags = nullptr, *gidx = nullptr, *gstart = nullptr;
+    u32 *admitted = nullptr, *rank = nullptr, *pos = nullptr, *added = nullptr;
+    u32 *hist = nullptr, *partials = nullptr;
+    u32* scal = nullptr;       // device scalars, see SCAL_*
+    // registration sources
+    float4 *src = nullptr, *src_cov = nullptr;
+    u32* src_index = nullptr;
+    // stage outputs
+    u32* knn_ids = nullptr;
+    int32_t* i32_out = nullptr;
+    float* f32_out = nullptr;
+    int64_t* i64_out = nullptr;
+    // Gauss-Newton
+    double* gn_partials = nullptr;
+    u32 max_gn_blocks = 0;
+    RegState* st = nullptr;
+    // diagnostics
+    u32* touched = nullptr;              // one flag per registration-map slot
+    unsigned long long* foot = nullptr;  // footprint counters
+};
+
+enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_COUNT = 8 };
+
+struct InsertCfg {
+    int asmd = 0;
+    double sx = 0, sy = 0, sz = 0;  // sensor position (ignored when a device pose is given)
+    double rc2 = 0;                 // r_near^2
+    double r_max = 1;
+};
+
+// Pose of an insert kept on the device (the result of a registration): the map
+// transform and the sensor position are read from T, and nothing is inserted
+// unless *status == 0.
+struct DevicePose {
+    const double* T = nullptr;      // row-major 4x4
+    const u32* status = nullptr;
+};
+
+struct Pose12 {
+    double m[12];
+};
+
+// Pack `n` records of `stride` bytes (first 12 bytes xyz) into s.in4 (w = index).
+cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStream_t st);
+
+// Insert the packed points s.in4[0..n) into m (Sec. III-A.3). pose == nullptr keys the
+// raw points (scan-local map). Ids start at m.ctr->next_id. With `covariances`, Eq. 1
+// covariances of the added points are computed against the updated map.
+cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
+                             bool covariances, cudaStream_t st, DevicePose dpose = DevicePose());
+
+// Scan-local sources after map_insert_batch on the local map: s.src / s.src_index in
+// admission order, then their covariances from the local map.
+cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st);
+
+// Reset a map to empty (keys, counters, free ring).
+cudaError_t map_clear(DeviceMap& m, cudaStream_t st);
+
+// Evict voxels whose centre is farther than radius from center (tombstones the slots).
+cudaError_t map_evict(DeviceMap& m, const double center[3], double radius, cudaStream_t st,
+                      const double* dev_pose = nullptr);
+// Re-insert the live slots into the spare slot array and swap (drops tombstones).
+cudaError_t map_rebuild(DeviceMap& m, cudaStream_t st);
+
+// Compact live slots into (key, bucket, count) triples (at most cap_out written); *n_out
+// receives the number of live slots found.
+cudaError_t map_list_slots(const DeviceMap& m, u64* keys, u32* buckets, u32* counts, u32* n_out, u32 cap_out,
+                           cudaStream_t st);
+
+// Gather points of the listed buckets into contiguous arrays (offsets = exclusive prefix of counts).
+cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets, u32 nvox,
+                       float4* pts_out, float4* cov_out, cudaStream_t st);
+
+// k-NN and 1-NN of packed queries (stage entry points).
+cudaError_t map_knn(const DeviceMap& m, const float4* q, u32 n, u32 k, u32* ids, int32_t* found, cudaStream_t st);
+cudaError_t map_nearest(const DeviceMap& m, const float4* q, u32 n, float tau2, int64_t* ids, float* d2,
+                        cudaStream_t st);
+
+}  // namespace far

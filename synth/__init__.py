@@ -221,7 +221,8 @@ def oval_track_scene(seed: int) -> Scene:
     """Walled oval: straights of 700 m, radius 120 m, walls at +-10 m.
 
     Each side has a 1.5 m barrier and a fence from 1.5 m to 6 m just behind it,
-    0.3 m poles every 25 m in front of the barriers, grandstands outside the
+    0.3 m poles every 25 m in front of the barriers, marshal posts and sign
+    boards (small boxes) on the verges about every 12 m, grandstands outside the
     straights and a few buildings in the infield.
     """
     rng = np.random.default_rng(seed)
@@ -242,6 +243,14 @@ def oval_track_scene(seed: int) -> Scene:
         for side in (-9.5, 9.5):
             sc.pole(x + side * nx, y + side * ny, 0.15, 0.0, 8.0)
         s += 25.0
+    s = 6.0
+    while s < TRACK_LENGTH - 1e-6:
+        x, y, h = track_centreline(s)
+        nx, ny = -math.sin(h), math.cos(h)
+        side = rng.choice([-1.0, 1.0]) * rng.uniform(8.3, 9.0)
+        hx, hy, hz = rng.uniform(0.3, 1.0), rng.uniform(0.15, 0.5), rng.uniform(0.5, 1.4)
+        sc.box(x + side * nx, y + side * ny, hz, hx, hy, hz, h + rng.uniform(-0.8, 0.8))
+        s += rng.uniform(8.0, 16.0)
     for xc in (-220.0, 0.0, 220.0):
         for sgn in (-1.0, 1.0):
             h = rng.uniform(14.0, 22.0)

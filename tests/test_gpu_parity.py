@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: voxel keys, map contents (sorted key -> ordered ids and FP32
+points), admitted source indices, k-NN and 1-NN id sets, validity flags.
+Tolerances (floating point, derived in the design notes):
+  covariances   |Sigma_gpu - Sigma_oracle|_max <= 1e-3 |Sigma_oracle|_F  (FP32 Eq. 1, condition <= 1e3)
+  final pose    1e-4 m translation and 1e-5 rad rotation (the stated target)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+COV_RTOL = 1e-3
+POSE_T_TOL = 1e-4
+POSE_R_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def far():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2606_26010_gb300 import build, far as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def pose_err(A, B):
+    D = np.linalg.inv(A) @ B
+    return np.linalg.norm(D[:3, 3]), abs(math.acos(max(-1.0, min(1.0, (np.trace(D[:3, :3]) - 1) / 2))))
+
+
+def assert_maps_equal(gpu, ora):
+    np.testing.assert_array_equal(gpu["keys"], ora["keys"])
+    np.testing.assert_array_equal(gpu["counts"], ora["counts"])
+    np.testing.assert_array_equal(gpu["ids"], ora["ids"])
+    np.testing.assert_array_equal(gpu["xyz"], ora["xyz"])
+    np.testing.assert_array_equal(gpu["valid"].astype(bool), ora["valid"].astype(bool))
+    assert_cov_close(gpu["cov"], ora["cov"], ora["valid"].astype(bool))
+
+
+def assert_cov_close(g, o, valid):
+    g = np.asarray(g, np.float64)[valid]
+    o = np.asarray(o, np.float64)[valid]
+    if len(o) == 0:
+        return
+    fro = np.sqrt(o[:, 0] ** 2 + o[:, 3] ** 2 + o[:, 5] ** 2 + 2 * (o[:, 1] ** 2 + o[:, 2] ** 2 + o[:, 4] ** 2))
+    err = np.abs(g - o).max(axis=1)
+    assert (err <= COV_RTOL * fro).all(), f"worst relative covariance error {np.max(err / fro):.3g}"
+
+
+def build_pair(far, scans, poses, v=0.5, nmax=20, k=5, asmd=False, r_near=10.0, r_max=100.0, max_scan=300_000,
+               max_voxels=1 << 20, spacing=-1.0):
+    g = far.VoxelMap(v, nmax, k, spacing, max_voxels=max_voxels, max_scan_points=max_scan)
+    o = oracle.OracleMap(v, nmax, k, spacing)
+    for s, T in zip(scans, poses):
+        ng = g.insert(s, T, asmd=asmd, r_near=r_near, r_max=r_max)
+        no, _ = o.insert(s, T, asmd=asmd, r_c=r_near, r_max=r_max)
+        assert ng == no
+    return g, o
+
+
+@pytest.fixture(scope="module")
+def problem1():
+    return synth.single_scan_problem(1)
+
+
+@pytest.fixture(scope="module")
+def maps1(far, problem1):
+    return build_pair(far, problem1.map_scans, problem1.map_poses)
+
+
+# ------------------------------------------------------------------ map contents
+def test_map_insert_bit_exact(maps1):
+    g, o = maps1
+    assert g.size() == (o.num_voxels, o.num_points)
+    assert_maps_equal(g.export(), o.export())
+
+
+def test_map_insert_asmd_and_evict_bit_exact_full_size(far):
+    seq = synth.TrackSequence(42)
+    g, o = build_pair(far, [seq.scan(t) for t in range(3)], [seq.pose(t) for t in range(3)], asmd=True,
+                      r_near=10.0, r_max=200.0)
+    assert_maps_equal(g.export(), o.export())
+    c = seq.pose(2)[:3, 3]
+    assert g.evict(c, 40.0) == o.evict(c, 40.0)
+    assert_maps_equal(g.export(), o.export())
+    s3, T3 = seq.scan(3), seq.pose(3)
+    assert g.insert(s3, T3, asmd=True, r_near=10.0, r_max=200.0) == o.insert(s3, T3, asmd=True, r_c=10.0,
+                                                                           r_max=200.0)[0]
+    assert_maps_equal(g.export(), o.export())
+
+
+def test_no_spacing_and_single_voxel_cap(far):
+    rng = np.random.default_rng(5)
+    pts = (rng.uniform(0.01, 0.49, size=(500, 3))).astype(np.float32)   # all in voxel (0,0,0)
+    for spacing in (0.0, 0.05):
+        g, o = build_pair(far, [pts, pts[::-1].copy()], [np.eye(4), np.eye(4)], nmax=40, spacing=spacing)
+        assert_maps_equal(g.export(), o.export())
+
+
+# ------------------------------------------------------------------ searches
+def test_scan_sources_bit_exact(far, problem1):
+    g = far.VoxelMap(0.5, 20, 5, max_scan_points=300_000)
+    for scan in (problem1.query, synth.TrackSequence(42).scan(0)):
+        a = g.scan_sources(scan)
+        b = oracle.scan_sources(scan, 0.5, 20, 5)
+        np.testing.assert_array_equal(a["index"], b["index"])
+        np.testing.assert_array_equal(a["valid"].astype(bool), b["valid"].astype(bool))
+        np.testing.assert_array_equal(a["knn"], b["knn"])
+        assert_cov_close(a["cov"], b["cov"], b["valid"].astype(bool))
+
+
+def test_nearest_and_knn_bit_exact(far, problem1, maps1):
+    g, o = maps1
+    rng = np.random.default_rng(2)
+    q = problem1.query.astype(np.float64) @ problem1.truth[:3, :3].T + problem1.truth[:3, 3]
+    q = np.concatenate([q, q + rng.normal(scale=0.3, size=q.shape)]).astype(np.float32)
+    ig, dg = g.nearest(q, 0.8)
+    io, do = o.nearest(q, 0.8)
+    np.testing.assert_array_equal(ig, io)
+    np.testing.assert_array_equal(dg, do)
+    for k in (1, 5, 16):
+        a, fa = g.knn(q[::7], k)
+        b, fb = o.knn(q[::7], k)
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------------------------ Gauss-Newton
+def test_linearize_matches_oracle(far, problem1, maps1):
+    g, o = maps1
+    src = oracle.scan_sources(problem1.query, 0.5, 20, 5)
+    L_o = o.linearize(problem1.query[src["index"]], src["cov"], src["valid"], problem1.init, 2.0, 2.0 / 9)
+    L_g = g.linearize(problem1.query, problem1.init, 2.0, 2.0 / 9)
+    assert L_g["n_src"] == len(src["index"])
+    agree = np.mean(L_g["corr"] == L_o["corr"])
+    assert agree > 0.999, agree
+    assert abs(L_g["n_corr"] - L_o["n_corr"]) <= 0.001 * L_o["n_corr"] + 1
+    Hn = np.linalg.norm(L_o["H"])
+    assert np.linalg.norm(L_g["H"] - L_o["H"]) <= 2e-3 * Hn
+    xi_g = np.linalg.solve(L_g["H"], -L_g["g"])
+    xi_o = np.linalg.solve(L_o["H"], -L_o["g"])
+    assert np.abs(xi_g - xi_o).max() < 1e-4
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_register_pose_parity(far, seed):
+    p = synth.single_scan_problem(seed)
+    g, o = build_pair(far, p.map_scans, p.map_poses)
+    Tg, Cg, sg = g.register(p.query, p.init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+    To, Co, so = o.register(p.query, p.init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+    assert sg["status"] == 0 and so["status"] == 0
+    assert sg["iters"] == so["iters"] == 10
+    assert sg["n_src"] == so["n_src"]
+    dt, dr = pose_err(To, Tg)
+    assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (dt, dr)
+    np.testing.assert_allclose(Cg, Co, rtol=0.05, atol=1e-3 * np.abs(Co).max())
+
+
+def test_register_full_size_sequence_parity(far):
+    """128 x 2048 scans at 7 m per frame: identical maps from the first frames, then the
+    next frame registered from a constant-velocity guess with the adaptive threshold."""
+    seq = synth.TrackSequence(42)
+    poses = [seq.pose(t) for t in range(3)]
+    g, o = build_pair(far, [seq.scan(t) for t in range(3)], poses, asmd=True, r_near=10.0, r_max=200.0)
+    thr = oracle.Threshold(2.0, 0.1, 200.0)
+    tau, kappa = thr.get()
+    init = synth.constant_velocity_guess(poses[1], poses[2])
+    Tg, _, sg = g.register(seq.scan(3), init, max_iters=10, conv_eps=0.0, tau=tau, kappa=kappa)
+    To, _, so = o.register(seq.scan(3), init, max_iters=10, conv_eps=0.0, tau=tau, kappa=kappa)
+    assert sg["n_src"] == so["n_src"]
+    dt, dr = pose_err(To, Tg)
+    assert dt <= POSE_T_TOL and dr <= POSE_R_TOL, (dt, dr)
+
+
+# ------------------------------------------------------------------ edge cases and API behaviour
+def test_empty_and_tiny_inputs(far):
+    g = far.VoxelMap(0.5, 20, 5, max_voxels=1000, max_scan_points=1000)
+    assert g.insert(np.zeros((0, 3), np.float32), np.eye(4)) == 0
+    assert g.size() == (0, 0)
+    T, _, st = g.register(np.zeros((0, 3), np.float32), np.eye(4))
+    assert st["status"] == far.FAR_ERR_DEGENERATE and np.array_equal(T, np.eye(4))
+    assert g.insert(np.array([[1.0, 2.0, 3.0]], np.float32), np.eye(4)) == 1
+    ex = g.export()
+    assert ex["ids"].tolist() == [0] and ex["valid"].tolist() == [0]
+    T, _, st = g.register(np.array([[1.0, 2.0, 3.0]], np.float32), np.eye(4))
+    assert st["status"] == far.FAR_ERR_DEGENERATE
+
+
+def test_non_finite_and_out_of_range_points_are_skipped(far):
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-5, 5, size=(300, 3)).astype(np.float32)
+    pts[::11, 0] = np.nan
+    pts[::13, 1] = np.inf
+    pts[5] = [1e9, 0, 0]           # key beyond 2^20 voxels
+    pts[6] = [-524288.0, 0, 0]     # exactly the lower key limit at v = 0.5
+    g, o = build_pair(far, [pts], [np.eye(4)], max_scan=1000, max_voxels=10000)
+    assert_maps_equal(g.export(), o.export())
+
+
+def test_capacity_overflow_reports_error(far):
+    g = far.VoxelMap(0.5, 4, 2, max_voxels=8, max_scan_points=1000)
+    pts = np.random.default_rng(4).uniform(-20, 20, size=(500, 3)).astype(np.float32)
+    with pytest.raises(far.FarError) as e:
+        g.insert(pts, np.eye(4))
+    assert e.value.status == far.FAR_ERR_CAPACITY
+    assert g.size()[0] == 8
+
+
+def test_too_many_points_is_invalid(far):
+    g = far.VoxelMap(0.5, 4, 2, max_voxels=100, max_scan_points=10)
+    with pytest.raises(far.FarError) as e:
+        g.insert(np.zeros((11, 3), np.float32), np.eye(4))
+    assert e.value.status == far.FAR_ERR_INVALID
+
+
+def test_time_budget_stops_with_timeout(far, problem1, maps1):
+    g, _ = maps1
+    T, _, st = g.register(problem1.query, problem1.init, max_iters=10, tau=2.0, kappa=0.2, time_budget_s=1e-9)
+    assert st["status"] == far.FAR_ERR_TIMEOUT and st["iters"] == 1
+
+
+def test_strides_and_device_inputs_agree(far, problem1, maps1):
+    import torch
+    g, _ = maps1
+    base = g.register(problem1.query, problem1.init)[0]
+    wide = np.zeros((len(problem1.query), 10), np.float32)
+    wide[:, :3] = problem1.query
+    assert np.array_equal(g.register(wide, problem1.init)[0], base)          # 40 B stride (2D copy)
+    w4 = np.ascontiguousarray(wide[:, :4])
+    assert np.array_equal(g.register(w4, problem1.init)[0], base)            # 16 B stride
+    dev = torch.from_numpy(problem1.query).cuda()
+    assert np.array_equal(g.register(dev, problem1.init)[0], base)           # device pointer
+    assert np.array_equal(g.register(problem1.query, problem1.init)[0], base)  # deterministic
+
+
+def test_convergence_flag_stops_iterations(far, problem1, maps1):
+    g, o = maps1
+    T, _, st = g.register(problem1.query, problem1.init, max_iters=50, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+    assert st["converged"] == 1 and st["iters"] < 50
+    To, _, so = o.register(problem1.query, problem1.init, max_iters=50, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+    assert so["converged"] == 1 and so["iters"] == st["iters"]
