@@ -193,7 +193,8 @@ bool finite_pose(const double* T) {
 far_status check_points(const far_map* m, const float* xyz, uint64_t n, uint32_t stride) {
     if (!m) return fail(FAR_ERR_INVALID, "map is NULL");
     if (n > 0 && !xyz) return fail(FAR_ERR_INVALID, "xyz is NULL");
-    if (stride < 12 || stride % 4 != 0) return fail(FAR_ERR_INVALID, "stride_bytes must be >= 12 and a multiple of 4");
+    if (n > 0 && (stride < 12 || stride % 4 != 0))
+        return fail(FAR_ERR_INVALID, "stride_bytes must be >= 12 and a multiple of 4");
     if (n > m->p.max_scan_points)
         return fail(FAR_ERR_INVALID, "n = %llu exceeds max_scan_points = %u", (unsigned long long)n,
                     m->p.max_scan_points);

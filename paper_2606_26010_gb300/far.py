@@ -155,13 +155,13 @@ def _points(x):
         if isinstance(x, torch.Tensor):
             if x.dtype != torch.float32 or x.dim() != 2 or x.shape[1] < 3 or x.stride(1) != 1:
                 raise ValueError("points must be a float32 (n, >=3) tensor with unit column stride")
-            return x.data_ptr() if x.numel() else None, x.shape[0], x.stride(0) * 4, x
+            return (x.data_ptr() if x.numel() else None), x.shape[0], max(12, x.stride(0) * 4), x
     except ImportError:
         pass
     a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
     if a.ndim != 2 or a.shape[1] < 3:
         a = a.reshape(-1, 3)
-    return (a.ctypes.data if a.size else None), a.shape[0], a.strides[0], a
+    return (a.ctypes.data if a.size else None), a.shape[0], (a.strides[0] if a.shape[0] else 12), a
 
 
 def _pose(T) -> np.ndarray:
