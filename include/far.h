@@ -215,6 +215,31 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
                             const double init_pose[16], const far_reg_params* reg, const far_insert_params* ins,
                             double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result);
 
+/*
+ * far_scan_sources_static - far_scan_sources without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc - a process whose device memory is fixed before it starts (an
+ * embedded or safety partition, a memory-capped client of a shared GPU server),
+ * or a thread that must not allocate while other threads capture CUDA graphs -
+ * and therefore cannot create a far_map. It runs the same kernels (scan-local
+ * downsampling with the spacing rule, then Eq. 1 covariances from k neighbours)
+ * on one ~8 MB file-scope device array that every GPU loading the library keeps
+ * until the process exits. Limits: n <= 16384 points, max_pts_per_voxel <= 20,
+ * k_cov <= 16; larger sizes return FAR_ERR_INVALID with a message.
+ * Inputs and outputs are DEVICE pointers owned by the caller (outputs have room
+ * for n entries: index[n], cov[6 n], valid[n], knn_ids[k n] or NULL); n_src is
+ * host memory. Work runs on `cuda_stream`; the call synchronises it.
+ * The first call on a device resolves the array's address (cudaGetSymbolAddress)
+ * for that device; make that first call before any stream capture. Every call
+ * reuses the same array and resets what must start at zero, so calls whose GPU
+ * work overlaps (other streams, other host threads, one device) race and must be
+ * serialised by the caller.
+ */
+far_status far_scan_sources_static(const float* xyz, uint64_t n, uint32_t stride_bytes, float voxel_size,
+                                   uint32_t max_pts_per_voxel, uint32_t k_cov, float min_spacing, void* cuda_stream,
+                                   int64_t* out_index, float* out_cov, uint8_t* out_valid, uint32_t* out_knn_ids,
+                                   uint64_t* n_src);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* Kernel launches issued by the library since it was loaded (all maps). */

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfar.so")
-SOURCES = ["primitives.cu", "map.cu", "gicp.cu", "capi.cu"]
+SOURCES = ["primitives.cu", "map.cu", "gicp.cu", "capi.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

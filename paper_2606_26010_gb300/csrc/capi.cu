@@ -29,6 +29,12 @@ thread_local std::string g_last_error;
 enum { EV_INGEST = 0, EV_SOURCES, EV_INSERT, EV_EVICT, EV_END, EV_GN0, EV_COUNT_FIXED = EV_GN0 };
 constexpr int MAX_ITERS = 1000;
 
+}  // namespace
+
+void far::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+
 far_status fail(far_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;

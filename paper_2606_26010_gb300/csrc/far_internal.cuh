@@ -18,6 +18,8 @@ namespace far {
 
 // Host-side count of kernel launches issued by the library (all maps, all threads).
 void note_launch();
+// Set the message far_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
 // Launch a kernel and count it.
 #define FAR_LAUNCH(kernel, grid, block, smem, stream, ...)              \
     do {                                                                \

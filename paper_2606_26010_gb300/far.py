@@ -102,6 +102,8 @@ _SIGS = {
     "far_linearize": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp,
                                      _vp]),
     "far_register_scan": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "far_scan_sources_static": (ctypes.c_int, [_vp, _u64, _u32, ctypes.c_float, _u32, _u32, ctypes.c_float, _vp,
+                                               _vp, _vp, _vp, _vp, _vp]),
     "far_process_scan": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "far_launch_count": (ctypes.c_ulonglong, []),
     "far_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
