@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--max-voxels", type=int, default=MAX_VOXELS,
+                    help="bucket pool of the map (smaller values shrink the device footprint for profiling)")
     return ap.parse_args()
 
 
@@ -191,7 +193,7 @@ def run_ours(args):
 
     def make_map():
         with torch.cuda.stream(stream):
-            m = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=MAX_VOXELS, load_factor=0.5,
+            m = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=args.max_voxels, load_factor=0.5,
                              max_scan_points=MAX_SCAN, stream=stream.cuda_stream)
             m.insert(dev[0], veh.seq.pose(0), asmd=True, r_near=R_NEAR, r_max=R_MAX)
         return m
