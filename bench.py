@@ -159,8 +159,8 @@ def kernel_source_hash():
 
 
 def ncu_traffic():
-    """DRAM bytes per k_gn_iter launch from the committed ncu summary, if it matches the source."""
-    p = os.path.join(ROOT, "profiles", "k_gn_iter_hbm_128x2048.md")
+    """DRAM bytes per k_gn_lin launch from the committed ncu summary, if it matches the source."""
+    p = os.path.join(ROOT, "profiles", "k_gn_lin_hbm_128x2048.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -262,14 +262,14 @@ def run_ours(args):
     value = pts_all / dev_s_all / 1e6
     lat = np.array(step_ms)
 
-    # roofline of the dominant kernel (k_gn_iter)
+    # roofline of the dominant kernel (k_gn_lin)
     peak, peak_kind = measured_peaks()
     tot_b = sum(b * n for b, n in zip(gn_bytes, gn_launches))
     tot_t = sum(ms * n for ms, n in zip(gn_ms, gn_launches)) / 1e3
     achieved = tot_b / tot_t / 1e9 if tot_t > 0 else 0.0
     per_launch_bytes = tot_b / max(1, sum(gn_launches))
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": ncu_traffic(), "kernel": "k_gn_iter",
+                "frac": round(achieved / peak, 5), "traffic": ncu_traffic(), "kernel": "k_gn_lin",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": round(per_launch_bytes),

@@ -76,7 +76,7 @@ typedef struct far_reg_params {
     float tau;                  /* correspondence distance threshold (m) */
     float kappa;                /* Cauchy kernel scale (Eq. 5) */
     double time_budget_s;       /* wall-clock cap of one registration; <= 0 => none */
-    uint32_t threads_per_point; /* 1 (default); other values are tuning hints */
+    uint32_t threads_per_point; /* lanes that search one source point together: 1, 4, 8 or 32; 0 = default */
 } far_reg_params;
 
 typedef struct far_reg_stats {
@@ -251,12 +251,14 @@ unsigned long long far_launch_count(void);
  * Sec. IV-B, Fig. 4a). Stages: ingest (a copy of host points and packing),
  * sources (scan-local map and Eq. 1 covariances), Gauss-Newton (all launches),
  * insert (ASMD cap, admission, added-point covariances), evict.
- * gn_launch_ms is the mean duration of the launches that did work.
+ * Each Gauss-Newton iteration is a linearisation launch (search, Eq. 3-5, block
+ * sums) and a one-block solve launch (reduction, Cholesky, SE(3) update);
+ * gn_launch_ms / gn_solve_ms are their mean durations over the iterations that did work.
  */
 typedef struct far_stage_times {
     double ingest_ms, sources_ms, gauss_newton_ms, gn_launch_ms;
     uint32_t gn_launches;
-    double insert_ms, evict_ms, total_ms;
+    double insert_ms, evict_ms, total_ms, gn_solve_ms;
 } far_stage_times;
 far_status far_set_profiling(far_map* map, int enable);
 far_status far_get_stage_times(const far_map* map, far_stage_times* out);

@@ -153,7 +153,8 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     add((void**)&t->s.world, n * sizeof(float4));
     add((void**)&t->s.keys, n * sizeof(u64));
     for (u32** a : {&t->s.sk, &t->s.sv, &t->s.sk_alt, &t->s.sv_alt, &t->s.flags, &t->s.gidx, &t->s.admitted,
-                    &t->s.rank, &t->s.pos, &t->s.added, &t->s.src_index})
+                    &t->s.rank, &t->s.pos, &t->s.added, &t->s.src_index, &t->s.head_ord, &t->s.grp_cnt,
+                    &t->s.a_ord, &t->s.a_j, &t->s.dest})
         add((void**)a, (n + 1) * sizeof(u32));
     add((void**)&t->s.gstart, (n + 2) * sizeof(u32));
     add((void**)&t->s.hist, (size_t)256 * rblk * sizeof(u32));
@@ -277,10 +278,18 @@ void collect_times(far_map* m, u32 iters_done, u32 status) {
     if (m->ev_used[EV_INGEST] && m->ev_used[EV_SOURCES]) t.ingest_ms = span_ms(m, EV_INGEST, EV_SOURCES);
     if (m->ev_used[EV_SOURCES] && m->gn_launched) t.sources_ms = span_ms(m, EV_SOURCES, EV_GN0);
     if (m->gn_launched) {
-        t.gauss_newton_ms = span_ms(m, EV_GN0, EV_GN0 + m->gn_launched);
+        t.gauss_newton_ms = span_ms(m, EV_GN0, EV_GN0 + 2 * (int)m->gn_launched);
         u32 working = std::min(m->gn_launched, iters_done + (status != 0 ? 1u : 0u));
         t.gn_launches = working;
-        if (working) t.gn_launch_ms = span_ms(m, EV_GN0, EV_GN0 + working) / working;
+        double lin = 0.0, sol = 0.0;
+        for (u32 i = 0; i < working; ++i) {
+            lin += span_ms(m, EV_GN0 + 2 * (int)i, EV_GN0 + 1 + 2 * (int)i);
+            sol += span_ms(m, EV_GN0 + 1 + 2 * (int)i, EV_GN0 + 2 + 2 * (int)i);
+        }
+        if (working) {
+            t.gn_launch_ms = lin / working;
+            t.gn_solve_ms = sol / working;
+        }
     }
     if (m->ev_used[EV_INSERT] && m->ev_used[EV_EVICT]) t.insert_ms = span_ms(m, EV_INSERT, EV_EVICT);
     if (m->ev_used[EV_EVICT] && m->ev_used[EV_END]) t.evict_ms = span_ms(m, EV_EVICT, EV_END);
@@ -291,12 +300,16 @@ void collect_times(far_map* m, u32 iters_done, u32 status) {
     m->last = t;
 }
 
-// Launch the Gauss-Newton chain (max_iters launches), marking each launch when profiling.
+// Launch the Gauss-Newton chain (max_iters iterations of linearise + solve), marking the
+// start, the end of each linearisation and the end of each solve when profiling.
 far_status run_gn(far_map* m, const GnArgs& a, u32 n_upper, u32 iters) {
     mark(m, EV_GN0);
     for (u32 it = 0; it < iters; ++it) {
-        CK(gn_iteration(a, n_upper, m->stream));
-        mark(m, EV_GN0 + 1 + (int)it);
+        u32 nb = 0;
+        CK(gn_linearise(a, n_upper, m->stream, &nb));
+        mark(m, EV_GN0 + 1 + 2 * (int)it);
+        CK(gn_solve(a, nb, m->stream));
+        mark(m, EV_GN0 + 2 + 2 * (int)it);
     }
     m->gn_launched = iters;
     return FAR_OK;
@@ -318,8 +331,9 @@ far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
 }
 
 GnArgs gn_args(far_map* m, u32 n, float tau, float kappa, double conv_eps, int update, int32_t* corr,
-               double budget_s) {
+               double budget_s, int tpp = 0) {
     GnArgs a;
+    a.tpp = tpp;
     a.map = m->map.view();
     a.src = m->s.src;
     a.src_cov = m->s.src_cov;
@@ -423,7 +437,7 @@ far_status far_map_create(const far_map_params* params, void* cuda_stream, far_m
     m->local.slots_alt = nullptr;
     m->s.max_n = pl.max_n;
     m->s.staging_bytes = (size_t)pl.max_n * 32;
-    m->s.max_gn_blocks = gn_grid(pl.max_n);
+    m->s.max_gn_blocks = (u32)(gn_partials_doubles(pl.max_n) / 32);
     cudaError_t e = map_clear(m->map, m->stream);
     if (e == cudaSuccess) e = map_clear(m->local, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
@@ -677,10 +691,13 @@ far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t st
     }
     CK(gn_begin(map->s.st, pose, map->s.scal + SCAL_NADMIT, map->stream));
     GnArgs a = gn_args(map, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0);
-    CK(gn_iteration(a, std::max(nn, 1u), map->stream));
+    reset_marks(map);
+    if ((st = run_gn(map, a, std::max(nn, 1u), 1)) != FAR_OK) return st;
+    mark(map, EV_END);
     CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
     CK(cudaMemcpyAsync(map->h_scal, map->s.scal, SCAL_COUNT * sizeof(u32), cudaMemcpyDeviceToHost, map->stream));
     CK(cudaStreamSynchronize(map->stream));
+    collect_times(map, 0, 1);
     const uint64_t m = map->h_st->n_src;
     if ((st = copy_out(out_corr, map->s.i32_out, m * sizeof(int32_t), map->stream)) != FAR_OK) return st;
     CK(cudaStreamSynchronize(map->stream));
@@ -719,7 +736,7 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
     }
     CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
     GnArgs a = gn_args(map, std::max(nn, 1u), params->tau, params->kappa, params->conv_eps, 1, nullptr,
-                       params->time_budget_s);
+                       params->time_budget_s, (int)params->threads_per_point);
     if ((st = run_gn(map, a, std::max(nn, 1u), params->max_iters)) != FAR_OK) return st;
     mark(map, EV_END);
     if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
@@ -775,7 +792,8 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
         CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
     }
     CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
-    GnArgs a = gn_args(map, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr, reg->time_budget_s);
+    GnArgs a = gn_args(map, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr, reg->time_budget_s,
+                       (int)reg->threads_per_point);
     if ((st = run_gn(map, a, std::max(nn, 1u), reg->max_iters)) != FAR_OK) return st;
     if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
     mark(map, EV_INSERT);
@@ -828,7 +846,7 @@ unsigned long long far_launch_count(void) { return g_launches.load(); }
 far_status far_set_profiling(far_map* map, int enable) {
     if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
     if (enable && map->ev.empty()) {
-        map->ev.resize(EV_COUNT_FIXED + MAX_ITERS + 1, nullptr);
+        map->ev.resize(EV_COUNT_FIXED + 2 * MAX_ITERS + 1, nullptr);
         for (cudaEvent_t& e : map->ev) CK(cudaEventCreate(&e));
     }
     map->profiling = enable != 0;

@@ -80,6 +80,7 @@ struct MapView {
     u32 mask;
     u32 nmax;
     float inv_v;
+    float v;
 };
 
 // Registration state kept on the device between Gauss-Newton launches.

@@ -17,9 +17,18 @@ namespace far {
 
 namespace {
 
-constexpr int GN_THREADS = 256;
+// Threads per block and minimum resident blocks per SM of the linearisation kernel
+// (compile-time tuning knobs; 128 x 4 keeps the kernel free of register spills).
+#ifndef FAR_GN_THREADS
+#define FAR_GN_THREADS 128
+#endif
+#ifndef FAR_GN_MIN_BLOCKS
+#define FAR_GN_MIN_BLOCKS 4
+#endif
+constexpr int GN_THREADS = FAR_GN_THREADS;
 constexpr int NACC = 28;   // 21 H + 6 g + chi2
 constexpr int NPART = 32;  // doubles per block partial: 28 + n_corr + n_p2p + pad
+constexpr int kDefaultTpp = 4;  // measured fastest on the 128 x 2048 workload
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -27,70 +36,84 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// ---- FP64 6x6 Cholesky solve and SE(3) exponential (single thread) ----
-__device__ bool chol6_solve(const double* H, const double* b, double* x) {
-    double L[6][6];
+// ---- FP64 6x6 Cholesky solve and SE(3) exponential (single thread, registers only) ----
+// Every loop has constant bounds and is unrolled, so the matrices stay in registers.
+// Cholesky H = L L^T with one reciprocal square root per column (no divisions):
+// r_j = 1 / sqrt(s_j), L_jj = s_j r_j, L_ij = t_ij r_j, and the substitutions multiply by r_j.
+__device__ __forceinline__ bool chol6_solve(const double (&H)[6][6], const double (&b)[6], double (&x)[6]) {
+    double L[6][6], r[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) L[i][j] = 0.0;
     for (int j = 0; j < 6; ++j) {
-        double s = H[6 * j + j];
-        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-        if (!(s > 0.0)) return false;
-        const double d = sqrt(s);
-        L[j][j] = d;
+        double sj = H[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) sj -= L[j][k] * L[j][k];
+        if (!(sj > 0.0)) return false;
+        r[j] = rsqrt(sj);
+        L[j][j] = sj * r[j];
+#pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            double t = H[6 * i + j];
+            double t = H[i][j];
+#pragma unroll
             for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-            L[i][j] = t / d;
+            L[i][j] = t * r[j];
         }
     }
     double y[6];
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-        y[i] = s / L[i][i];
+        double t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+        y[i] = t * r[i];
     }
+#pragma unroll
     for (int i = 5; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
-        x[i] = s / L[i][i];
+        double t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t -= L[k][i] * x[k];
+        x[i] = t * r[i];
     }
     return true;
 }
 
-__device__ void se3_exp_dev(const double* xi, double* E) {
+// SE(3) exponential, xi = [phi; rho]: R = I + A K + B K^2, V = I + B K + C K^2 with
+// A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3. Below t = 0.1 the three are
+// evaluated from their Taylor series in t^2 (terms through t^10; the first omitted term is
+// below 1e-21), which needs neither sqrt nor sincos; above, from sincos.
+__device__ __forceinline__ void se3_exp_dev(const double (&xi)[6], double (&E)[12]) {
     const double px = xi[0], py = xi[1], pz = xi[2];
-    const double th2 = px * px + py * py + pz * pz;
-    const double th = sqrt(th2);
+    const double t2 = px * px + py * py + pz * pz;
     double A, B, C;
-    if (th < 1e-8) {
-        A = 1.0 - th2 / 6.0;
-        B = 0.5 - th2 / 24.0;
-        C = 1.0 / 6.0 - th2 / 120.0;
+    if (t2 < 1e-2) {
+        A = 1.0 - t2 * (1.0 / 6.0) * (1.0 - t2 * (1.0 / 20.0) * (1.0 - t2 * (1.0 / 42.0) *
+                                                                     (1.0 - t2 * (1.0 / 72.0) * (1.0 - t2 * (1.0 / 110.0)))));
+        B = 0.5 * (1.0 - t2 * (1.0 / 12.0) * (1.0 - t2 * (1.0 / 30.0) * (1.0 - t2 * (1.0 / 56.0) *
+                                                                         (1.0 - t2 * (1.0 / 90.0) * (1.0 - t2 * (1.0 / 132.0))))));
+        C = (1.0 / 6.0) * (1.0 - t2 * (1.0 / 20.0) * (1.0 - t2 * (1.0 / 42.0) * (1.0 - t2 * (1.0 / 72.0) *
+                                                                                 (1.0 - t2 * (1.0 / 110.0) * (1.0 - t2 * (1.0 / 156.0))))));
     } else {
-        double s, c;
-        sincos(th, &s, &c);
-        A = s / th;
-        B = (1.0 - c) / th2;
-        C = (th - s) / (th2 * th);
+        const double th = sqrt(t2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / t2;
+        C = (th - sn) / (t2 * th);
     }
-    const double K[3][3] = {{0, -pz, py}, {pz, 0, -px}, {-py, px, 0}};
-    double K2[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) K2[i][j] = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
+    // K^2 = phi phi^T - t2 I
+    const double K[3][3] = {{0.0, -pz, py}, {pz, 0.0, -px}, {-py, px, 0.0}};
+    const double ph[3] = {px, py, pz};
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
         double t = 0.0;
+#pragma unroll
         for (int j = 0; j < 3; ++j) {
+            const double k2 = ph[i] * ph[j] - ((i == j) ? t2 : 0.0);
             const double id = (i == j) ? 1.0 : 0.0;
-            E[4 * i + j] = id + A * K[i][j] + B * K2[i][j];
-            t += (id + B * K[i][j] + C * K2[i][j]) * xi[3 + j];
+            E[4 * i + j] = id + A * K[i][j] + B * k2;
+            t += (id + B * K[i][j] + C * k2) * xi[3 + j];
         }
         E[4 * i + 3] = t;
     }
-    E[12] = E[13] = E[14] = 0.0;
-    E[15] = 1.0;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -104,9 +127,71 @@ __device__ __forceinline__ u32 warp_sum_u(u32 v) {
     return v;
 }
 
-__global__ void __launch_bounds__(GN_THREADS) k_gn_iter(GnArgs a) {
+// Nearest map point of q (smallest (d^2, id)) searched by a group of TPP consecutive
+// lanes. The 27 voxels are taken in the order own, faces, edges, corners, in rounds of
+// TPP (lane sl takes entry round * TPP + sl); after each round the group shares its best
+// packed key (d2 bits << 32 | id, ordered like (d2, id) since d2 >= 0), and a voxel whose
+// box distance exceeds min(best, tau^2) is skipped. Candidates are loaded four at a time.
+// Every lane of the warp must call this (full-warp shuffles).
+template <int TPP>
+__device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, float qx, float qy, float qz,
+                                              float limit2, bool active, int sl, unsigned long long& best_key,
+                                              u32& best_pos) {
+    best_key = ~0ull;
+    best_pos = 0;
+    int kx = 0, ky = 0, kz = 0;
+    const bool keyed = active && voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz);
+    const FaceDist fd = face_distances(qx, qy, qz, kx, ky, kz, m.v);
+    constexpr int kRounds = (27 + TPP - 1) / TPP;
+    for (int round = 0; round < kRounds; ++round) {
+        const int v = round * TPP + sl;
+        float bound = fminf(__uint_as_float((u32)(best_key >> 32)), limit2);
+        if (best_key == ~0ull) bound = limit2;
+        if (keyed && v < 27) {
+            const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
+            const int nx = kx + dx, ny = ky + dy, nz = kz + dz;
+            u32 bucket, count;
+            if (!(box_lb2(fd, dx, dy, dz) > bound) && key_in_range(nx) && key_in_range(ny) && key_in_range(nz) &&
+                find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) {
+                const u32 base = bucket * m.nmax;
+                for (u32 j0 = 0; j0 < count; j0 += 4) {
+                    float4 c[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (j0 + u < count) {
+                            const float d2 = dist2_rn(qx, qy, qz, c[u].x, c[u].y, c[u].z);
+                            const unsigned long long key =
+                                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c[u].w);
+                            if (key < best_key) {
+                                best_key = key;
+                                best_pos = base + j0 + u;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best_key, o);
+            const u32 op = __shfl_xor_sync(0xffffffffu, best_pos, o);
+            if (ok < best_key) {
+                best_key = ok;
+                best_pos = op;
+            }
+        }
+    }
+}
+
+// Linearisation half of a Gauss-Newton iteration: TPP lanes cooperate on each source
+// point's search, the group's first lane linearises it, and every block writes its
+// partial sums (FP32 within warps, FP64 across the block's warps).
+template <int TPP>
+__global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs a) {
     __shared__ float red[GN_THREADS / 32][NACC + 2];
-    __shared__ double tot[NPART];
     __shared__ float pose_f[12];
     __shared__ u32 s_flag;
     RegState* st = a.st;
@@ -121,23 +206,39 @@ __global__ void __launch_bounds__(GN_THREADS) k_gn_iter(GnArgs a) {
     const MapView m = a.map;
     const u32 max_probe = m.ctr->max_probe;
     const u32 n = min(a.n_max, *a.n_src);
+    const int sl = threadIdx.x % TPP;
+    constexpr u32 kGroupsPerBlock = GN_THREADS / TPP;
+    const u32 group = blockIdx.x * kGroupsPerBlock + threadIdx.x / TPP;
+    const u32 warp_first = blockIdx.x * kGroupsPerBlock + (threadIdx.x & ~31u) / TPP;
+    const u32 stride = gridDim.x * kGroupsPerBlock;
 
     float acc[NACC];
 #pragma unroll
     for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
     u32 n_corr = 0, n_p2p = 0;
 
-    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 s = a.src[i];
+    for (u32 off = 0; warp_first + off < n; off += stride) {   // warp-uniform trip count
+        const u32 i = group + off;
+        const bool active = i < n;
+        const float4 s = active ? a.src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         // Eq. 2 / Eq. 6: current estimate applied to the source point
         const float qx = fmaf(R00, s.x, fmaf(R01, s.y, fmaf(R02, s.z, tx)));
         const float qy = fmaf(R10, s.x, fmaf(R11, s.y, fmaf(R12, s.z, ty)));
         const float qz = fmaf(R20, s.x, fmaf(R21, s.y, fmaf(R22, s.z, tz)));
-        float bd2;
-        u32 bid, bpos;
-        const bool any = nearest27(m, max_probe, qx, qy, qz, bd2, bid, bpos);
-        const bool ok = any && !(bd2 > a.tau2);
-        if (a.corr_out) a.corr_out[i] = ok ? (int32_t)bid : -1;
+        unsigned long long bkey = ~0ull;
+        u32 bpos = 0;
+        if constexpr (TPP == 1) {
+            float d2b;
+            u32 idb;
+            if (active && nearest27(m, max_probe, qx, qy, qz, a.tau2, d2b, idb, bpos))
+                bkey = ((unsigned long long)__float_as_uint(d2b) << 32) | idb;
+        } else {
+            group_nearest<TPP>(m, max_probe, qx, qy, qz, a.tau2, active, sl, bkey, bpos);
+        }
+        if (!active || sl != 0) continue;
+        const float bd2 = __uint_as_float((u32)(bkey >> 32));
+        const bool ok = bkey != ~0ull && !(bd2 > a.tau2);
+        if (a.corr_out) a.corr_out[__float_as_uint(s.w)] = ok ? (int32_t)(u32)bkey : -1;
         if (!ok) continue;
         const float4 r = __ldg(m.pts + bpos);
         const float4 rc0 = __ldg(m.cov + 2 * (size_t)bpos);
@@ -229,86 +330,108 @@ __global__ void __launch_bounds__(GN_THREADS) k_gn_iter(GnArgs a) {
         } else if (threadIdx.x < NACC + 2) {
             for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)__float_as_uint(red[w][threadIdx.x]);
         }
-        a.partials[(size_t)blockIdx.x * NPART + threadIdx.x] = s;
+        // value-major: partials[v * gridDim.x + block], read coalesced by the solve kernel
+        a.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const u32 ticket = atomicAdd(&st->block_counter, 1u);
-        s_flag = (ticket == gridDim.x - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (!s_flag) return;
+}
 
-    // ---- last block: fixed-order FP64 reduction of the block partials ----
-    __threadfence();
+// Solve half: one block reduces the block partials in a fixed order (FP64), then one
+// thread solves H xi = -g by Cholesky and applies T <- exp(xi) T (Eq. 6) in FP64.
+constexpr int SOLVE_THREADS = 256;
+__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) {
+    __shared__ double tot[NPART];
+    __shared__ u32 s_flag;
+    RegState* st = a.st;
+    if (threadIdx.x == 0) s_flag = *reinterpret_cast<volatile u32*>(&st->done);
+    __syncthreads();
+    if (s_flag) return;
     {
-        const int v = threadIdx.x >> 3, j = threadIdx.x & 7;  // 32 values x 8 lanes
-        double s = 0.0;
-        for (u32 b = j; b < gridDim.x; b += 8) s += __ldcg(a.partials + (size_t)b * NPART + v);
+        // warp w reduces values w, w + 8, ...: lane l sums blocks l, l + 32, ... (coalesced,
+        // four loads in flight), then a fixed shuffle tree; the order never depends on timing
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int v = warp; v < NPART; v += SOLVE_THREADS / 32) {
+            const double* col = a.partials + (size_t)v * nblocks;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            u32 b = lane;
+            for (; b + 96 < nblocks; b += 128) {
+                s0 += col[b];
+                s1 += col[b + 32];
+                s2 += col[b + 64];
+                s3 += col[b + 96];
+            }
+            for (; b < nblocks; b += 32) s0 += col[b];
+            double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (j == 0) tot[v] = s;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) tot[v] = s;
+        }
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
 
-    st->block_counter = 0;
-    double H[36], g[6];
-    {
-        int idx = 0;
-        for (int r = 0; r < 6; ++r)
-            for (int c = r; c < 6; ++c) {
-                H[6 * r + c] = tot[idx];
-                H[6 * c + r] = tot[idx];
-                ++idx;
+    double H[6][6], g[6];
+#pragma unroll
+    for (int r = 0, idx = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c, ++idx) {
+            H[r][c] = tot[idx];
+            H[c][r] = tot[idx];
+        }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) g[r] = tot[21 + r];
+    const u32 n_corr_tot = (u32)tot[28];
+    if (a.update) {
+        bool ok = n_corr_tot >= 6;
+        double mg[6], xi[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) mg[j] = -g[j];
+        if (ok) ok = chol6_solve(H, mg, xi);
+        if (ok) {
+            // Eq. 6: T <- exp(xi) T, written before the bookkeeping (the next launch waits on it)
+            double E[12];
+            se3_exp_dev(xi, E);
+            double T[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) T[j] = st->T[j];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    st->T[4 * r + c] = E[4 * r + 0] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c];
+                st->T[4 * r + 3] = E[4 * r + 0] * T[3] + E[4 * r + 1] * T[7] + E[4 * r + 2] * T[11] + E[4 * r + 3];
             }
-        for (int r = 0; r < 6; ++r) g[r] = tot[21 + r];
+            double nx = 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                st->xi[j] = xi[j];
+                nx += xi[j] * xi[j];
+            }
+            st->xi_norm = sqrt(nx);
+            st->iters += 1;
+            if (nx <= a.conv_eps * a.conv_eps) {
+                st->converged = 1;
+                st->done = 1;
+            }
+            if (a.budget_ns > 0 && globaltimer_ns() - st->t_start_ns > a.budget_ns) {
+                st->status = 6;
+                st->done = 1;
+            }
+        } else {
+            st->status = 5;
+            st->done = 1;
+        }
+    } else {
+        st->done = 1;
     }
-    for (int j = 0; j < 36; ++j) st->H[j] = H[j];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) st->H[6 * r + c] = H[r][c];
+#pragma unroll
     for (int j = 0; j < 6; ++j) st->g[j] = g[j];
     st->chi2 = tot[27];
-    st->n_corr = (u32)tot[28];
+    st->n_corr = n_corr_tot;
     st->n_p2p = (u32)tot[29];
-    if (!a.update) {
-        st->done = 1;
-        return;
-    }
-    if (st->n_corr < 6) {
-        st->status = 5;
-        st->done = 1;
-        return;
-    }
-    double mg[6], xi[6];
-    for (int j = 0; j < 6; ++j) mg[j] = -g[j];
-    if (!chol6_solve(H, mg, xi)) {
-        st->status = 5;
-        st->done = 1;
-        return;
-    }
-    double E[16], T[16], Tn[16];
-    se3_exp_dev(xi, E);
-    for (int j = 0; j < 16; ++j) T[j] = st->T[j];
-    for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c)
-            Tn[4 * r + c] = E[4 * r + 0] * T[0 + c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c] +
-                            E[4 * r + 3] * T[12 + c];
-    for (int j = 0; j < 16; ++j) st->T[j] = Tn[j];
-    double nx = 0.0;
-    for (int j = 0; j < 6; ++j) {
-        st->xi[j] = xi[j];
-        nx += xi[j] * xi[j];
-    }
-    st->xi_norm = sqrt(nx);
-    st->iters += 1;
-    if (st->xi_norm <= a.conv_eps) {
-        st->converged = 1;
-        st->done = 1;
-    }
-    if (a.budget_ns > 0 && globaltimer_ns() - st->t_start_ns > a.budget_ns) {
-        st->status = 6;
-        st->done = 1;
-    }
 }
 
 __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
@@ -328,13 +451,19 @@ __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
 
 // Output covariance: H^-1 of the last linearisation (FP64, single thread).
 __global__ void k_gn_cov(RegState* st, double* cov) {
-    double e[6], x[6];
+    double H[6][6], e[6], x[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) H[r][c] = st->H[6 * r + c];
     for (int c = 0; c < 6; ++c) {
+#pragma unroll
         for (int r = 0; r < 6; ++r) e[r] = (r == c) ? 1.0 : 0.0;
-        if (!chol6_solve(st->H, e, x)) {
+        if (!chol6_solve(H, e, x)) {
             for (int j = 0; j < 36; ++j) cov[j] = 0.0;
             return;
         }
+#pragma unroll
         for (int r = 0; r < 6; ++r) cov[6 * r + c] = x[r];
     }
 }
@@ -386,7 +515,7 @@ cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    FAR_LAUNCH(k_footprint, gn_grid(n_upper), GN_THREADS, 0, s, m, src, st, touched, out2);
+    FAR_LAUNCH(k_footprint, gn_grid(n_upper, 1), GN_THREADS, 0, s, m, src, st, touched, out2);
     return cudaGetLastError();
 }
 
@@ -395,13 +524,60 @@ cudaError_t gn_covariance(RegState* st, double* cov36, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-u32 gn_grid(u32 n_upper) {
-    u32 b = (n_upper + GN_THREADS - 1) / GN_THREADS;
-    if (b == 0) b = 1;
-    return b < 152u * 8u ? b : 152u * 8u;
+namespace {
+constexpr u32 kMaxGnBlocks = 152u * 8u;
+
+// Blocks of k_gn_lin<TPP> that fit on the device at once (one wave), at most kMaxGnBlocks.
+template <int TPP>
+u32 resident_gn_blocks() {
+    static u32 cached = 0;
+    if (cached) return cached;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gn_lin<TPP>, GN_THREADS, 0) != cudaSuccess ||
+        sms <= 0 || per_sm <= 0) {
+        cudaGetLastError();
+        return kMaxGnBlocks;
+    }
+    const u32 r = (u32)sms * (u32)per_sm;
+    cached = r < kMaxGnBlocks ? r : kMaxGnBlocks;
+    return cached;
 }
 
-size_t gn_partials_doubles(u32 n_upper) { return (size_t)gn_grid(n_upper) * NPART; }
+template <int TPP>
+u32 grid_for(u32 n_upper) {
+    const u64 groups = (u64)n_upper;
+    u64 b = (groups * TPP + GN_THREADS - 1) / GN_THREADS;
+    if (b == 0) b = 1;
+    const u32 r = resident_gn_blocks<TPP>();
+    return b < r ? (u32)b : r;
+}
+}  // namespace
+
+int gn_tpp(int requested) {
+    switch (requested) {
+        case 1: case 4: case 8: case 32: return requested;
+        default: return kDefaultTpp;
+    }
+}
+
+// One wave of resident blocks; each group of lanes strides over the source points.
+u32 gn_grid(u32 n_upper, int tpp) {
+    switch (gn_tpp(tpp)) {
+        case 4: return grid_for<4>(n_upper);
+        case 8: return grid_for<8>(n_upper);
+        case 32: return grid_for<32>(n_upper);
+        default: return grid_for<1>(n_upper);
+    }
+}
+
+// Partials for the largest grid any lanes-per-point setting can launch (32 lanes per point).
+size_t gn_partials_doubles(u32 n_upper) {
+    u64 b = ((u64)n_upper * 32 + GN_THREADS - 1) / GN_THREADS;
+    if (b == 0) b = 1;
+    return (size_t)(b < kMaxGnBlocks ? b : kMaxGnBlocks) * NPART;
+}
 
 cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s) {
     Pose16 p;
@@ -410,9 +586,28 @@ cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cuda
     return cudaGetLastError();
 }
 
-cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s) {
-    FAR_LAUNCH(k_gn_iter, gn_grid(n_upper), GN_THREADS, 0, s, a);
+cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks) {
+    const u32 g = gn_grid(n_upper, a.tpp);
+    switch (gn_tpp(a.tpp)) {
+        case 4: FAR_LAUNCH(k_gn_lin<4>, g, GN_THREADS, 0, s, a); break;
+        case 8: FAR_LAUNCH(k_gn_lin<8>, g, GN_THREADS, 0, s, a); break;
+        case 32: FAR_LAUNCH(k_gn_lin<32>, g, GN_THREADS, 0, s, a); break;
+        default: FAR_LAUNCH(k_gn_lin<1>, g, GN_THREADS, 0, s, a); break;
+    }
+    *nblocks = g;
     return cudaGetLastError();
+}
+
+cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s) {
+    FAR_LAUNCH(k_gn_solve, 1, SOLVE_THREADS, 0, s, a, nblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s) {
+    u32 nb = 0;
+    cudaError_t e = gn_linearise(a, n_upper, s, &nb);
+    if (e != cudaSuccess) return e;
+    return gn_solve(a, nb, s);
 }
 
 }  // namespace far

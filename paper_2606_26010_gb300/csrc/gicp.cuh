@@ -20,13 +20,21 @@ struct GnArgs {
     int update;                  // 0: linearise only (stage entry point)
     int32_t* corr_out;           // optional per-source correspondence ids
     unsigned long long budget_ns;  // 0: no time cap
+    int tpp;                     // lanes per source point in the search: 1, 4, 8 or 32 (other: default)
 };
 
-u32 gn_grid(u32 n_upper);
+// Supported lanes-per-point value for a request (unsupported values map to the default).
+int gn_tpp(int requested);
+u32 gn_grid(u32 n_upper, int tpp);
 size_t gn_partials_doubles(u32 n_upper);
 // Reset the registration state to `init`; n_src (device, may be null) is recorded in st->n_src.
 cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s);
+// One Gauss-Newton iteration = k_gn_lin (search, linearisation, block partials) then
+// k_gn_solve (fixed-order FP64 reduction, Cholesky, SE(3) update); both return at entry
+// once the state's stop flag is set.
 cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s);
+cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks);
+cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s);
 // Distinct map voxels (out2[0]) and their points (out2[1]) probed by the source points at st->T.
 cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st, u32* touched, u32 cap,
                          unsigned long long* out2, u32 n_upper, cudaStream_t s);

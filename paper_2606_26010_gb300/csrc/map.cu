@@ -174,6 +174,10 @@ struct AdmitArgs {
     InsertCfg cfg;
     const double* dev_T;
     u32* admitted;
+    const u32* head_ord;
+    u32* grp_cnt;
+    u32* a_ord;
+    u32* a_j;
     u32* pos;
 };
 
@@ -199,6 +203,7 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps_total) {
         const u32 start = a.gstart[g], end = a.gstart[g + 1];
         const u32 slot = a.sk[start];
+        const u32 ord = a.head_ord[a.sv[start]];
         Slot* sp = a.slots + slot;
         u32 bucket = sp->bucket;
         u32 cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
@@ -217,7 +222,10 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
                 }
             }
             b = __shfl_sync(0xffffffffu, b, 0);
-            if (b == NO_BUCKET) continue;
+            if (b == NO_BUCKET) {
+                if (lane == 0) a.grp_cnt[ord] = 0;
+                continue;
+            }
             bucket = b;
         }
         int kx, ky, kz;
@@ -228,48 +236,81 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
         float4 e1 = (lane + 32 < (int)cnt) ? bp[lane + 32] : far4;
         const u32 cnt0 = cnt;
         for (u32 w0 = start; w0 < end && cnt < cap; w0 += 32) {
+            // lane l holds candidate w0 + l and tests it against the points held at window start
             const u32 i = w0 + lane;
-            const u32 my_idx = (i < end) ? a.sv[i] : 0u;
-            const float4 my_c = (i < end) ? a.world[my_idx] : far4;
-            const u32 wn = min(32u, end - w0);
-            for (u32 j = 0; j < wn && cnt < cap; ++j) {
-                const float cx = __shfl_sync(0xffffffffu, my_c.x, j);
-                const float cy = __shfl_sync(0xffffffffu, my_c.y, j);
-                const float cz = __shfl_sync(0xffffffffu, my_c.z, j);
-                const u32 cidx = __shfl_sync(0xffffffffu, my_idx, j);
-                bool conflict = false;
-                if (lane < (int)cnt) conflict = !(dist2_rn(cx, cy, cz, e0.x, e0.y, e0.z) >= a.dmin2);
-                if (lane + 32 < (int)cnt) conflict |= !(dist2_rn(cx, cy, cz, e1.x, e1.y, e1.z) >= a.dmin2);
-                if (__any_sync(0xffffffffu, conflict)) continue;
+            const bool in_window = i < end;
+            const u32 my_idx = in_window ? a.sv[i] : 0u;
+            const float4 my_c = in_window ? a.world[my_idx] : far4;
+            bool pass = in_window;
+            for (u32 j = 0; j < cnt; ++j) {
+                const float ex = __shfl_sync(0xffffffffu, j < 32 ? e0.x : e1.x, j & 31u);
+                const float ey = __shfl_sync(0xffffffffu, j < 32 ? e0.y : e1.y, j & 31u);
+                const float ez = __shfl_sync(0xffffffffu, j < 32 ? e0.z : e1.z, j & 31u);
+                pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, ex, ey, ez) >= a.dmin2);
+            }
+            // resolve in input order: the first passing lane is admitted, later lanes are
+            // re-tested against it only (earlier lanes already failed against a subset)
+            while (cnt < cap) {
+                const u32 ballot = __ballot_sync(0xffffffffu, pass);
+                if (ballot == 0u) break;
+                const int f = __ffs(ballot) - 1;
+                const float cx = __shfl_sync(0xffffffffu, my_c.x, f);
+                const float cy = __shfl_sync(0xffffffffu, my_c.y, f);
+                const float cz = __shfl_sync(0xffffffffu, my_c.z, f);
                 const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
                 if (lane == (int)(cnt & 31u)) {
                     if (cnt < 32) e0 = c;
                     else e1 = c;
                 }
-                if (lane == 0) {
+                if (lane == f) {
                     bp[cnt] = c;
-                    a.pos[cidx] = bucket * a.nmax + cnt;
-                    a.admitted[cidx] = 1u;
+                    a.pos[my_idx] = bucket * a.nmax + cnt;
+                    a.admitted[my_idx] = 1u;
+                    a.a_ord[my_idx] = ord;
+                    a.a_j[my_idx] = cnt - cnt0;
                 }
                 ++cnt;
+                if (lane <= f) pass = false;
+                else if (pass) pass = dist2_rn(my_c.x, my_c.y, my_c.z, cx, cy, cz) >= a.dmin2;
             }
         }
-        if (lane == 0 && cnt != cnt0) sp->count = cnt;
+        if (lane == 0) {
+            if (cnt != cnt0) sp->count = cnt;
+            a.grp_cnt[ord] = cnt - cnt0;
+        }
     }
 }
 
 __global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __restrict__ rank,
-                             const u32* __restrict__ pos, u32 n, float4* pts, u32* __restrict__ added,
-                             const u32* __restrict__ scal, MapCounters* ctr) {
+                             const u32* __restrict__ pos, u32 n, float4* pts, const u32* __restrict__ scal,
+                             MapCounters* ctr) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
     const u32 base = ctr->next_id;
     const u32 r = rank[i];
     pts[pos[i]].w = __uint_as_float(base + r);
-    added[r] = pos[i];
-    if (i == 0 || r + 1 == scal[SCAL_NADMIT]) {
-        if ((unsigned long long)base + scal[SCAL_NADMIT] > 0xFFFFFFFFull) atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
-    }
+    if (r + 1 == scal[SCAL_NADMIT] && (unsigned long long)base + scal[SCAL_NADMIT] > 0xFFFFFFFFull)
+        atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
+}
+
+// Group heads: the first (smallest) input index of every voxel of the batch.
+__global__ void k_mark_heads(const u32* __restrict__ gstart, const u32* __restrict__ sv,
+                             const u32* __restrict__ scal, u32* __restrict__ head_flag) {
+    const u32 ng = scal[SCAL_NGROUPS];
+    for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        head_flag[sv[gstart[g]]] = 1u;
+}
+
+// Position of each admitted point in the grouped order and the list of added positions.
+__global__ void k_grouped_dest(const u32* __restrict__ admitted, const u32* __restrict__ a_ord,
+                               const u32* __restrict__ a_j, const u32* __restrict__ grp_base,
+                               const u32* __restrict__ pos, u32 n, u32* __restrict__ dest,
+                               u32* __restrict__ added) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !admitted[i]) return;
+    const u32 d = grp_base[a_ord[i]] + a_j[i];
+    dest[i] = d;
+    if (added) added[d] = pos[i];
 }
 
 __global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal) {
@@ -281,10 +322,11 @@ __global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal
 
 // Eq. 1 covariances of query points against map m. Queries are either q[r]
 // (q != null) or m.pts[qpos[r]]; output index is out_pos[r] (map points) or r.
+// With knn_ids, the output row of a query is its rank, taken from q[r].w.
 template <int K>
 __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __restrict__ q,
                                                  const u32* __restrict__ qpos, u32 n, const u32* __restrict__ n_dev,
-                                                 int k, float4* __restrict__ cov_out, const u32* __restrict__ out_pos,
+                                                 float4* __restrict__ cov_out, const u32* __restrict__ out_pos,
                                                  u32* __restrict__ knn_ids) {
     const u32 nn = n_dev ? min(n, *n_dev) : n;
     const u32 max_probe = m.ctr->max_probe;
@@ -292,29 +334,31 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
         const float4 p = q ? q[r] : m.pts[qpos[r]];
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, k, bd, bid, bpos);
+        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (found >= k) covariance_from_neighbours<K>(m.pts, bpos, k, p.x, p.y, p.z, c0, c1);
+        if (found >= K) covariance_from_neighbours<K>(m.pts, bpos, p.x, p.y, p.z, c0, c1);
         const u32 o = out_pos ? out_pos[r] : r;
         cov_out[2 * (size_t)o] = c0;
         cov_out[2 * (size_t)o + 1] = c1;
         if (knn_ids) {
+            const size_t row = __float_as_uint(p.w);
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (j < k) knn_ids[(size_t)r * k + j] = (j < found) ? bid[j] : NO_ID;
+            for (int j = 0; j < K; ++j) knn_ids[row * K + j] = (j < found) ? bid[j] : NO_ID;
         }
     }
 }
 
-__global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __restrict__ rank,
-                               const float4* __restrict__ in4, u32 n, float4* __restrict__ src,
-                               u32* __restrict__ src_index) {
+// Sources in voxel-grouped order: consecutive threads of the registration kernels then
+// share their 27-neighbourhoods. w carries the admission rank (the local id).
+__global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __restrict__ dest,
+                               const u32* __restrict__ rank, const float4* __restrict__ in4, u32 n,
+                               float4* __restrict__ src, u32* __restrict__ src_index) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
-    const u32 r = rank[i];
-    const float4 p = in4[i];
-    src[r] = make_float4(p.x, p.y, p.z, __uint_as_float(r));
-    src_index[r] = i;
+    const u32 d = dest[i];
+    const float4 v = in4[i];
+    src[d] = make_float4(v.x, v.y, v.z, __uint_as_float(rank[i]));
+    src_index[d] = i;
 }
 
 __global__ void k_iota(u32* a, u32 n) {
@@ -401,18 +445,17 @@ __global__ void k_gather(const float4* __restrict__ pts, const float4* __restric
 }
 
 template <int K>
-__global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __restrict__ q, u32 n, int k,
+__global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __restrict__ q, u32 n,
                                                    u32* __restrict__ ids, int32_t* __restrict__ found_out) {
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const float4 p = q[r];
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, k, bd, bid, bpos);
+        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
         found_out[r] = found;
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (j < k) ids[(size_t)r * k + j] = (j < found) ? bid[j] : NO_ID;
+        for (int j = 0; j < K; ++j) ids[(size_t)r * K + j] = (j < found) ? bid[j] : NO_ID;
     }
 }
 
@@ -423,7 +466,7 @@ __global__ void __launch_bounds__(TPB) k_nearest_stage(MapView m, const float4* 
         const float4 p = q[r];
         float bd2;
         u32 bid, bpos;
-        const bool any = nearest27(m, max_probe, p.x, p.y, p.z, bd2, bid, bpos);
+        const bool any = nearest27(m, max_probe, p.x, p.y, p.z, F_INF, bd2, bid, bpos);
         d2_out[r] = bd2;
         ids[r] = (any && !(bd2 > tau2)) ? (int64_t)bid : (int64_t)-1;
     }
@@ -433,14 +476,42 @@ template <int K>
 cudaError_t launch_knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n, const u32* n_dev,
                            float4* cov_out, const u32* out_pos, u32* knn_ids, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_knn_cov<K>, blocks_for(n), TPB, 0, st, m.view(), q, qpos, n, n_dev, (int)m.k, cov_out, out_pos, knn_ids);
+    FAR_LAUNCH(k_knn_cov<K>, blocks_for(n), TPB, 0, st, m.view(), q, qpos, n, n_dev, cov_out, out_pos, knn_ids);
     return cudaGetLastError();
 }
 
+template <int K>
+cudaError_t launch_knn_stage(const DeviceMap& m, const float4* q, u32 n, u32* ids, int32_t* found, cudaStream_t st) {
+    FAR_LAUNCH(k_knn_stage<K>, blocks_for(n), TPB, 0, st, m.view(), q, n, ids, found);
+    return cudaGetLastError();
+}
+
+// One instantiation per exact k (1..16).
+#define FAR_K_CASES(F, ...)                    \
+    switch (k) {                               \
+        case 1: return F<1>(__VA_ARGS__);      \
+        case 2: return F<2>(__VA_ARGS__);      \
+        case 3: return F<3>(__VA_ARGS__);      \
+        case 4: return F<4>(__VA_ARGS__);      \
+        case 5: return F<5>(__VA_ARGS__);      \
+        case 6: return F<6>(__VA_ARGS__);      \
+        case 7: return F<7>(__VA_ARGS__);      \
+        case 8: return F<8>(__VA_ARGS__);      \
+        case 9: return F<9>(__VA_ARGS__);      \
+        case 10: return F<10>(__VA_ARGS__);    \
+        case 11: return F<11>(__VA_ARGS__);    \
+        case 12: return F<12>(__VA_ARGS__);    \
+        case 13: return F<13>(__VA_ARGS__);    \
+        case 14: return F<14>(__VA_ARGS__);    \
+        case 15: return F<15>(__VA_ARGS__);    \
+        case 16: return F<16>(__VA_ARGS__);    \
+        default: return cudaErrorInvalidValue; \
+    }
+
 cudaError_t knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n, const u32* n_dev,
                     float4* cov_out, const u32* out_pos, u32* knn_ids, cudaStream_t st) {
-    if (m.k <= 8) return launch_knn_cov<8>(m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st);
-    return launch_knn_cov<16>(m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st);
+    const u32 k = m.k;
+    FAR_K_CASES(launch_knn_cov, m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st)
 }
 
 }  // namespace
@@ -481,6 +552,10 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
         FAR_LAUNCH(k_asmd_near, blocks_for(n), TPB, 0, st, s.gstart, s.scal, sk, m.slots, (double)m.v, cfg, dpose.T,
                                                    m.ctr);
     FAR_TRY(cudaMemsetAsync(s.admitted, 0, (size_t)n * sizeof(u32), st));
+    // voxel ordinals in first-input-index order
+    FAR_TRY(cudaMemsetAsync(s.flags, 0, (size_t)n * sizeof(u32), st));
+    FAR_LAUNCH(k_mark_heads, blocks_for(n), TPB, 0, st, s.gstart, sv, s.scal, s.flags);
+    FAR_TRY(scan_exclusive(s.flags, s.head_ord, n, nullptr, nullptr, s.partials, st));
     AdmitArgs a;
     a.sk = sk;
     a.sv = sv;
@@ -499,13 +574,20 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     a.cfg = cfg;
     a.dev_T = dpose.T;
     a.admitted = s.admitted;
+    a.head_ord = s.head_ord;
+    a.grp_cnt = s.grp_cnt;
+    a.a_ord = s.a_ord;
+    a.a_j = s.a_j;
     a.pos = s.pos;
     // one warp per group; groups <= n
     const u32 warps = min(n, 152u * 64u);
     FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
     FAR_TRY(scan_exclusive(s.admitted, s.rank, n, nullptr, s.scal + SCAL_NADMIT, s.partials, st));
-    FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.added, s.scal, m.ctr);
+    FAR_TRY(scan_exclusive(s.grp_cnt, s.grp_cnt, n, s.scal + SCAL_NGROUPS, nullptr, s.partials, st));
+    FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.scal, m.ctr);
     FAR_LAUNCH(k_finalize_insert, 1, 1, 0, st, m.ctr, s.scal);
+    FAR_LAUNCH(k_grouped_dest, blocks_for(n), TPB, 0, st, s.admitted, s.a_ord, s.a_j, s.grp_cnt, s.pos, n, s.dest,
+               (covariances && m.cov) ? s.added : nullptr);
     if (covariances && m.cov)
         FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));
     return cudaGetLastError();
@@ -513,7 +595,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
 
 cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_make_sources, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.in4, n, s.src, s.src_index);
+    FAR_LAUNCH(k_make_sources, blocks_for(n), TPB, 0, st, s.admitted, s.dest, s.rank, s.in4, n, s.src, s.src_index);
     return knn_cov(local, s.src, nullptr, n, s.scal + SCAL_NADMIT, s.src_cov, nullptr, knn_ids_out, st);
 }
 
@@ -570,11 +652,7 @@ cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts
 
 cudaError_t map_knn(const DeviceMap& m, const float4* q, u32 n, u32 k, u32* ids, int32_t* found, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    if (k <= 8)
-        FAR_LAUNCH(k_knn_stage<8>, blocks_for(n), TPB, 0, st, m.view(), q, n, (int)k, ids, found);
-    else
-        FAR_LAUNCH(k_knn_stage<16>, blocks_for(n), TPB, 0, st, m.view(), q, n, (int)k, ids, found);
-    return cudaGetLastError();
+    FAR_K_CASES(launch_knn_stage, m, q, n, ids, found, st)
 }
 
 cudaError_t map_nearest(const DeviceMap& m, const float4* q, u32 n, float tau2, int64_t* ids, float* d2,
@@ -589,13 +667,15 @@ cudaError_t map_nearest(const DeviceMap& m, const float4* q, u32 n, float tau2, 
 namespace far {
 
 namespace {
-__global__ void k_export_sources(const u32* __restrict__ src_index, const float4* __restrict__ src_cov,
-                                 const u32* __restrict__ n_dev, u32 n, int64_t* __restrict__ index,
-                                 float* __restrict__ cov6, uint8_t* __restrict__ valid) {
+// Outputs in admission-rank order (ascending input index); sources are stored voxel-grouped.
+__global__ void k_export_sources(const float4* __restrict__ src, const u32* __restrict__ src_index,
+                                 const float4* __restrict__ src_cov, const u32* __restrict__ n_dev, u32 n,
+                                 int64_t* __restrict__ index, float* __restrict__ cov6, uint8_t* __restrict__ valid) {
     const u32 nn = min(n, *n_dev);
-    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
-        index[r] = (int64_t)src_index[r];
-        const float4 c0 = src_cov[2 * (size_t)r], c1 = src_cov[2 * (size_t)r + 1];
+    for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < nn; j += gridDim.x * blockDim.x) {
+        const u32 r = __float_as_uint(src[j].w);
+        index[r] = (int64_t)src_index[j];
+        const float4 c0 = src_cov[2 * (size_t)j], c1 = src_cov[2 * (size_t)j + 1];
         float* o = cov6 + 6 * (size_t)r;
         o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c0.w; o[4] = c1.x; o[5] = c1.y;
         valid[r] = c1.z > 0.5f ? 1 : 0;
@@ -605,8 +685,8 @@ __global__ void k_export_sources(const u32* __restrict__ src_index, const float4
 
 cudaError_t export_sources(const Scratch& s, u32 n, int64_t* index, float* cov6, uint8_t* valid, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_export_sources, blocks_for(n), TPB, 0, st, s.src_index, s.src_cov, s.scal + SCAL_NADMIT, n, index, cov6,
-                                                    valid);
+    FAR_LAUNCH(k_export_sources, blocks_for(n), TPB, 0, st, s.src, s.src_index, s.src_cov, s.scal + SCAL_NADMIT, n,
+               index, cov6, valid);
     return cudaGetLastError();
 }
 

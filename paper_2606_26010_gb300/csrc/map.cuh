@@ -27,6 +27,7 @@ struct DeviceMap {
         mv.mask = mask;
         mv.nmax = nmax;
         mv.inv_v = inv_v;
+        mv.v = v;
         return mv;
     }
 };
@@ -42,6 +43,13 @@ struct Scratch {
     u32 *sk = nullptr, *sv = nullptr, *sk_alt = nullptr, *sv_alt = nullptr;
     u32 *flags = nullptr, *gidx = nullptr, *gstart = nullptr;
     u32 *admitted = nullptr, *rank = nullptr, *pos = nullptr, *added = nullptr;
+    // voxel-grouped order of the admitted points: voxels ordered by their first input index,
+    // points of a voxel in input order (deterministic, and follows the scan's spatial order)
+    u32 *head_ord = nullptr;   // by input index: ordinal of the voxel whose first candidate it is
+    u32 *grp_cnt = nullptr;    // by voxel ordinal: points admitted by this batch -> exclusive prefix
+    u32 *a_ord = nullptr;      // by input index: voxel ordinal of an admitted point
+    u32 *a_j = nullptr;        // by input index: position among the voxel's points admitted by this batch
+    u32 *dest = nullptr;       // by input index: position of an admitted point in the grouped order
     u32 *hist = nullptr, *partials = nullptr;
     u32* scal = nullptr;       // device scalars, see SCAL_*
     // registration sources
@@ -92,7 +100,8 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
                              bool covariances, cudaStream_t st, DevicePose dpose = DevicePose());
 
 // Scan-local sources after map_insert_batch on the local map: s.src / s.src_index in
-// admission order, then their covariances from the local map.
+// voxel-grouped order (s.src[j].w = admission rank), then their covariances from the
+// local map; knn_ids_out rows are indexed by rank.
 cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st);
 
 // Reset a map to empty (keys, counters, free ring).

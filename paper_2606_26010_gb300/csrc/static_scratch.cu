@@ -33,7 +33,7 @@ constexpr size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Byte offsets of every sub-buffer inside the static array.
 struct Layout {
-    size_t slots, pts, ring, ctr, in4, world, keys, u32s[11], gstart, hist, partials, scal, src, src_cov, total;
+    size_t slots, pts, ring, ctr, in4, world, keys, u32s[16], gstart, hist, partials, scal, src, src_cov, total;
 };
 
 constexpr Layout make_layout() {
@@ -51,7 +51,7 @@ constexpr Layout make_layout() {
     L.in4 = take((size_t)kStaticMaxPoints * sizeof(float4));
     L.world = take((size_t)kStaticMaxPoints * sizeof(float4));
     L.keys = take((size_t)kStaticMaxPoints * sizeof(u64));
-    for (int i = 0; i < 11; ++i) L.u32s[i] = take((size_t)(kStaticMaxPoints + 1) * sizeof(u32));
+    for (int i = 0; i < 16; ++i) L.u32s[i] = take((size_t)(kStaticMaxPoints + 1) * sizeof(u32));
     L.gstart = take((size_t)(kStaticMaxPoints + 2) * sizeof(u32));
     L.hist = take((size_t)kHistWords * sizeof(u32));
     L.partials = take((size_t)kPartialWords * sizeof(u32));
@@ -166,9 +166,9 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     s.in4 = reinterpret_cast<float4*>(base + kLayout.in4);
     s.world = reinterpret_cast<float4*>(base + kLayout.world);
     s.keys = reinterpret_cast<u64*>(base + kLayout.keys);
-    u32** u32s[11] = {&s.sk, &s.sv, &s.sk_alt, &s.sv_alt, &s.flags, &s.gidx, &s.admitted, &s.rank, &s.pos, &s.added,
-                      &s.src_index};
-    for (int i = 0; i < 11; ++i) *u32s[i] = reinterpret_cast<u32*>(base + kLayout.u32s[i]);
+    u32** u32s[16] = {&s.sk,   &s.sv,    &s.sk_alt,    &s.sv_alt,   &s.flags,   &s.gidx,  &s.admitted, &s.rank,
+                      &s.pos,  &s.added, &s.src_index, &s.head_ord, &s.grp_cnt, &s.a_ord, &s.a_j,      &s.dest};
+    for (int i = 0; i < 16; ++i) *u32s[i] = reinterpret_cast<u32*>(base + kLayout.u32s[i]);
     s.gstart = reinterpret_cast<u32*>(base + kLayout.gstart);
     s.hist = reinterpret_cast<u32*>(base + kLayout.hist);
     s.partials = reinterpret_cast<u32*>(base + kLayout.partials);

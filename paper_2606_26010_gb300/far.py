@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfar.so")
+# FAR_LIBRARY may name another build of the library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("FAR_LIBRARY") or os.path.join(_HERE, "libfar.so")
 
 FAR_OK, FAR_ERR_INVALID, FAR_ERR_OOM, FAR_ERR_CAPACITY, FAR_ERR_CUDA, FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT = range(7)
 
@@ -70,7 +71,7 @@ class StageTimes(ctypes.Structure):
     _fields_ = [("ingest_ms", ctypes.c_double), ("sources_ms", ctypes.c_double),
                 ("gauss_newton_ms", ctypes.c_double), ("gn_launch_ms", ctypes.c_double),
                 ("gn_launches", ctypes.c_uint32), ("insert_ms", ctypes.c_double), ("evict_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("gn_solve_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -303,9 +304,9 @@ class VoxelMap:
 
     # ---- registration (Sec. III-A.2)
     def register(self, xyz, init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0, time_budget_s=0.0,
-                 raise_on_degenerate=False):
+                 raise_on_degenerate=False, threads_per_point=0):
         ptr, n, stride, keep = _points(xyz)
-        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, 1)
+        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
         pose = np.zeros(16)
         cov = np.zeros(36)
         st = RegStats()
@@ -315,12 +316,12 @@ class VoxelMap:
         return pose.reshape(4, 4), cov.reshape(6, 6), st.as_dict()
 
     def process_scan(self, xyz, init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0, time_budget_s=0.0,
-                     asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0, want_cov=False):
+                     asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0, want_cov=False, threads_per_point=0):
         """Register, insert at the registered pose and evict, all on the device (one sync).
         Returns (pose 4x4, cov 6x6 or None, result dict); degenerate/timed-out scans are
         reported in result['status'] and not inserted."""
         ptr, n, stride, keep = _points(xyz)
-        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, 1)
+        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
         ins = InsertParams(int(asmd), r_near, r_max)
         pose = np.zeros(16)
         cov = np.zeros(36) if want_cov else None
