@@ -45,7 +45,7 @@ R_NEAR, R_MAX, EVICT_R = 10.0, 200.0, 150.0
 MAX_ITERS, CONV_EPS = 10, 5e-3
 SIGMA0, MIN_MOTION = 2.0, 0.1
 MAX_SCAN = 300_000
-MAX_VOXELS = 1 << 21
+MAX_VOXELS = 1 << 19        # 0.5 M voxels (10 M points at N = 20); the map holds ~0.05 M
 PRIOR_NOISE = (0.05, 0.1)   # IMU-like prior: metres, degrees per frame
 
 

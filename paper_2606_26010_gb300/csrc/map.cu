@@ -372,12 +372,27 @@ __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, do
         cy = dev_T[7];
         cz = dev_T[11];
     }
+    const float fv = (float)v, fcx = (float)cx, fcy = (float)cy, fcz = (float)cz, fr2 = (float)r2;
+    // Each FP32 centre difference is off by at most a few ulps of the largest coordinate M,
+    // so e2 is within about 8 * 2^-23 * M / r of d^2 in relative terms near the radius r;
+    // the band below is wider than that, and everything inside it takes the FP64 test.
+    const double M = fabs(cx) + fabs(cy) + fabs(cz) + sqrt(r2) + v;
+    const float band = (float)(1e-5 + 1e-6 * M / fmax(sqrt(r2), 1e-3));
+    const float lo2 = fr2 * (1.0f - band), hi2 = fr2 * (1.0f + band);
     for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
         const u64 key = slots[h].key;
         if (key >> 63) continue;  // empty or tombstone
         int kx, ky, kz;
         unpack_key(key, kx, ky, kz);
-        if (!(centre_dist2(kx, ky, kz, v, cx, cy, cz) > r2)) continue;
+        // FP32 estimate first; only distances near the radius take the exact FP64 test
+        const float ex = ((float)kx + 0.5f) * fv - fcx, ey = ((float)ky + 0.5f) * fv - fcy,
+                    ez = ((float)kz + 0.5f) * fv - fcz;
+        const float e2 = ex * ex + ey * ey + ez * ez;
+        bool far_away;
+        if (e2 < lo2) far_away = false;
+        else if (e2 > hi2) far_away = true;
+        else far_away = centre_dist2(kx, ky, kz, v, cx, cy, cz) > r2;
+        if (!far_away) continue;
         const u32 b = slots[h].bucket;
         const u32 c = slots[h].count;
         slots[h].key = KEY_TOMB;

@@ -55,32 +55,21 @@ __global__ void k_scan_reduce(const u32* __restrict__ in, u32 n, const u32* __re
     if (threadIdx.x == 0) partials[blockIdx.x] = total;
 }
 
-__global__ void k_scan_partials(u32* partials, u32 nb, u32* total_out) {
-    __shared__ u32 sw[33];
-    // each of 1024 threads owns a contiguous run of partials
-    const u32 per = (nb + blockDim.x - 1) / blockDim.x;
-    const u32 b0 = threadIdx.x * per;
-    u32 s = 0;
-    for (u32 i = 0; i < per; ++i)
-        if (b0 + i < nb) s += partials[b0 + i];
-    u32 total;
-    u32 run = block_excl_scan(s, sw, total);
-    for (u32 i = 0; i < per; ++i)
-        if (b0 + i < nb) {
-            u32 t = partials[b0 + i];
-            partials[b0 + i] = run;
-            run += t;
-        }
-    if (threadIdx.x == 0) {
-        partials[nb] = total;
-        if (total_out) *total_out = total;
-    }
-}
-
+// Downsweep: every block adds up the sums of the blocks before it (a short strided
+// sum over at most a few hundred partials) and scans its own tile; the last block also
+// writes the total. Two launches per scan, no waiting between blocks.
 __global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u32 n, const u32* __restrict__ n_dev,
-                            const u32* __restrict__ partials) {
+                            const u32* __restrict__ partials, u32 nb, u32* __restrict__ total_out) {
     __shared__ u32 sw[33];
+    __shared__ u32 s_off;
     if (n_dev) n = min(n, *n_dev);
+    u32 pre = 0;
+    for (u32 b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += partials[b];
+    u32 ptot;
+    block_excl_scan(pre, sw, ptot);
+    if (threadIdx.x == 0) s_off = ptot;
+    __syncthreads();
+    const u32 off = s_off;
     const u32 base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     u32 v[SCAN_ITEMS];
     u32 s = 0;
@@ -90,13 +79,14 @@ __global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u
         s += v[i];
     }
     u32 total;
-    u32 run = block_excl_scan(s, sw, total) + partials[blockIdx.x];
+    u32 run = block_excl_scan(s, sw, total) + off;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i)
         if (base + i < n) {
             out[base + i] = run;
             run += v[i];
         }
+    if (total_out && blockIdx.x == nb - 1 && threadIdx.x == 0) *total_out = off + total;
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -173,8 +163,7 @@ cudaError_t scan_exclusive(const u32* in, u32* out, u32 n, const u32* n_dev, u32
     if (nb == 0) nb = 1;
     if (nb > 1024u * 64u) return cudaErrorInvalidValue;
     FAR_LAUNCH(k_scan_reduce, nb, SCAN_THREADS, 0, s, in, n, n_dev, partials);
-    FAR_LAUNCH(k_scan_partials, 1, 1024, 0, s, partials, nb, total_dev);
-    FAR_LAUNCH(k_scan_down, nb, SCAN_THREADS, 0, s, in, out, n, n_dev, partials);
+    FAR_LAUNCH(k_scan_down, nb, SCAN_THREADS, 0, s, in, out, n, n_dev, partials, nb, total_dev);
     return cudaGetLastError();
 }
 

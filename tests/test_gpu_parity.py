@@ -97,6 +97,21 @@ def test_map_insert_asmd_and_evict_bit_exact_full_size(far):
     assert_maps_equal(g.export(), o.export())
 
 
+@pytest.mark.parametrize("offset", [0.0, 1.0e5])
+def test_evict_boundary_far_from_origin(far, offset):
+    """Eviction decides in FP64 exactly like the oracle, also 100 km from the origin where an
+    FP32 pre-test alone would misclassify voxels near the radius."""
+    rng = np.random.default_rng(6)
+    pts = rng.uniform(-30, 30, size=(40000, 3)).astype(np.float64)
+    pose = np.eye(4)
+    pose[:3, 3] = [offset, -0.5 * offset, 3.0]
+    g, o = build_pair(far, [pts.astype(np.float32)], [pose], nmax=8, spacing=0.0, max_scan=50_000)
+    for radius in (17.3, 25.0):
+        c = pose[:3, 3] + np.array([0.123, -0.456, 0.789])
+        assert g.evict(c, radius) == o.evict(c, radius)
+        assert_maps_equal(g.export(), o.export())
+
+
 def test_no_spacing_and_single_voxel_cap(far):
     rng = np.random.default_rng(5)
     pts = (rng.uniform(0.01, 0.49, size=(500, 3))).astype(np.float32)   # all in voxel (0,0,0)
