@@ -216,6 +216,27 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
                             double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result);
 
 /*
+ * Batched registration: many independent problems (each scan against its own map) run
+ * together. Per problem the scan-local sources are built on worker streams; then every
+ * Gauss-Newton iteration is ONE linearisation launch whose resident grid is shared by all
+ * problems (blocks in proportion to the point counts) and ONE solve launch with a block per
+ * problem; each problem stops on its own convergence flag. The whole batch is captured in
+ * a CUDA graph on the first call and replayed while the input pointers, sizes, strides,
+ * max_iters and threads_per_point stay the same (init poses, tau, kappa, conv_eps and the
+ * time budget may change between calls). Inputs must be device or pinned host memory.
+ * The batch runs on its own stream after the work already queued on `cuda_stream`, and
+ * returns when it is done. The maps are used exclusively by the batch during a call.
+ */
+typedef struct far_batch far_batch;
+far_status far_batch_create(far_map* const* maps, uint32_t count, void* cuda_stream, far_batch** out);
+far_status far_batch_destroy(far_batch* batch);
+/* xyz[i], n[i], stride_bytes[i]: problem i; init_poses / out_poses: 16 doubles per problem;
+ * stats (may be NULL): one per problem. Returns FAR_OK, or the first problem's failure. */
+far_status far_batch_register(far_batch* batch, const float* const* xyz, const uint64_t* n,
+                              const uint32_t* stride_bytes, const double* init_poses, const far_reg_params* params,
+                              double* out_poses, far_reg_stats* stats);
+
+/*
  * far_scan_sources_static - far_scan_sources without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc - a process whose device memory is fixed before it starts (an

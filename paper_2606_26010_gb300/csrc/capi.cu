@@ -841,6 +841,259 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     return res;
 }
 
+// ---------------------------------------------------------------- batched registration
+}  // extern "C"
+
+struct far_batch {
+    std::vector<far_map*> maps;
+    cudaStream_t user_stream = nullptr;   // the caller's stream: the batch starts after its prior work
+    cudaEvent_t ev_user = nullptr;
+    cudaStream_t stream = nullptr;        // own stream: graphs cannot be captured on the legacy default stream
+    std::vector<cudaStream_t> side;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    BatchProblem* d_probs = nullptr;
+    BatchProblem* h_probs = nullptr;       // pinned mirror, copied by the graph each launch
+    unsigned short* d_block_prob = nullptr;
+    double* d_init = nullptr;
+    double* h_init = nullptr;              // pinned
+    RegState* d_states = nullptr;
+    RegState* h_states = nullptr;          // pinned
+    u32 total_blocks = 0;
+    cudaGraphExec_t exec = nullptr;
+    // what the captured graph was built for
+    std::vector<const void*> key_ptr;
+    std::vector<uint64_t> key_n;
+    std::vector<uint32_t> key_stride;
+    uint32_t key_iters = 0;
+    int key_tpp = -1;
+};
+
+namespace {
+
+void batch_release(far_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_user) cudaEventDestroy(b->ev_user);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaFree(b->d_probs);
+    cudaFree(b->d_block_prob);
+    cudaFree(b->d_init);
+    cudaFree(b->d_states);
+    cudaFreeHost(b->h_probs);
+    cudaFreeHost(b->h_init);
+    cudaFreeHost(b->h_states);
+}
+
+bool is_registered_or_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost;
+}
+
+// Record the whole batch (sources of every problem on worker streams, then the batched
+// Gauss-Newton chain and the state gather on the main stream) into a CUDA graph.
+far_status batch_capture(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
+                         uint32_t iters, int tpp) {
+    const u32 np = (u32)b->maps.size();
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    // share of the resident grid for each problem, by point count
+    const u32 resident = gn_batch_resident_blocks(tpp);
+    const u32 gt = gn_threads_per_block();
+    double sum_n = 0;
+    for (u32 p = 0; p < np; ++p) sum_n += (double)std::max<uint64_t>(n[p], 1);
+    std::vector<unsigned short> block_prob;
+    for (u32 p = 0; p < np; ++p) {
+        far_map* m = b->maps[p];
+        const u64 n_up = std::max<uint64_t>(n[p], 1);
+        const u32 need = (u32)std::min<u64>((n_up * (u64)gn_tpp(tpp) + gt - 1) / gt, 65535);
+        const u32 alloc = (u32)(gn_partials_doubles(m->p.max_scan_points) / 32);
+        u32 share = (u32)std::llround(resident * (double)n_up / sum_n);
+        share = std::max(1u, std::min({share, need, alloc}));
+        BatchProblem& bp = b->h_probs[p];
+        bp.block_begin = (u32)block_prob.size();
+        bp.nblocks = share;
+        for (u32 j = 0; j < share; ++j) block_prob.push_back((unsigned short)p);
+    }
+    if (block_prob.size() > 65535) return fail(FAR_ERR_INVALID, "batch grid too large");
+    b->total_blocks = (u32)block_prob.size();
+    cudaFree(b->d_block_prob);
+    b->d_block_prob = nullptr;
+    CK(cudaMalloc(&b->d_block_prob, block_prob.size() * sizeof(unsigned short)));
+    CK(cudaMemcpy(b->d_block_prob, block_prob.data(), block_prob.size() * sizeof(unsigned short),
+                  cudaMemcpyHostToDevice));
+
+    // the maps' own streams are swapped for the batch's worker streams during the capture
+    std::vector<cudaStream_t> saved(np);
+    for (u32 p = 0; p < np; ++p) saved[p] = b->maps[p]->stream;
+    auto restore = [&]() {
+        for (u32 p = 0; p < np; ++p) b->maps[p]->stream = saved[p];
+    };
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    far_status st = FAR_OK;
+    cudaError_t e = cudaMemcpyAsync(b->d_probs, b->h_probs, np * sizeof(BatchProblem), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_init, b->h_init, np * 16 * sizeof(double), cudaMemcpyHostToDevice,
+                                              b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+    for (size_t i = 0; e == cudaSuccess && i < b->side.size(); ++i) e = cudaStreamWaitEvent(b->side[i], b->ev_fork, 0);
+    for (u32 p = 0; e == cudaSuccess && st == FAR_OK && p < np; ++p) {
+        far_map* m = b->maps[p];
+        m->stream = b->side[p % b->side.size()];
+        const u32 nn = (u32)n[p];
+        if ((st = ingest(m, xyz[p], nn, stride[p])) != FAR_OK) break;
+        if (nn) {
+            if ((st = build_sources(m, nn, nullptr)) != FAR_OK) break;
+        } else {
+            e = cudaMemsetAsync(m->s.scal, 0, SCAL_COUNT * sizeof(u32), m->stream);
+        }
+    }
+    for (size_t i = 0; e == cudaSuccess && st == FAR_OK && i < b->side.size(); ++i) {
+        e = cudaEventRecord(b->ev_join[i], b->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[i], 0);
+    }
+    restore();
+    if (e == cudaSuccess && st == FAR_OK) e = gn_batch_begin(b->d_probs, np, b->d_init, b->stream);
+    for (u32 it = 0; e == cudaSuccess && st == FAR_OK && it < iters; ++it)
+        e = gn_batch_iteration(b->d_probs, b->d_block_prob, b->total_blocks, np, tpp, b->stream);
+    if (e == cudaSuccess && st == FAR_OK) e = gn_batch_gather(b->d_probs, np, b->d_states, b->stream);
+    if (e == cudaSuccess && st == FAR_OK)
+        e = cudaMemcpyAsync(b->h_states, b->d_states, np * sizeof(RegState), cudaMemcpyDeviceToHost, b->stream);
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+    if (st != FAR_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FAR_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    }
+    b->key_ptr.assign(xyz, xyz + np);
+    b->key_n.assign(n, n + np);
+    b->key_stride.assign(stride, stride + np);
+    b->key_iters = iters;
+    b->key_tpp = tpp;
+    return FAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+far_status far_batch_create(far_map* const* maps, uint32_t count, void* cuda_stream, far_batch** out) {
+    if (!maps || !out || count == 0 || count > 4096) return fail(FAR_ERR_INVALID, "maps/out NULL or count not in 1..4096");
+    for (uint32_t i = 0; i < count; ++i) {
+        if (!maps[i]) return fail(FAR_ERR_INVALID, "maps[%u] is NULL", i);
+        for (uint32_t j = 0; j < i; ++j)
+            if (maps[j] == maps[i]) return fail(FAR_ERR_INVALID, "a map appears twice in the batch");
+    }
+    far_batch* b = new far_batch();
+    b->maps.assign(maps, maps + count);
+    b->user_stream = static_cast<cudaStream_t>(cuda_stream);
+    const u32 nside = std::min<u32>(count, 8);
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    for (u32 i = 0; e == cudaSuccess && i < nside; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->side.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->ev_join.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, count * sizeof(BatchProblem));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_init, count * 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_states, count * sizeof(RegState));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_probs, count * sizeof(BatchProblem));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_init, count * 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_states, count * sizeof(RegState));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_release(b);
+        delete b;
+        return fail(FAR_ERR_OOM, "batch allocation failed: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return FAR_OK;
+}
+
+far_status far_batch_destroy(far_batch* batch) {
+    if (!batch) return fail(FAR_ERR_INVALID, "batch is NULL");
+    batch_release(batch);
+    delete batch;
+    return FAR_OK;
+}
+
+far_status far_batch_register(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
+                              const double* init_poses, const far_reg_params* params, double* out_poses,
+                              far_reg_stats* stats) {
+    if (!b || !xyz || !n || !stride || !init_poses || !params || !out_poses)
+        return fail(FAR_ERR_INVALID, "NULL argument");
+    if (!(params->kappa > 0.0f) || !(params->tau >= 0.0f) || params->max_iters > 1000)
+        return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000");
+    const u32 np = (u32)b->maps.size();
+    for (u32 p = 0; p < np; ++p) {
+        far_status st = check_points(b->maps[p], xyz[p], n[p], stride[p]);
+        if (st != FAR_OK) return st;
+        if (n[p] && !is_registered_or_device(xyz[p]))
+            return fail(FAR_ERR_INVALID, "batch inputs must be device or pinned host memory (problem %u)", p);
+        if (!finite_pose(init_poses + 16 * (size_t)p)) return fail(FAR_ERR_INVALID, "init pose %u not finite", p);
+    }
+    const int tpp = gn_tpp((int)params->threads_per_point);
+    // per-call arguments, read by the graph from the pinned mirrors
+    for (u32 p = 0; p < np; ++p) {
+        far_map* m = b->maps[p];
+        const u32 n_up = (u32)std::max<uint64_t>(n[p], 1);
+        b->h_probs[p].args = gn_args(m, n_up, params->tau, params->kappa, params->conv_eps, 1, nullptr,
+                                     params->time_budget_s, tpp);
+    }
+    std::memcpy(b->h_init, init_poses, np * 16 * sizeof(double));
+    bool same = b->exec && b->key_iters == params->max_iters && b->key_tpp == tpp;
+    for (u32 p = 0; same && p < np; ++p)
+        same = b->key_ptr[p] == (const void*)xyz[p] && b->key_n[p] == n[p] && b->key_stride[p] == stride[p];
+    if (!same) {
+        far_status st = batch_capture(b, xyz, n, stride, params->max_iters, tpp);
+        if (st != FAR_OK) return st;
+    }
+    CK(cudaEventRecord(b->ev_user, b->user_stream));
+    CK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+    CK(cudaGraphLaunch(b->exec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    far_status worst = FAR_OK;
+    for (u32 p = 0; p < np; ++p) {
+        const RegState& r = b->h_states[p];
+        std::memcpy(out_poses + 16 * (size_t)p, r.T, 16 * sizeof(double));
+        far_status sp = r.status == 5 ? FAR_ERR_DEGENERATE : (r.status == 6 ? FAR_ERR_TIMEOUT : FAR_OK);
+        if (sp != FAR_OK && worst == FAR_OK) worst = sp;
+        if (stats) {
+            stats[p].iters = r.iters;
+            stats[p].n_src = r.n_src;
+            stats[p].n_corr = r.n_corr;
+            stats[p].n_p2p = r.n_p2p;
+            stats[p].converged = (int32_t)r.converged;
+            stats[p].status = sp;
+            stats[p].chi2 = r.chi2;
+        }
+    }
+    if (worst != FAR_OK) return fail(worst, "at least one problem of the batch did not register (see stats)");
+    return FAR_OK;
+}
+
 unsigned long long far_launch_count(void) { return g_launches.load(); }
 
 far_status far_set_profiling(far_map* map, int enable) {

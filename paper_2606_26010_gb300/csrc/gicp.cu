@@ -190,7 +190,7 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, f
 // point's search, the group's first lane linearises it, and every block writes its
 // partial sums (FP32 within warps, FP64 across the block's warps).
 template <int TPP>
-__global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs a) {
+__device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vgrid) {
     __shared__ float red[GN_THREADS / 32][NACC + 2];
     __shared__ float pose_f[12];
     __shared__ u32 s_flag;
@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs
     const u32 n = min(a.n_max, *a.n_src);
     const int sl = threadIdx.x % TPP;
     constexpr u32 kGroupsPerBlock = GN_THREADS / TPP;
-    const u32 group = blockIdx.x * kGroupsPerBlock + threadIdx.x / TPP;
-    const u32 warp_first = blockIdx.x * kGroupsPerBlock + (threadIdx.x & ~31u) / TPP;
-    const u32 stride = gridDim.x * kGroupsPerBlock;
+    const u32 group = vblock * kGroupsPerBlock + threadIdx.x / TPP;
+    const u32 warp_first = vblock * kGroupsPerBlock + (threadIdx.x & ~31u) / TPP;
+    const u32 stride = vgrid * kGroupsPerBlock;
 
     float acc[NACC];
 #pragma unroll
@@ -330,15 +330,29 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs
         } else if (threadIdx.x < NACC + 2) {
             for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)__float_as_uint(red[w][threadIdx.x]);
         }
-        // value-major: partials[v * gridDim.x + block], read coalesced by the solve kernel
-        a.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+        // value-major: partials[v * blocks + block], read coalesced by the solve kernel
+        a.partials[(size_t)threadIdx.x * vgrid + vblock] = s;
     }
+}
+
+template <int TPP>
+__global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs a) {
+    gn_lin_block<TPP>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched linearisation: the grid is shared by all problems; block b works for problem
+// block_prob[b] as its (b - block_begin)-th block of nblocks.
+template <int TPP>
+__global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(const BatchProblem* __restrict__ probs,
+                                                                                const unsigned short* __restrict__ block_prob) {
+    const BatchProblem& p = probs[block_prob[blockIdx.x]];
+    gn_lin_block<TPP>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
 
 // Solve half: one block reduces the block partials in a fixed order (FP64), then one
 // thread solves H xi = -g by Cholesky and applies T <- exp(xi) T (Eq. 6) in FP64.
 constexpr int SOLVE_THREADS = 256;
-__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) {
+__device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
     __shared__ double tot[NPART];
     __shared__ u32 s_flag;
     RegState* st = a.st;
@@ -432,6 +446,42 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblock
     st->chi2 = tot[27];
     st->n_corr = n_corr_tot;
     st->n_p2p = (u32)tot[29];
+}
+
+__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) { gn_solve_block(a, nblocks); }
+
+// Batched solve: block p reduces and solves problem p.
+__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_batch(const BatchProblem* __restrict__ probs) {
+    const BatchProblem& p = probs[blockIdx.x];
+    gn_solve_block(p.args, p.nblocks);
+}
+
+// Reset every problem's state to its initial pose (init: 16 doubles per problem).
+__global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 nprob, const double* __restrict__ init) {
+    const u32 p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    RegState* st = probs[p].args.st;
+    for (int j = 0; j < 16; ++j) st->T[j] = init[16 * (size_t)p + j];
+    for (int j = 0; j < 36; ++j) st->H[j] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        st->g[j] = 0.0;
+        st->xi[j] = 0.0;
+    }
+    st->chi2 = 0.0;
+    st->xi_norm = 0.0;
+    st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
+    st->block_counter = 0;
+    st->n_src = *probs[p].args.n_src;
+    st->t_start_ns = globaltimer_ns();
+}
+
+// Copy every problem's state into one array (one device-to-host copy afterwards).
+__global__ void k_gather_states(const BatchProblem* __restrict__ probs, u32 nprob, RegState* __restrict__ out) {
+    const u32 p = blockIdx.x;
+    if (p >= nprob) return;
+    const u32* src = reinterpret_cast<const u32*>(probs[p].args.st);
+    u32* dst = reinterpret_cast<u32*>(out + p);
+    for (u32 j = threadIdx.x; j < sizeof(RegState) / 4; j += blockDim.x) dst[j] = src[j];
 }
 
 __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
@@ -602,6 +652,39 @@ cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s) {
     FAR_LAUNCH(k_gn_solve, 1, SOLVE_THREADS, 0, s, a, nblocks);
     return cudaGetLastError();
 }
+
+u32 gn_batch_resident_blocks(int tpp) {
+    switch (gn_tpp(tpp)) {
+        case 4: return resident_gn_blocks<4>();
+        case 8: return resident_gn_blocks<8>();
+        case 32: return resident_gn_blocks<32>();
+        default: return resident_gn_blocks<1>();
+    }
+}
+
+cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* init, cudaStream_t s) {
+    FAR_LAUNCH(k_gn_begin_batch, (nprob + 127) / 128, 128, 0, s, probs, nprob, init);
+    return cudaGetLastError();
+}
+
+cudaError_t gn_batch_iteration(const BatchProblem* probs, const unsigned short* block_prob, u32 total_blocks, u32 nprob,
+                               int tpp, cudaStream_t s) {
+    switch (gn_tpp(tpp)) {
+        case 4: FAR_LAUNCH(k_gn_lin_batch<4>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
+        case 8: FAR_LAUNCH(k_gn_lin_batch<8>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
+        case 32: FAR_LAUNCH(k_gn_lin_batch<32>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
+        default: FAR_LAUNCH(k_gn_lin_batch<1>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
+    }
+    FAR_LAUNCH(k_gn_solve_batch, nprob, SOLVE_THREADS, 0, s, probs);
+    return cudaGetLastError();
+}
+
+cudaError_t gn_batch_gather(const BatchProblem* probs, u32 nprob, RegState* out, cudaStream_t s) {
+    FAR_LAUNCH(k_gather_states, nprob, 128, 0, s, probs, nprob, out);
+    return cudaGetLastError();
+}
+
+u32 gn_threads_per_block() { return GN_THREADS; }
 
 cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s) {
     u32 nb = 0;

@@ -23,6 +23,22 @@ struct GnArgs {
     int tpp;                     // lanes per source point in the search: 1, 4, 8 or 32 (other: default)
 };
 
+// One problem of a batched registration: its arguments and its share of the shared grid.
+struct BatchProblem {
+    GnArgs args;
+    u32 block_begin;   // first block of the batched linearisation grid owned by this problem
+    u32 nblocks;       // number of blocks it owns (its partials hold nblocks entries per value)
+};
+
+// Batched Gauss-Newton: one linearisation launch and one solve launch per iteration for all
+// problems; every problem stops on its own flag.
+u32 gn_batch_resident_blocks(int tpp);
+u32 gn_threads_per_block();
+cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* init, cudaStream_t s);
+cudaError_t gn_batch_iteration(const BatchProblem* probs, const unsigned short* block_prob, u32 total_blocks, u32 nprob,
+                               int tpp, cudaStream_t s);
+cudaError_t gn_batch_gather(const BatchProblem* probs, u32 nprob, RegState* out, cudaStream_t s);
+
 // Supported lanes-per-point value for a request (unsupported values map to the default).
 int gn_tpp(int requested);
 u32 gn_grid(u32 n_upper, int tpp);

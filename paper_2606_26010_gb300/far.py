@@ -107,6 +107,9 @@ _SIGS = {
                                                _vp, _vp, _vp, _vp, _vp]),
     "far_process_scan": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "far_launch_count": (ctypes.c_ulonglong, []),
+    "far_batch_create": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
+    "far_batch_destroy": (ctypes.c_int, [_vp]),
+    "far_batch_register": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "far_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "far_get_stage_times": (ctypes.c_int, [_vp, _vp]),
     "far_gn_footprint": (ctypes.c_int, [_vp, _vp]),
@@ -345,6 +348,49 @@ class VoxelMap:
         out = np.zeros(3, np.uint64)
         _check(self._L.far_gn_footprint(self._h, _p(out)))
         return int(out[0]), int(out[1]), int(out[2])
+
+
+class Batch:
+    """Batched registration of several maps in one CUDA graph (far_batch_*)."""
+
+    def __init__(self, maps, stream=None):
+        self._L = lib()
+        self.maps = list(maps)
+        self.stream = (self.maps[0].stream if stream is None else stream)
+        arr = (ctypes.c_void_p * len(self.maps))(*[m.handle.value for m in self.maps])
+        h = ctypes.c_void_p(0)
+        _check(self._L.far_batch_create(arr, len(self.maps), self.stream, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.far_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, scans, inits, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0, time_budget_s=0.0,
+                 threads_per_point=0):
+        """scans: device tensors or pinned host tensors (n_i, >=3); inits: (B, 4, 4).
+        Returns (poses (B, 4, 4), list of stats dicts)."""
+        B = len(self.maps)
+        assert len(scans) == B and len(inits) == B
+        infos = [_points(s) for s in scans]
+        ptrs = (ctypes.c_void_p * B)(*[i[0] for i in infos])
+        ns = (ctypes.c_uint64 * B)(*[i[1] for i in infos])
+        strides = (ctypes.c_uint32 * B)(*[i[2] for i in infos])
+        init = np.ascontiguousarray(np.asarray(inits, np.float64).reshape(B, 16))
+        out = np.zeros((B, 16))
+        stats = (RegStats * B)()
+        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
+        _check(self._L.far_batch_register(self._h, ptrs, ns, strides, _p(init), ctypes.byref(prm), _p(out), stats),
+               allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
+        return out.reshape(B, 4, 4), [st.as_dict() for st in stats]
 
 
 def launch_count() -> int:
