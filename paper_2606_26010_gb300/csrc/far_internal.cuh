@@ -126,9 +126,19 @@ __device__ __forceinline__ void unpack_key(u64 k, int& kx, int& ky, int& kz) {
     kz = (int)(k & 0x1FFFFF) - KEY_BIAS;
 }
 
-// Spatial hash of Teschner/Niessner (primes 73856093, 19349669, 83492791) on the voxel indices.
+// Spatial hash of Teschner/Niessner (primes 73856093, 19349669, 83492791) on the voxel
+// indices, followed by the MurmurHash3 32-bit finalizer: the XOR of products alone leaves
+// neighbouring voxels in clusters of the low bits, which lengthens linear-probing runs in a
+// power-of-two table. The finalizer is a bijection, so distinct hashes stay distinct; only
+// slot placement changes, never a result.
 __device__ __forceinline__ u32 hash_key(int kx, int ky, int kz) {
-    return ((u32)kx * 73856093u) ^ ((u32)ky * 19349669u) ^ ((u32)kz * 83492791u);
+    u32 h = ((u32)kx * 73856093u) ^ ((u32)ky * 19349669u) ^ ((u32)kz * 83492791u);
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
 }
 
 // Candidate distance reading: ((dx*dx + dy*dy) + dz*dz), FP32 round-to-nearest, no contraction.

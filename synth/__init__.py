@@ -315,3 +315,51 @@ class TrackSequence:
 def constant_velocity_guess(prev2: np.ndarray, prev1: np.ndarray) -> np.ndarray:
     """T_{t} ~= T_{t-1} (T_{t-2}^-1 T_{t-1})."""
     return prev1 @ (np.linalg.inv(prev2) @ prev1)
+
+
+# ---- many independent problems of uneven size ------------------------------------------
+@dataclass
+class BatchProblemSpec:
+    """One registration problem of a batch: the map is built from prior scans of the
+    shared track sequence (indices map_idx, nearest frame first, true poses), the query
+    comes from its own sensor."""
+    lidar: Lidar
+    map_idx: list
+    query: np.ndarray
+    truth: np.ndarray
+    init: np.ndarray
+    target_map_points: int
+
+
+def sensor_for_points(rng: np.random.Generator, n_target: float) -> Lidar:
+    """A 16/32/64/128-beam sensor whose azimuth count gives about n_target points."""
+    fits = [b for b in (16, 32, 64, 128) if b * 4096 * 0.85 >= n_target]
+    beams = int(rng.choice(fits[:2] if len(fits) > 1 else fits))
+    base = lidar_beams(beams)
+    az = int(np.clip(round(n_target / (beams * 0.85) / 32) * 32, 256, 4096))
+    return Lidar(beams, az, base.el_min_deg, base.el_max_deg, base.r_min, base.r_max, base.sigma)
+
+
+def batched_problems(seed: int = 7, count: int = 64, scan_range=(5e3, 3e5), map_range=(1e5, 3e6),
+                     max_prior: int = 80, sequence: "TrackSequence | None" = None):
+    """Problems with log-uniform scan sizes (mixed 16/32/64/128-beam sensors) and log-uniform
+    map targets, placed at random positions of the oval; priors are the preceding frames."""
+    seq = sequence or TrackSequence(seed=42)
+    rng = np.random.default_rng(seed)
+    lap = int(TRACK_LENGTH // seq.step)
+    out = []
+    for i in range(count):
+        n_scan = math.exp(rng.uniform(math.log(scan_range[0]), math.log(scan_range[1])))
+        n_map = math.exp(rng.uniform(math.log(map_range[0]), math.log(map_range[1])))
+        lidar = sensor_for_points(rng, n_scan)
+        q_idx = int(rng.integers(max_prior + 1, max_prior + 1 + lap))
+        truth = seq.pose(q_idx)
+        query = raycast(seq.scene, lidar, truth, seq.seed + 7919 * (i + 1), 10_000 + i)
+        if len(query) > scan_range[1]:   # keep within the size range: drop points evenly
+            keep = np.linspace(0, len(query) - 1, int(scan_range[1])).astype(np.int64)
+            query = np.ascontiguousarray(query[keep])
+        init = truth @ random_offset(rng, 2.0, 0.5)
+        # prior frames nearest to the query first, so that a map stopped at its target size overlaps the query
+        out.append(BatchProblemSpec(lidar, list(range(q_idx - 1, q_idx - max_prior - 1, -1)), query, truth, init,
+                                    int(n_map)))
+    return seq, out
