@@ -231,10 +231,22 @@ typedef struct far_batch far_batch;
 far_status far_batch_create(far_map* const* maps, uint32_t count, void* cuda_stream, far_batch** out);
 far_status far_batch_destroy(far_batch* batch);
 /* xyz[i], n[i], stride_bytes[i]: problem i; init_poses / out_poses: 16 doubles per problem;
- * stats (may be NULL): one per problem. Returns FAR_OK, or the first problem's failure. */
+ * params: one set for all (params_count = 1) or one per problem (params_count = count; their
+ * max_iters and threads_per_point must agree); stats (may be NULL): one per problem.
+ * Returns FAR_OK, or the first problem's failure. */
 far_status far_batch_register(far_batch* batch, const float* const* xyz, const uint64_t* n,
                               const uint32_t* stride_bytes, const double* init_poses, const far_reg_params* params,
-                              double* out_poses, far_reg_stats* stats);
+                              uint32_t params_count, double* out_poses, far_reg_stats* stats);
+/*
+ * The whole per-scan step (far_process_scan) for every problem of the batch at once:
+ * batched registration, then each scan inserted into its map at its registered pose (kept on
+ * the device) and eviction around it, on worker streams. Issued directly (no graph), so the
+ * sizes and inputs may change on every call (a serving loop). results: one per problem.
+ */
+far_status far_batch_process(far_batch* batch, const float* const* xyz, const uint64_t* n,
+                             const uint32_t* stride_bytes, const double* init_poses, const far_reg_params* params,
+                             uint32_t params_count, const far_insert_params* ins, double evict_radius,
+                             double* out_poses, far_step_result* results);
 
 /*
  * far_scan_sources_static - far_scan_sources without any device allocation.

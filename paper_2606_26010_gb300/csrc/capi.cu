@@ -850,15 +850,18 @@ struct far_batch {
     cudaEvent_t ev_user = nullptr;
     cudaStream_t stream = nullptr;        // own stream: graphs cannot be captured on the legacy default stream
     std::vector<cudaStream_t> side;
-    cudaEvent_t ev_fork = nullptr;
-    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr;
+    std::vector<cudaEvent_t> ev_join, ev_join2;
     BatchProblem* d_probs = nullptr;
-    BatchProblem* h_probs = nullptr;       // pinned mirror, copied by the graph each launch
-    unsigned short* d_block_prob = nullptr;
+    BatchProblem* h_probs = nullptr;       // pinned mirror, copied in stream order each launch
+    u32* d_block_prob = nullptr;
+    u32* h_block_prob = nullptr;           // pinned mirror
+    u32 max_blocks = 0;                    // capacity of the block -> problem table
     double* d_init = nullptr;
     double* h_init = nullptr;              // pinned
     RegState* d_states = nullptr;
     RegState* h_states = nullptr;          // pinned
+    MapCounters* h_ctr = nullptr;          // pinned, one per problem (process mode)
     u32 total_blocks = 0;
     cudaGraphExec_t exec = nullptr;
     // what the captured graph was built for
@@ -877,7 +880,9 @@ void batch_release(far_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_join2) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_fork2) cudaEventDestroy(b->ev_fork2);
     if (b->ev_user) cudaEventDestroy(b->ev_user);
     if (b->stream) cudaStreamDestroy(b->stream);
     cudaFree(b->d_probs);
@@ -885,8 +890,10 @@ void batch_release(far_batch* b) {
     cudaFree(b->d_init);
     cudaFree(b->d_states);
     cudaFreeHost(b->h_probs);
+    cudaFreeHost(b->h_block_prob);
     cudaFreeHost(b->h_init);
     cudaFreeHost(b->h_states);
+    cudaFreeHost(b->h_ctr);
 }
 
 bool is_registered_or_device(const void* p) {
@@ -898,8 +905,104 @@ bool is_registered_or_device(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost;
 }
 
-// Record the whole batch (sources of every problem on worker streams, then the batched
-// Gauss-Newton chain and the state gather on the main stream) into a CUDA graph.
+// Each problem gets exactly the linearisation grid that the single-problem path launches
+// for it (gn_grid of its point count), so its block partials, their reduction order and its
+// result are bit-identical alone and in any mix; the blocks of all problems share one launch.
+far_status batch_assign_blocks(far_batch* b, const uint64_t* n, int tpp) {
+    const u32 np = (u32)b->maps.size();
+    u32 total = 0;
+    for (u32 p = 0; p < np; ++p) {
+        const u32 n_up = (u32)std::max<uint64_t>(n[p], 1);
+        const u32 share = gn_grid(n_up, tpp);
+        if ((u64)total + share > b->max_blocks) return fail(FAR_ERR_INVALID, "batch grid larger than its table");
+        BatchProblem& bp = b->h_probs[p];
+        bp.block_begin = total;
+        bp.nblocks = share;
+        for (u32 j = 0; j < share; ++j) b->h_block_prob[total + j] = p;
+        total += share;
+    }
+    b->total_blocks = total;
+    return FAR_OK;
+}
+
+// Issue a batch on the batch's streams: sources of every problem on worker streams, the
+// batched Gauss-Newton chain on the main stream, optionally (ins != null) the insert of each
+// scan at its registered pose and the eviction on worker streams, then the state gather.
+far_status batch_enqueue(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
+                         uint32_t iters, int tpp, const InsertCfg* ins, double evict_radius) {
+    const u32 np = (u32)b->maps.size();
+    std::vector<cudaStream_t> saved(np);
+    for (u32 p = 0; p < np; ++p) saved[p] = b->maps[p]->stream;
+    struct Restore {
+        far_batch* b;
+        std::vector<cudaStream_t>& saved;
+        ~Restore() {
+            for (size_t p = 0; p < saved.size(); ++p) b->maps[p]->stream = saved[p];
+        }
+    } restore{b, saved};
+    // larger problems first, each to the worker stream with the least work so far
+    std::vector<u32> order(np);
+    for (u32 p = 0; p < np; ++p) order[p] = p;
+    std::sort(order.begin(), order.end(), [&](u32 a, u32 c) { return n[a] > n[c]; });
+    std::vector<double> load(b->side.size(), 0.0);
+    std::vector<u32> lane(np, 0);
+    for (u32 p : order) {
+        const size_t w = std::min_element(load.begin(), load.end()) - load.begin();
+        lane[p] = (u32)w;
+        load[w] += (double)n[p] + 1000.0;
+    }
+    CK(cudaMemcpyAsync(b->d_probs, b->h_probs, np * sizeof(BatchProblem), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_block_prob, b->h_block_prob, b->total_blocks * sizeof(u32),
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_init, b->h_init, np * 16 * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaEventRecord(b->ev_fork, b->stream));
+    for (cudaStream_t s : b->side) CK(cudaStreamWaitEvent(s, b->ev_fork, 0));
+    for (u32 p : order) {
+        far_map* m = b->maps[p];
+        m->stream = b->side[lane[p]];
+        const u32 nn = (u32)n[p];
+        far_status st = ingest(m, xyz[p], nn, stride[p]);
+        if (st != FAR_OK) return st;
+        if (nn) {
+            if ((st = build_sources(m, nn, nullptr)) != FAR_OK) return st;
+        } else {
+            CK(cudaMemsetAsync(m->s.scal, 0, SCAL_COUNT * sizeof(u32), m->stream));
+        }
+    }
+    for (size_t i = 0; i < b->side.size(); ++i) {
+        CK(cudaEventRecord(b->ev_join[i], b->side[i]));
+        CK(cudaStreamWaitEvent(b->stream, b->ev_join[i], 0));
+    }
+    CK(gn_batch_begin(b->d_probs, np, b->d_init, b->stream));
+    for (u32 it = 0; it < iters; ++it)
+        CK(gn_batch_iteration(b->d_probs, b->d_block_prob, b->total_blocks, np, tpp, b->stream));
+    if (ins) {
+        CK(cudaEventRecord(b->ev_fork2, b->stream));
+        for (cudaStream_t s : b->side) CK(cudaStreamWaitEvent(s, b->ev_fork2, 0));
+        for (u32 p : order) {
+            far_map* m = b->maps[p];
+            m->stream = b->side[lane[p]];
+            DevicePose dp;
+            dp.T = m->s.st->T;
+            dp.status = &m->s.st->status;
+            CK(map_insert_batch(m->map, m->s, (u32)n[p], nullptr, *ins, true, m->stream, dp));
+            if (evict_radius > 0.0 && std::isfinite(evict_radius))
+                CK(map_evict(m->map, nullptr, evict_radius, m->stream, m->s.st->T));
+            else
+                CK(cudaMemsetAsync(&m->map.ctr->removed, 0, sizeof(unsigned long long), m->stream));
+            CK(cudaMemcpyAsync(b->h_ctr + p, m->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, m->stream));
+        }
+        for (size_t i = 0; i < b->side.size(); ++i) {
+            CK(cudaEventRecord(b->ev_join2[i], b->side[i]));
+            CK(cudaStreamWaitEvent(b->stream, b->ev_join2[i], 0));
+        }
+    }
+    CK(gn_batch_gather(b->d_probs, np, b->d_states, b->stream));
+    CK(cudaMemcpyAsync(b->h_states, b->d_states, np * sizeof(RegState), cudaMemcpyDeviceToHost, b->stream));
+    return FAR_OK;
+}
+
+// Record a registration batch into a CUDA graph.
 far_status batch_capture(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
                          uint32_t iters, int tpp) {
     const u32 np = (u32)b->maps.size();
@@ -907,75 +1010,14 @@ far_status batch_capture(far_batch* b, const float* const* xyz, const uint64_t* 
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
-    // share of the resident grid for each problem, by point count
-    const u32 resident = gn_batch_resident_blocks(tpp);
-    const u32 gt = gn_threads_per_block();
-    double sum_n = 0;
-    for (u32 p = 0; p < np; ++p) sum_n += (double)std::max<uint64_t>(n[p], 1);
-    std::vector<unsigned short> block_prob;
-    for (u32 p = 0; p < np; ++p) {
-        far_map* m = b->maps[p];
-        const u64 n_up = std::max<uint64_t>(n[p], 1);
-        const u32 need = (u32)std::min<u64>((n_up * (u64)gn_tpp(tpp) + gt - 1) / gt, 65535);
-        const u32 alloc = (u32)(gn_partials_doubles(m->p.max_scan_points) / 32);
-        u32 share = (u32)std::llround(resident * (double)n_up / sum_n);
-        share = std::max(1u, std::min({share, need, alloc}));
-        BatchProblem& bp = b->h_probs[p];
-        bp.block_begin = (u32)block_prob.size();
-        bp.nblocks = share;
-        for (u32 j = 0; j < share; ++j) block_prob.push_back((unsigned short)p);
-    }
-    if (block_prob.size() > 65535) return fail(FAR_ERR_INVALID, "batch grid too large");
-    b->total_blocks = (u32)block_prob.size();
-    cudaFree(b->d_block_prob);
-    b->d_block_prob = nullptr;
-    CK(cudaMalloc(&b->d_block_prob, block_prob.size() * sizeof(unsigned short)));
-    CK(cudaMemcpy(b->d_block_prob, block_prob.data(), block_prob.size() * sizeof(unsigned short),
-                  cudaMemcpyHostToDevice));
-
-    // the maps' own streams are swapped for the batch's worker streams during the capture
-    std::vector<cudaStream_t> saved(np);
-    for (u32 p = 0; p < np; ++p) saved[p] = b->maps[p]->stream;
-    auto restore = [&]() {
-        for (u32 p = 0; p < np; ++p) b->maps[p]->stream = saved[p];
-    };
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    far_status st = FAR_OK;
-    cudaError_t e = cudaMemcpyAsync(b->d_probs, b->h_probs, np * sizeof(BatchProblem), cudaMemcpyHostToDevice,
-                                    b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_init, b->h_init, np * 16 * sizeof(double), cudaMemcpyHostToDevice,
-                                              b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
-    for (size_t i = 0; e == cudaSuccess && i < b->side.size(); ++i) e = cudaStreamWaitEvent(b->side[i], b->ev_fork, 0);
-    for (u32 p = 0; e == cudaSuccess && st == FAR_OK && p < np; ++p) {
-        far_map* m = b->maps[p];
-        m->stream = b->side[p % b->side.size()];
-        const u32 nn = (u32)n[p];
-        if ((st = ingest(m, xyz[p], nn, stride[p])) != FAR_OK) break;
-        if (nn) {
-            if ((st = build_sources(m, nn, nullptr)) != FAR_OK) break;
-        } else {
-            e = cudaMemsetAsync(m->s.scal, 0, SCAL_COUNT * sizeof(u32), m->stream);
-        }
-    }
-    for (size_t i = 0; e == cudaSuccess && st == FAR_OK && i < b->side.size(); ++i) {
-        e = cudaEventRecord(b->ev_join[i], b->side[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[i], 0);
-    }
-    restore();
-    if (e == cudaSuccess && st == FAR_OK) e = gn_batch_begin(b->d_probs, np, b->d_init, b->stream);
-    for (u32 it = 0; e == cudaSuccess && st == FAR_OK && it < iters; ++it)
-        e = gn_batch_iteration(b->d_probs, b->d_block_prob, b->total_blocks, np, tpp, b->stream);
-    if (e == cudaSuccess && st == FAR_OK) e = gn_batch_gather(b->d_probs, np, b->d_states, b->stream);
-    if (e == cudaSuccess && st == FAR_OK)
-        e = cudaMemcpyAsync(b->h_states, b->d_states, np * sizeof(RegState), cudaMemcpyDeviceToHost, b->stream);
-    cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+    far_status st = batch_enqueue(b, xyz, n, stride, iters, tpp, nullptr, 0.0);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
     if (st != FAR_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
     }
-    if (e == cudaSuccess) e = ee;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -987,6 +1029,70 @@ far_status batch_capture(far_batch* b, const float* const* xyz, const uint64_t* 
     b->key_stride.assign(stride, stride + np);
     b->key_iters = iters;
     b->key_tpp = tpp;
+    return FAR_OK;
+}
+
+far_status batch_check(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
+                       const double* init_poses, const far_reg_params* params, uint32_t params_count,
+                       const double* out_poses) {
+    if (!b || !xyz || !n || !stride || !init_poses || !params || !out_poses)
+        return fail(FAR_ERR_INVALID, "NULL argument");
+    const u32 np = (u32)b->maps.size();
+    if (params_count != 1 && params_count != np) return fail(FAR_ERR_INVALID, "params_count must be 1 or the batch size");
+    for (u32 i = 0; i < params_count; ++i) {
+        const far_reg_params& q = params[i];
+        if (!(q.kappa > 0.0f) || !(q.tau >= 0.0f) || q.max_iters > 1000)
+            return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000 (params %u)", i);
+        if (q.max_iters != params[0].max_iters || gn_tpp((int)q.threads_per_point) != gn_tpp((int)params[0].threads_per_point))
+            return fail(FAR_ERR_INVALID, "max_iters and threads_per_point must be the same for every problem");
+    }
+    for (u32 p = 0; p < np; ++p) {
+        far_status st = check_points(b->maps[p], xyz[p], n[p], stride[p]);
+        if (st != FAR_OK) return st;
+        if (n[p] && !is_registered_or_device(xyz[p]))
+            return fail(FAR_ERR_INVALID, "batch inputs must be device or pinned host memory (problem %u)", p);
+        if (!finite_pose(init_poses + 16 * (size_t)p)) return fail(FAR_ERR_INVALID, "init pose %u not finite", p);
+    }
+    return FAR_OK;
+}
+
+void batch_set_args(far_batch* b, const uint64_t* n, const double* init_poses, const far_reg_params* params,
+                    uint32_t params_count, int tpp) {
+    const u32 np = (u32)b->maps.size();
+    for (u32 p = 0; p < np; ++p) {
+        const u32 n_up = (u32)std::max<uint64_t>(n[p], 1);
+        const far_reg_params& q = params[params_count == 1 ? 0 : p];
+        b->h_probs[p].args = gn_args(b->maps[p], n_up, q.tau, q.kappa, q.conv_eps, 1, nullptr, q.time_budget_s, tpp);
+    }
+    std::memcpy(b->h_init, init_poses, np * 16 * sizeof(double));
+}
+
+far_status batch_results(far_batch* b, double* out_poses, far_reg_stats* stats, far_step_result* steps) {
+    const u32 np = (u32)b->maps.size();
+    far_status worst = FAR_OK;
+    for (u32 p = 0; p < np; ++p) {
+        const RegState& r = b->h_states[p];
+        std::memcpy(out_poses + 16 * (size_t)p, r.T, 16 * sizeof(double));
+        far_status sp = r.status == 5 ? FAR_ERR_DEGENERATE : (r.status == 6 ? FAR_ERR_TIMEOUT : FAR_OK);
+        if (sp != FAR_OK && worst == FAR_OK) worst = sp;
+        far_reg_stats rs;
+        rs.iters = r.iters;
+        rs.n_src = r.n_src;
+        rs.n_corr = r.n_corr;
+        rs.n_p2p = r.n_p2p;
+        rs.converged = (int32_t)r.converged;
+        rs.status = sp;
+        rs.chi2 = r.chi2;
+        if (stats) stats[p] = rs;
+        if (steps) {
+            steps[p].reg = rs;
+            steps[p].n_inserted = b->h_ctr[p].n_added;
+            steps[p].n_removed = b->h_ctr[p].removed;
+            steps[p].n_voxels = b->h_ctr[p].n_voxels;
+            steps[p].n_points = b->h_ctr[p].n_points;
+        }
+    }
+    if (worst != FAR_OK) return fail(worst, "at least one problem of the batch did not register (see stats)");
     return FAR_OK;
 }
 
@@ -1004,24 +1110,31 @@ far_status far_batch_create(far_map* const* maps, uint32_t count, void* cuda_str
     far_batch* b = new far_batch();
     b->maps.assign(maps, maps + count);
     b->user_stream = static_cast<cudaStream_t>(cuda_stream);
-    const u32 nside = std::min<u32>(count, 8);
+    const u32 nside = std::min<u32>(count, 16);
     cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     for (u32 i = 0; e == cudaSuccess && i < nside; ++i) {
         cudaStream_t s = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev = nullptr, ev2 = nullptr;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) b->side.push_back(s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) b->ev_join.push_back(ev);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->ev_join2.push_back(ev2);
     }
+    for (uint32_t i = 0; i < count; ++i) b->max_blocks += gn_max_blocks(maps[i]->p.max_scan_points);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_probs, count * sizeof(BatchProblem));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_block_prob, (size_t)b->max_blocks * sizeof(u32));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_init, count * 16 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_states, count * sizeof(RegState));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_probs, count * sizeof(BatchProblem));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_block_prob, (size_t)b->max_blocks * sizeof(u32));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_init, count * 16 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_states, count * sizeof(RegState));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_ctr, count * sizeof(MapCounters));
     if (e != cudaSuccess) {
         cudaGetLastError();
         batch_release(b);
@@ -1040,58 +1153,68 @@ far_status far_batch_destroy(far_batch* batch) {
 }
 
 far_status far_batch_register(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
-                              const double* init_poses, const far_reg_params* params, double* out_poses,
-                              far_reg_stats* stats) {
-    if (!b || !xyz || !n || !stride || !init_poses || !params || !out_poses)
-        return fail(FAR_ERR_INVALID, "NULL argument");
-    if (!(params->kappa > 0.0f) || !(params->tau >= 0.0f) || params->max_iters > 1000)
-        return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000");
+                              const double* init_poses, const far_reg_params* params, uint32_t params_count,
+                              double* out_poses, far_reg_stats* stats) {
+    far_status st = batch_check(b, xyz, n, stride, init_poses, params, params_count, out_poses);
+    if (st != FAR_OK) return st;
     const u32 np = (u32)b->maps.size();
-    for (u32 p = 0; p < np; ++p) {
-        far_status st = check_points(b->maps[p], xyz[p], n[p], stride[p]);
-        if (st != FAR_OK) return st;
-        if (n[p] && !is_registered_or_device(xyz[p]))
-            return fail(FAR_ERR_INVALID, "batch inputs must be device or pinned host memory (problem %u)", p);
-        if (!finite_pose(init_poses + 16 * (size_t)p)) return fail(FAR_ERR_INVALID, "init pose %u not finite", p);
-    }
     const int tpp = gn_tpp((int)params->threads_per_point);
-    // per-call arguments, read by the graph from the pinned mirrors
-    for (u32 p = 0; p < np; ++p) {
-        far_map* m = b->maps[p];
-        const u32 n_up = (u32)std::max<uint64_t>(n[p], 1);
-        b->h_probs[p].args = gn_args(m, n_up, params->tau, params->kappa, params->conv_eps, 1, nullptr,
-                                     params->time_budget_s, tpp);
-    }
-    std::memcpy(b->h_init, init_poses, np * 16 * sizeof(double));
+    batch_set_args(b, n, init_poses, params, params_count, tpp);
     bool same = b->exec && b->key_iters == params->max_iters && b->key_tpp == tpp;
     for (u32 p = 0; same && p < np; ++p)
         same = b->key_ptr[p] == (const void*)xyz[p] && b->key_n[p] == n[p] && b->key_stride[p] == stride[p];
-    if (!same) {
-        far_status st = batch_capture(b, xyz, n, stride, params->max_iters, tpp);
-        if (st != FAR_OK) return st;
-    }
+    // the graph copies the block table and descriptors from the pinned mirrors at launch; the
+    // assignment is a function of (n, tpp), so recomputing it restores what the graph was built for
+    if ((st = batch_assign_blocks(b, n, tpp)) != FAR_OK) return st;
+    if (!same && (st = batch_capture(b, xyz, n, stride, params->max_iters, tpp)) != FAR_OK) return st;
     CK(cudaEventRecord(b->ev_user, b->user_stream));
     CK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
     CK(cudaGraphLaunch(b->exec, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    far_status worst = FAR_OK;
+    return batch_results(b, out_poses, stats, nullptr);
+}
+
+far_status far_batch_process(far_batch* b, const float* const* xyz, const uint64_t* n, const uint32_t* stride,
+                             const double* init_poses, const far_reg_params* params, uint32_t params_count,
+                             const far_insert_params* ins, double evict_radius, double* out_poses,
+                             far_step_result* results) {
+    far_status st = batch_check(b, xyz, n, stride, init_poses, params, params_count, out_poses);
+    if (st != FAR_OK) return st;
+    if (!(evict_radius >= 0.0) || std::isnan(evict_radius)) return fail(FAR_ERR_INVALID, "evict_radius must be >= 0");
+    InsertCfg cfg;
+    if (ins && ins->asmd) {
+        if (!(ins->r_max > 0.0) || !(ins->r_near >= 0.0) || !std::isfinite(ins->r_max))
+            return fail(FAR_ERR_INVALID, "ASMD needs r_near >= 0 and finite r_max > 0");
+        cfg.asmd = 1;
+        cfg.rc2 = ins->r_near * ins->r_near;
+        cfg.r_max = ins->r_max;
+    }
+    const u32 np = (u32)b->maps.size();
+    const int tpp = gn_tpp((int)params->threads_per_point);
+    batch_set_args(b, n, init_poses, params, params_count, tpp);
+    if ((st = batch_assign_blocks(b, n, tpp)) != FAR_OK) return st;
+    CK(cudaEventRecord(b->ev_user, b->user_stream));
+    CK(cudaStreamWaitEvent(b->stream, b->ev_user, 0));
+    if ((st = batch_enqueue(b, xyz, n, stride, params->max_iters, tpp, &cfg, evict_radius)) != FAR_OK) return st;
+    CK(cudaStreamSynchronize(b->stream));
     for (u32 p = 0; p < np; ++p) {
-        const RegState& r = b->h_states[p];
-        std::memcpy(out_poses + 16 * (size_t)p, r.T, 16 * sizeof(double));
-        far_status sp = r.status == 5 ? FAR_ERR_DEGENERATE : (r.status == 6 ? FAR_ERR_TIMEOUT : FAR_OK);
-        if (sp != FAR_OK && worst == FAR_OK) worst = sp;
-        if (stats) {
-            stats[p].iters = r.iters;
-            stats[p].n_src = r.n_src;
-            stats[p].n_corr = r.n_corr;
-            stats[p].n_p2p = r.n_p2p;
-            stats[p].converged = (int32_t)r.converged;
-            stats[p].status = sp;
-            stats[p].chi2 = r.chi2;
+        far_map* m = b->maps[p];
+        if (b->h_ctr[p].n_tomb > m->map.cap / 4) {
+            CK(map_rebuild(m->map, m->stream));
+            CK(cudaStreamSynchronize(m->stream));
         }
     }
-    if (worst != FAR_OK) return fail(worst, "at least one problem of the batch did not register (see stats)");
-    return FAR_OK;
+    st = batch_results(b, out_poses, nullptr, results);
+    if (st == FAR_OK) {
+        for (u32 p = 0; p < np; ++p) {
+            if (b->h_ctr[p].err) {
+                *b->maps[p]->h_ctr = b->h_ctr[p];
+                far_status e2 = check_device_errors(b->maps[p], "far_batch_process");
+                if (e2 != FAR_OK) return e2;
+            }
+        }
+    }
+    return st;
 }
 
 unsigned long long far_launch_count(void) { return g_launches.load(); }

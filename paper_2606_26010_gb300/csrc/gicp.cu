@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs
 // block_prob[b] as its (b - block_begin)-th block of nblocks.
 template <int TPP>
 __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(const BatchProblem* __restrict__ probs,
-                                                                                const unsigned short* __restrict__ block_prob) {
+                                                                                const u32* __restrict__ block_prob) {
     const BatchProblem& p = probs[block_prob[blockIdx.x]];
     gn_lin_block<TPP>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
@@ -623,6 +623,8 @@ u32 gn_grid(u32 n_upper, int tpp) {
 }
 
 // Partials for the largest grid any lanes-per-point setting can launch (32 lanes per point).
+u32 gn_max_blocks(u32 n_upper) { return (u32)(gn_partials_doubles(n_upper) / NPART); }
+
 size_t gn_partials_doubles(u32 n_upper) {
     u64 b = ((u64)n_upper * 32 + GN_THREADS - 1) / GN_THREADS;
     if (b == 0) b = 1;
@@ -653,21 +655,13 @@ cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-u32 gn_batch_resident_blocks(int tpp) {
-    switch (gn_tpp(tpp)) {
-        case 4: return resident_gn_blocks<4>();
-        case 8: return resident_gn_blocks<8>();
-        case 32: return resident_gn_blocks<32>();
-        default: return resident_gn_blocks<1>();
-    }
-}
 
 cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* init, cudaStream_t s) {
     FAR_LAUNCH(k_gn_begin_batch, (nprob + 127) / 128, 128, 0, s, probs, nprob, init);
     return cudaGetLastError();
 }
 
-cudaError_t gn_batch_iteration(const BatchProblem* probs, const unsigned short* block_prob, u32 total_blocks, u32 nprob,
+cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob, u32 total_blocks, u32 nprob,
                                int tpp, cudaStream_t s) {
     switch (gn_tpp(tpp)) {
         case 4: FAR_LAUNCH(k_gn_lin_batch<4>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;

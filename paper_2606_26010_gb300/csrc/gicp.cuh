@@ -32,10 +32,9 @@ struct BatchProblem {
 
 // Batched Gauss-Newton: one linearisation launch and one solve launch per iteration for all
 // problems; every problem stops on its own flag.
-u32 gn_batch_resident_blocks(int tpp);
 u32 gn_threads_per_block();
 cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* init, cudaStream_t s);
-cudaError_t gn_batch_iteration(const BatchProblem* probs, const unsigned short* block_prob, u32 total_blocks, u32 nprob,
+cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob, u32 total_blocks, u32 nprob,
                                int tpp, cudaStream_t s);
 cudaError_t gn_batch_gather(const BatchProblem* probs, u32 nprob, RegState* out, cudaStream_t s);
 
@@ -43,6 +42,7 @@ cudaError_t gn_batch_gather(const BatchProblem* probs, u32 nprob, RegState* out,
 int gn_tpp(int requested);
 u32 gn_grid(u32 n_upper, int tpp);
 size_t gn_partials_doubles(u32 n_upper);
+u32 gn_max_blocks(u32 n_upper);   // largest grid gn_grid returns for n_upper points, any lanes per point
 // Reset the registration state to `init`; n_src (device, may be null) is recorded in st->n_src.
 cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s);
 // One Gauss-Newton iteration = k_gn_lin (search, linearisation, block partials) then

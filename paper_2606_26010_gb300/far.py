@@ -109,7 +109,8 @@ _SIGS = {
     "far_launch_count": (ctypes.c_ulonglong, []),
     "far_batch_create": (ctypes.c_int, [_vp, _u32, _vp, _vp]),
     "far_batch_destroy": (ctypes.c_int, [_vp]),
-    "far_batch_register": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "far_batch_register": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp]),
+    "far_batch_process": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, ctypes.c_double, _vp, _vp]),
     "far_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "far_get_stage_times": (ctypes.c_int, [_vp, _vp]),
     "far_gn_footprint": (ctypes.c_int, [_vp, _vp]),
@@ -350,6 +351,19 @@ class VoxelMap:
         return int(out[0]), int(out[1]), int(out[2])
 
 
+def _reg_params(B, max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point):
+    """tau / kappa may be scalars (shared) or sequences of length B (per problem)."""
+    if np.isscalar(tau) and np.isscalar(kappa):
+        arr = (RegParams * 1)(RegParams(max_iters, conv_eps, float(tau), float(kappa), time_budget_s,
+                                        threads_per_point))
+        return arr, 1
+    taus = np.broadcast_to(np.asarray(tau, np.float64), (B,))
+    kappas = np.broadcast_to(np.asarray(kappa, np.float64), (B,))
+    arr = (RegParams * B)(*[RegParams(max_iters, conv_eps, float(t), float(k), time_budget_s, threads_per_point)
+                            for t, k in zip(taus, kappas)])
+    return arr, B
+
+
 class Batch:
     """Batched registration of several maps in one CUDA graph (far_batch_*)."""
 
@@ -387,10 +401,30 @@ class Batch:
         init = np.ascontiguousarray(np.asarray(inits, np.float64).reshape(B, 16))
         out = np.zeros((B, 16))
         stats = (RegStats * B)()
-        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
-        _check(self._L.far_batch_register(self._h, ptrs, ns, strides, _p(init), ctypes.byref(prm), _p(out), stats),
+        prm, cnt = _reg_params(B, max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
+        _check(self._L.far_batch_register(self._h, ptrs, ns, strides, _p(init), prm, cnt, _p(out), stats),
                allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
         return out.reshape(B, 4, 4), [st.as_dict() for st in stats]
+
+    def process(self, scans, inits, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0, time_budget_s=0.0,
+                threads_per_point=0, asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0):
+        """The full per-scan step (register, insert at the result, evict) for every problem.
+        Returns (poses (B, 4, 4), list of result dicts)."""
+        B = len(self.maps)
+        assert len(scans) == B and len(inits) == B
+        infos = [_points(s) for s in scans]
+        ptrs = (ctypes.c_void_p * B)(*[i[0] for i in infos])
+        ns = (ctypes.c_uint64 * B)(*[i[1] for i in infos])
+        strides = (ctypes.c_uint32 * B)(*[i[2] for i in infos])
+        init = np.ascontiguousarray(np.asarray(inits, np.float64).reshape(B, 16))
+        out = np.zeros((B, 16))
+        res = (StepResult * B)()
+        prm, cnt = _reg_params(B, max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
+        ins = InsertParams(int(asmd), r_near, r_max)
+        _check(self._L.far_batch_process(self._h, ptrs, ns, strides, _p(init), prm, cnt, ctypes.byref(ins),
+                                         float(evict_radius), _p(out), res),
+               allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
+        return out.reshape(B, 4, 4), [r.as_dict() for r in res]
 
 
 def launch_count() -> int:

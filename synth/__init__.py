@@ -363,3 +363,12 @@ def batched_problems(seed: int = 7, count: int = 64, scan_range=(5e3, 3e5), map_
         out.append(BatchProblemSpec(lidar, list(range(q_idx - 1, q_idx - max_prior - 1, -1)), query, truth, init,
                                     int(n_map)))
     return seq, out
+
+
+# ---- vehicles for a serving run ---------------------------------------------------------
+def vehicle_pose(s0: float, speed: float, rate_hz: float, frame: int) -> np.ndarray:
+    return track_pose(s0 + speed * frame / rate_hz)
+
+
+def vehicle_scan(scene: Scene, lidar: Lidar, s0: float, speed: float, rate_hz: float, frame: int, seed: int):
+    return raycast(scene, lidar, vehicle_pose(s0, speed, rate_hz, frame), seed, frame)
