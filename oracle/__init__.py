@@ -57,6 +57,7 @@ def _load():
     L = ctypes.CDLL(_LIB_PATH)
     sig = {
         "om_create": (_vp, [ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_float]),
+        "om_create_prec": (_vp, [ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int]),
         "om_destroy": (None, [_vp]),
         "om_dmin2": (ctypes.c_float, [_vp]),
         "om_insert": (ctypes.c_uint64, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int, ctypes.c_double,
@@ -104,12 +105,20 @@ def _p(a):
 
 
 class OracleMap:
-    """std::unordered_map voxel grid (cuVoxelMap analogue, Sec. III-A.2/III-A.3)."""
+    """std::unordered_map voxel grid (cuVoxelMap analogue, Sec. III-A.2/III-A.3).
 
-    def __init__(self, voxel_size: float, max_pts_per_voxel: int, k_cov: int, min_spacing: float = -1.0):
+    precision_mode = 1 is the precision variant: FP64 world points, 50 m tile keys,
+    tile-relative FP32 decision coordinates, Gauss-Newton about the tile-corner anchor."""
+
+    def __init__(self, voxel_size: float, max_pts_per_voxel: int, k_cov: int, min_spacing: float = -1.0,
+                 precision_mode: int = 0):
         self._L = _load()
         self.voxel_size, self.nmax, self.k = float(voxel_size), int(max_pts_per_voxel), int(k_cov)
-        self._h = self._L.om_create(ctypes.c_float(voxel_size), self.nmax, self.k, ctypes.c_float(min_spacing))
+        self.precision_mode = int(precision_mode)
+        self._h = self._L.om_create_prec(ctypes.c_float(voxel_size), self.nmax, self.k, ctypes.c_float(min_spacing),
+                                         self.precision_mode)
+        if not self._h:
+            raise ValueError("precision_mode 1 needs a voxel size that divides 50 m")
 
     def __del__(self):
         h = getattr(self, "_h", None)

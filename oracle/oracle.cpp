@@ -21,6 +21,14 @@
 // Readings where the paper is silent (key rounding, spacing rule, tie-break,
 // Cauchy argument, linearisation, exp map, adaptive threshold, ASMD constants)
 // are the ones listed in the design notes; each is restated where it is used.
+//
+// Precision variant (precision_mode = 1, the mixed-precision storage scheme):
+// the method is the same; what changes is where rounding to FP32 happens. Map
+// points keep their unrounded FP64 world position for all arithmetic; keys use
+// the tile rule (50 m tiles, see tile_key); the FP32 decision expressions
+// (spacing, candidate order) are evaluated on coordinates relative to a tile
+// origin instead of the world origin; Gauss-Newton is linearised about an
+// anchor (the tile corner of the initial position) instead of the world origin.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -76,6 +84,46 @@ float dist2_f32(const float a[3], const float b[3]) {
     float s = sx + sy;
     return s + sz;
 }
+
+// ------------------------------------------------------------------ precision variant: 50 m tiles
+// Tile reading (precision_mode = 1): the tile of a world coordinate x is
+// T = floor(x / 50) (FP64 division), the tile-relative coordinate is
+// x_t = fp32(x - 50 T), and the voxel key is T tv + clamp(floor(fp32(x_t * inv_v)), 0, tv - 1)
+// with tv = 50 / v voxels per tile side (v must divide 50 m). The clamp keeps every key
+// inside the tile of its point when x_t rounds to 50 or to a tiny negative value.
+constexpr double kTile = 50.0;
+
+bool tile_key(const double x[3], float inv_v, int tv, Key* out, float local[3], int32_t tile[3]) {
+    int32_t k[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(x[a])) return false;
+        double T = std::floor(x[a] / kTile);
+        if (!(std::fabs(T) * tv < (double)kKeyLimit)) return false;
+        float xt = (float)(x[a] - kTile * T);
+        float s = xt * inv_v;
+        int32_t kin = (int32_t)std::floor(s);
+        if (kin < 0) kin = 0;
+        if (kin > tv - 1) kin = tv - 1;
+        int64_t key = (int64_t)T * tv + kin;
+        if (key < -(int64_t)kKeyLimit || key >= (int64_t)kKeyLimit) return false;
+        k[a] = (int32_t)key;
+        local[a] = xt;
+        tile[a] = (int32_t)T;
+    }
+    *out = Key{k[0], k[1], k[2]};
+    return true;
+}
+
+// Tile of a key (floor division by tv).
+int32_t tile_of(int32_t k, int tv) { return (int32_t)std::floor((double)k / (double)tv); }
+
+// A search frame: the origin of tile (fx, fy, fz); fx = fy = fz = 0 with tv = 0 is the
+// world frame of the plain map. Frame coordinates of a map point: fp32(p + 50 (T_p - F)),
+// one FP32 addition of an exact multiple of 50.
+struct Frame {
+    int32_t f[3] = {0, 0, 0};
+    int tv = 0;
+};
 
 // ------------------------------------------------------------------ small linear algebra (FP64)
 
@@ -226,7 +274,9 @@ void cholesky6_solve(const double L[36], const double b[6], double x[6]) {
 
 // ------------------------------------------------------------------ voxel map (cuVoxelMap analogue)
 struct MapPoint {
-    float p[3];
+    float p[3];        // FP32 world point (plain) or tile-relative coordinates (precision variant)
+    double w[3];       // world point used by all arithmetic: (double)p (plain) or the unrounded transform
+    int32_t tile[3];   // tile of the point's voxel (precision variant; 0 otherwise)
     uint32_t id;
     double cov[6];  // xx xy xz yy yz zz
     int valid;
@@ -243,6 +293,8 @@ struct OracleMap {
     int nmax;
     int k;
     float dmin2;
+    int prec = 0;   // precision variant (tile keys, FP64 world points)
+    int tv = 0;     // voxels per tile side (precision variant)
     std::unordered_map<Key, Voxel, KeyHash> vox;
     uint32_t next_id = 0;
     uint64_t npoints = 0;
@@ -250,12 +302,35 @@ struct OracleMap {
 
 namespace {
 
-// kNN over the 27 voxels around the query's voxel, ordered by (d^2, id).
-// Returns the number found (<= k); ids/points of the k best in order.
-int knn27(const OracleMap& m, const float q[3], int k, std::vector<const MapPoint*>* best) {
-    best->clear();
+// Frame coordinates of a map point (see Frame).
+void frame_coords(const MapPoint& p, const Frame& fr, float out[3]) {
+    for (int a = 0; a < 3; ++a) {
+        float off = (fr.tv > 0) ? (float)(kTile * (double)(p.tile[a] - fr.f[a])) : 0.0f;
+        out[a] = p.p[a] + off;
+    }
+}
+
+// Centre key of a query given in frame coordinates: K_F + floor(fp32(q_F * inv_v)).
+bool frame_key(const OracleMap& m, const float qf[3], const Frame& fr, Key* out) {
     Key c;
-    if (!voxel_key(q, m.inv_v, &c)) return 0;
+    if (!voxel_key(qf, m.inv_v, &c)) return false;
+    if (fr.tv > 0) {
+        int64_t k[3] = {(int64_t)c.x + (int64_t)fr.f[0] * fr.tv, (int64_t)c.y + (int64_t)fr.f[1] * fr.tv,
+                        (int64_t)c.z + (int64_t)fr.f[2] * fr.tv};
+        for (int a = 0; a < 3; ++a)
+            if (k[a] < -(int64_t)kKeyLimit || k[a] >= (int64_t)kKeyLimit) return false;
+        c = Key{(int32_t)k[0], (int32_t)k[1], (int32_t)k[2]};
+    }
+    *out = c;
+    return true;
+}
+
+// kNN over the 27 voxels around centre key c, ordered by (d^2, id) with the FP32
+// distance between the query and the points, both in frame coordinates.
+// Returns the number found (<= k); ids/points of the k best in order.
+int knn27_at(const OracleMap& m, const Key& c, const float qf[3], const Frame& fr, int k,
+             std::vector<const MapPoint*>* best) {
+    best->clear();
     std::vector<std::pair<std::pair<float, uint32_t>, const MapPoint*>> cand;
     for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
@@ -263,8 +338,11 @@ int knn27(const OracleMap& m, const float q[3], int k, std::vector<const MapPoin
                 Key n{c.x + dx, c.y + dy, c.z + dz};
                 auto it = m.vox.find(n);
                 if (it == m.vox.end()) continue;
-                for (const MapPoint& p : it->second.pts)
-                    cand.push_back({{dist2_f32(q, p.p), p.id}, &p});
+                for (const MapPoint& p : it->second.pts) {
+                    float pf[3];
+                    frame_coords(p, fr, pf);
+                    cand.push_back({{dist2_f32(qf, pf), p.id}, &p});
+                }
             }
     std::sort(cand.begin(), cand.end(),
               [](const auto& a, const auto& b) { return a.first < b.first; });
@@ -273,17 +351,36 @@ int knn27(const OracleMap& m, const float q[3], int k, std::vector<const MapPoin
     return found;
 }
 
+// kNN of a query in world FP32 coordinates (plain map: the world frame; precision
+// variant: the frame of the query's own tile).
+int knn27(const OracleMap& m, const float q[3], int k, std::vector<const MapPoint*>* best) {
+    best->clear();
+    Frame fr;
+    float qf[3] = {q[0], q[1], q[2]};
+    if (m.prec) {
+        fr.tv = m.tv;
+        for (int a = 0; a < 3; ++a) {
+            double T = std::floor((double)q[a] / kTile);
+            fr.f[a] = (int32_t)T;
+            qf[a] = (float)((double)q[a] - kTile * T);
+        }
+    }
+    Key c;
+    if (!frame_key(m, qf, fr, &c)) return 0;
+    return knn27_at(m, c, qf, fr, k, best);
+}
+
 // Eq. 1: Sigma-hat from the k nearest neighbours (population form, 1/k, around
 // the neighbour mean), C = Sigma-hat + 1e-3 I, Sigma = (C^-1 / ||C^-1||_F)^-1.
 void covariance_eq1(const std::vector<const MapPoint*>& nb, double out[6]) {
     double k = (double)nb.size();
     double mu[3] = {0, 0, 0};
     for (const MapPoint* p : nb)
-        for (int a = 0; a < 3; ++a) mu[a] += (double)p->p[a];
+        for (int a = 0; a < 3; ++a) mu[a] += p->w[a];
     for (int a = 0; a < 3; ++a) mu[a] /= k;
     double S[3][3] = {{0}};
     for (const MapPoint* p : nb) {
-        double d[3] = {(double)p->p[0] - mu[0], (double)p->p[1] - mu[1], (double)p->p[2] - mu[2]};
+        double d[3] = {p->w[0] - mu[0], p->w[1] - mu[1], p->w[2] - mu[2]};
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) S[i][j] += d[i] * d[j];
     }
@@ -320,6 +417,19 @@ void transform_point_f32(const double T[16], const float p[3], float out[3]) {
     }
 }
 
+// World point of an insert in FP64 (precision variant): the same expression, not rounded.
+void transform_point_f64(const double T[16], const float p[3], double out[3]) {
+    double x = p[0], y = p[1], z = p[2];
+    for (int r = 0; r < 3; ++r) {
+        double a = T[4 * r + 0] * x;
+        double b = T[4 * r + 1] * y;
+        double c = T[4 * r + 2] * z;
+        double s = a + b;
+        s = s + c;
+        out[r] = s + T[4 * r + 3];
+    }
+}
+
 bool finite3(const float p[3]) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
 struct InsertResult {
@@ -342,7 +452,9 @@ InsertResult map_insert(OracleMap& m, const float* xyz, int64_t n, const double*
                         double r_c, double r_max) {
     InsertResult res;
     const double sensor[3] = {T ? T[3] : 0.0, T ? T[7] : 0.0, T ? T[11] : 0.0};
-    std::vector<float> w(3 * (size_t)n);
+    std::vector<float> w(3 * (size_t)n);      // FP32 decision coordinates (world or tile-relative)
+    std::vector<double> w64(3 * (size_t)n);   // world point for arithmetic
+    std::vector<int32_t> tiles(3 * (size_t)n, 0);
     std::vector<Key> keys((size_t)n);
     std::vector<char> ok((size_t)n, 0);
     std::unordered_map<Key, int64_t, KeyHash> scan_count;
@@ -350,9 +462,18 @@ InsertResult map_insert(OracleMap& m, const float* xyz, int64_t n, const double*
         const float* p = xyz + 3 * i;
         if (!finite3(p)) continue;
         float* x = &w[3 * i];
-        if (T) transform_point_f32(T, p, x);
-        else std::memcpy(x, p, 3 * sizeof(float));
-        if (!voxel_key(x, m.inv_v, &keys[i])) continue;
+        double* x64 = &w64[3 * i];
+        if (m.prec) {
+            // precision variant: FP64 world point, tile key, tile-relative FP32 coordinates
+            if (T) transform_point_f64(T, p, x64);
+            else for (int a = 0; a < 3; ++a) x64[a] = (double)p[a];
+            if (!tile_key(x64, m.inv_v, m.tv, &keys[i], x, &tiles[3 * i])) continue;
+        } else {
+            if (T) transform_point_f32(T, p, x);
+            else std::memcpy(x, p, 3 * sizeof(float));
+            if (!voxel_key(x, m.inv_v, &keys[i])) continue;
+            for (int a = 0; a < 3; ++a) x64[a] = (double)x[a];
+        }
         ok[i] = 1;
         scan_count[keys[i]] += 1;
     }
@@ -401,6 +522,8 @@ InsertResult map_insert(OracleMap& m, const float* xyz, int64_t n, const double*
         if (!spaced) continue;
         MapPoint mp;
         std::memcpy(mp.p, x, sizeof(mp.p));
+        std::memcpy(mp.w, &w64[3 * i], sizeof(mp.w));
+        std::memcpy(mp.tile, &tiles[3 * i], sizeof(mp.tile));
         mp.id = m.next_id++;
         std::memset(mp.cov, 0, sizeof(mp.cov));
         mp.valid = 0;
@@ -421,7 +544,14 @@ void added_covariances(OracleMap& m, InsertResult& res) {
     std::vector<double> covs(6 * res.added.size());
     std::vector<int> valid(res.added.size());
     for (size_t i = 0; i < res.added.size(); ++i) {
-        int found = knn27(m, res.added[i].second->p, m.k, &nb);
+        const MapPoint* p = res.added[i].second;
+        Frame fr;
+        if (m.prec) {
+            fr.tv = m.tv;
+            std::memcpy(fr.f, p->tile, sizeof(fr.f));
+        }
+        // the query is the point itself, centred on its own voxel, in the frame of its tile
+        int found = knn27_at(m, res.added[i].first, p->p, fr, m.k, &nb);
         valid[i] = (found >= m.k) ? 1 : 0;
         if (valid[i]) covariance_eq1(nb, &covs[6 * i]);
         else std::fill(&covs[6 * i], &covs[6 * i] + 6, 0.0);
@@ -475,10 +605,12 @@ std::vector<SourcePoint> scan_local_sources(const float* xyz, int64_t n, float v
     return src;
 }
 
-const MapPoint* nearest27(const OracleMap& m, const float q[3], float* d2_out) {
+// 1-NN over the 27 voxels around the centre key of qf (frame coordinates), smallest
+// (FP32 d^2, id) in frame coordinates.
+const MapPoint* nearest27_frame(const OracleMap& m, const float qf[3], const Frame& fr, float* d2_out) {
     Key c;
     *d2_out = std::numeric_limits<float>::infinity();
-    if (!voxel_key(q, m.inv_v, &c)) return nullptr;
+    if (!frame_key(m, qf, fr, &c)) return nullptr;
     const MapPoint* best = nullptr;
     float bd = std::numeric_limits<float>::infinity();
     for (int dx = -1; dx <= 1; ++dx)
@@ -487,7 +619,9 @@ const MapPoint* nearest27(const OracleMap& m, const float q[3], float* d2_out) {
                 auto it = m.vox.find(Key{c.x + dx, c.y + dy, c.z + dz});
                 if (it == m.vox.end()) continue;
                 for (const MapPoint& p : it->second.pts) {
-                    float d2 = dist2_f32(q, p.p);
+                    float pf[3];
+                    frame_coords(p, fr, pf);
+                    float d2 = dist2_f32(qf, pf);
                     if (best == nullptr || d2 < bd || (d2 == bd && p.id < best->id)) {
                         best = &p;
                         bd = d2;
@@ -496,6 +630,50 @@ const MapPoint* nearest27(const OracleMap& m, const float q[3], float* d2_out) {
             }
     *d2_out = bd;
     return best;
+}
+
+// 1-NN of a query in world FP32 coordinates (frame as in knn27).
+const MapPoint* nearest27(const OracleMap& m, const float q[3], float* d2_out) {
+    Frame fr;
+    float qf[3] = {q[0], q[1], q[2]};
+    if (m.prec) {
+        fr.tv = m.tv;
+        for (int a = 0; a < 3; ++a) {
+            double T = std::floor((double)q[a] / kTile);
+            fr.f[a] = (int32_t)T;
+            qf[a] = (float)((double)q[a] - kTile * T);
+        }
+    }
+    return nearest27_frame(m, qf, fr, d2_out);
+}
+
+// Gauss-Newton anchor: the world origin for the plain map; for the precision variant the
+// corner of the tile holding the initial position, A = 50 floor(t / 50). The linearisation
+// and the update are expressed about A (J = [[q - A]x, -I], T <- exp(xi) applied to the pose
+// relative to A); the GN iterates are the same as about the origin, since exp(Ad_A xi) =
+// A exp(xi) A^-1 and the linear model changes by the same invertible map.
+Frame anchor_frame(const OracleMap& m, const double T[16], double A[3]) {
+    Frame fr;
+    A[0] = A[1] = A[2] = 0.0;
+    if (m.prec) {
+        fr.tv = m.tv;
+        for (int a = 0; a < 3; ++a) {
+            double t = std::floor(T[4 * a + 3] / kTile);
+            fr.f[a] = (int32_t)t;
+            A[a] = kTile * t;
+        }
+    }
+    return fr;
+}
+
+// T <- exp(xi) T about the anchor A (Eq. 6).
+void apply_update(const double xi[6], const double A[3], double T[16]) {
+    double E[16], Tr[16];
+    se3_exp(xi, E);
+    std::memcpy(Tr, T, sizeof(Tr));
+    for (int a = 0; a < 3; ++a) Tr[4 * a + 3] = T[4 * a + 3] - A[a];
+    mat4_mul(E, Tr, T);
+    for (int a = 0; a < 3; ++a) T[4 * a + 3] = T[4 * a + 3] + A[a];
 }
 
 struct LinResult {
@@ -511,10 +689,11 @@ struct LinResult {
 //   Eq. 3 residual d = r - T s; Mahalanobis matrix M = (Sigma_r + R Sigma_s R^T)^-1,
 //   or M = I when either covariance is invalid (SA GICP).
 //   Cauchy (Eq. 5) is applied to e = sqrt(d^T M d): IRLS weight w = 1 / (1 + e^2/kappa^2).
-//   Left perturbation T <- exp(xi) T, xi = [phi; rho]: J = [[q]x, -I].
+//   Left perturbation T <- exp(xi) T, xi = [phi; rho]: J = [[q]x, -I], with q taken
+//   relative to the anchor A (the origin for the plain map, see anchor_frame).
 //   H = sum w J^T M J, g = sum w J^T M d.
-LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, const double T[16], float tau2,
-                    double kappa, int32_t* corr_out) {
+LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, const double T[16], const Frame& fr,
+                    const double A[3], float tau2, double kappa, int32_t* corr_out) {
     LinResult L;
     std::memset(L.H, 0, sizeof(L.H));
     std::memset(L.g, 0, sizeof(L.g));
@@ -528,9 +707,10 @@ LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, con
         const SourcePoint& sp = src[n];
         double q[3];
         for (int i = 0; i < 3; ++i) q[i] = R[i][0] * sp.s[0] + R[i][1] * sp.s[1] + R[i][2] * sp.s[2] + t[i];  // Eq. 2 / Eq. 6
-        float qf[3] = {(float)q[0], (float)q[1], (float)q[2]};
+        // FP32 query in the frame of the anchor (the world frame for the plain map)
+        float qf[3] = {(float)(q[0] - A[0]), (float)(q[1] - A[1]), (float)(q[2] - A[2])};
         float d2;
-        const MapPoint* nn = nearest27(m, qf, &d2);
+        const MapPoint* nn = nearest27_frame(m, qf, fr, &d2);
         if (corr_out) corr_out[n] = -1;
         if (!nn || d2 > tau2) continue;
         if (corr_out) corr_out[n] = (int32_t)nn->id;
@@ -559,14 +739,15 @@ LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, con
                 }
             mat3_inverse(C, M, nullptr);
         }
-        double d[3] = {(double)nn->p[0] - q[0], (double)nn->p[1] - q[1], (double)nn->p[2] - q[2]};  // Eq. 3
+        double d[3] = {nn->w[0] - q[0], nn->w[1] - q[1], nn->w[2] - q[2]};  // Eq. 3
         double Md[3];
         for (int i = 0; i < 3; ++i) Md[i] = M[i][0] * d[0] + M[i][1] * d[1] + M[i][2] * d[2];
         double e2 = d[0] * Md[0] + d[1] * Md[1] + d[2] * Md[2];
         double w = 1.0 / (1.0 + e2 / k2);
         double J[3][6];
         double Q[3][3];
-        skew(q, Q);
+        const double qa[3] = {q[0] - A[0], q[1] - A[1], q[2] - A[2]};  // about the anchor
+        skew(qa, Q);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
                 J[i][j] = Q[i][j];
@@ -606,8 +787,17 @@ struct om_reg_stats {
     double chi2;
 };
 
-OracleMap* om_create(float voxel_size, int nmax, int k, float min_spacing) {
+OracleMap* om_create_prec(float voxel_size, int nmax, int k, float min_spacing, int precision_mode) {
+    int tv = 0;
+    if (precision_mode) {
+        // tiles of 50 m: v must divide 50 m
+        double r = 50.0 / (double)voxel_size;
+        tv = (int)std::lround(r);
+        if (tv < 1 || std::fabs(r - (double)tv) > 1e-9 * r) return nullptr;
+    }
     OracleMap* m = new OracleMap();
+    m->prec = precision_mode ? 1 : 0;
+    m->tv = tv;
     m->v = voxel_size;
     m->inv_v = 1.0f / voxel_size;
     m->nmax = nmax;
@@ -616,6 +806,10 @@ OracleMap* om_create(float voxel_size, int nmax, int k, float min_spacing) {
     float dmin = (min_spacing < 0.0f) ? (float)((double)voxel_size / std::sqrt((double)nmax)) : min_spacing;
     m->dmin2 = dmin * dmin;
     return m;
+}
+
+OracleMap* om_create(float voxel_size, int nmax, int k, float min_spacing) {
+    return om_create_prec(voxel_size, nmax, k, min_spacing, 0);
 }
 
 void om_destroy(OracleMap* m) { delete m; }
@@ -672,7 +866,12 @@ void om_export(const OracleMap* m, int32_t* keys, uint32_t* counts, uint32_t* id
         counts[i] = (uint32_t)vx.pts.size();
         for (const MapPoint& p : vx.pts) {
             ids[pi] = p.id;
-            std::memcpy(xyz + 3 * pi, p.p, 3 * sizeof(float));
+            if (m->prec) {
+                // world FP32: fp32(50 T + x_t), the tile-relative value restored exactly in FP64
+                for (int a = 0; a < 3; ++a) xyz[3 * pi + a] = (float)(kTile * (double)p.tile[a] + (double)p.p[a]);
+            } else {
+                std::memcpy(xyz + 3 * pi, p.p, 3 * sizeof(float));
+            }
             std::memcpy(cov + 6 * pi, p.cov, 6 * sizeof(double));
             valid[pi] = p.valid;
             ++pi;
@@ -730,7 +929,9 @@ void om_linearize(const OracleMap* m, const float* src_xyz, const double* src_co
         src[i].index = i;
     }
     float tau2 = tau * tau;
-    LinResult L = linearize(*m, src, pose, tau2, kappa, corr);
+    double A[3];
+    Frame fr = anchor_frame(*m, pose, A);
+    LinResult L = linearize(*m, src, pose, fr, A, tau2, kappa, corr);
     std::memcpy(H, L.H, sizeof(L.H));
     std::memcpy(g, L.g, sizeof(L.g));
     *n_corr = L.n_corr;
@@ -756,7 +957,7 @@ int om_gn_step(const double* H, const double* g, const double* T, double* xi_out
 
 // Full registration (Sec. III-A.2): scan-local map, source covariances, then
 // Gauss-Newton iterations until ||xi|| <= conv_eps or max_iters.
-// out_cov = H^-1 of the last linearisation, ordered [rotation; translation].
+// out_cov = H^-1 of the last linearisation, ordered [rotation; translation], about the anchor.
 int om_register(const OracleMap* m, const float* xyz, int64_t n, const double* init, const om_reg_params* prm,
                 double* out_pose, double* out_cov, om_reg_stats* st) {
     std::vector<SourcePoint> src = scan_local_sources(xyz, n, m->v, m->nmax, m->k, m->dmin2, nullptr);
@@ -772,8 +973,10 @@ int om_register(const OracleMap* m, const float* xyz, int64_t n, const double* i
     st->chi2 = 0;
     double Hlast[36] = {0};
     bool have_h = false;
+    double A[3];
+    const Frame fr = anchor_frame(*m, init, A);
     for (uint32_t it = 0; it < prm->max_iters; ++it) {
-        LinResult L = linearize(*m, src, T, tau2, prm->kappa, nullptr);
+        LinResult L = linearize(*m, src, T, fr, A, tau2, prm->kappa, nullptr);
         st->n_corr = (uint32_t)L.n_corr;
         st->n_p2p = (uint32_t)L.n_p2p;
         st->chi2 = L.chi2;
@@ -785,9 +988,7 @@ int om_register(const OracleMap* m, const float* xyz, int64_t n, const double* i
         double mg[6], xi[6];
         for (int i = 0; i < 6; ++i) mg[i] = -L.g[i];
         cholesky6_solve(Lc, mg, xi);
-        double E[16];
-        se3_exp(xi, E);
-        mat4_mul(E, T, T);  // Eq. 6: the increment is applied on the left
+        apply_update(xi, A, T);  // Eq. 6: the increment is applied on the left, about the anchor
         st->iters = it + 1;
         double nx = 0;
         for (int i = 0; i < 6; ++i) nx += xi[i] * xi[i];

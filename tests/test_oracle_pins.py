@@ -498,3 +498,159 @@ def test_threshold_closed_forms():
     delta = 2 * 100.0 * math.sin(th / 2) + 0.2
     sigma = math.sqrt((0.25 + delta ** 2) / 2)
     assert thr.get() == pytest.approx((3 * sigma, sigma / 3))
+
+
+# ----------------------------------------------------------------------------- precision variant (50 m tiles)
+def _exact_voxel_index(x32, t64, v):
+    """floor((x + t) / v) in exact rational arithmetic (x FP32, t FP64)."""
+    from fractions import Fraction
+    return [math.floor((Fraction(float(a)) + Fraction(float(b))) / Fraction(v)) for a, b in zip(x32, t64)]
+
+
+@pytest.mark.parametrize("offset", [(0.0, 0.0, 0.0), (1e5 + 0.37, -3.1e4 - 0.81, 212.6)])
+def test_prec_tile_keys_are_the_exact_voxel_index(offset):
+    """Tile keys (T tv + in-tile index) equal floor(x / v) computed exactly, for points not
+    within rounding distance of a voxel face, near the origin and 100 km away; the exported
+    world point is within the tile-relative FP32 rounding of the FP64 point."""
+    rng = np.random.default_rng(21)
+    v = 0.5
+    n = 600
+    cells = rng.integers(-90, 90, size=(n, 3))
+    local = ((cells + rng.uniform(0.02, 0.98, size=(n, 3))) * 0.6).astype(np.float32)
+    T = synth.make_pose(np.eye(3), offset)
+    m = oracle.OracleMap(v, 64, 1, min_spacing=0.0, precision_mode=1)
+    m.insert(local, T)
+    ex = m.export()
+    keys_of = {}
+    pi = 0
+    for key, c in zip(ex["keys"], ex["counts"]):
+        for j in range(c):
+            keys_of[int(ex["ids"][pi])] = (tuple(int(x) for x in key), ex["xyz"][pi])
+            pi += 1
+    assert len(keys_of) == n
+    checked = 0
+    for i in range(n):
+        w = local[i].astype(np.float64) + np.asarray(offset)
+        key, xyz = keys_of[i]
+        frac = w / v - np.floor(w / v)
+        if np.all(np.minimum(frac, 1 - frac) > 1e-6):
+            assert list(key) == _exact_voxel_index(local[i], offset, v), i
+            checked += 1
+        # tile-relative FP32 (half an ulp of 32..64 m = 2^-19 m), then one rounding to FP32 world
+        bound = 2.0 ** -19 + np.spacing(np.abs(w).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(xyz.astype(np.float64) - w) <= bound), (i, xyz, w)
+    assert checked > 0.95 * n
+
+
+def _problem_points(seed, n_prior=4, lidar=None):
+    p = synth.single_scan_problem(seed, lidar=lidar or synth.lidar_beams(32, 512), n_prior=n_prior)
+    return p
+
+
+def test_prec_translation_equivariance_at_100_km():
+    """Moving the whole problem by D (a multiple of 50 m, here ~100 km) moves every tile key by
+    D / v, keeps ids, counts and covariances, and the registered pose moves by D exactly (to
+    FP64 rounding). The plain FP32 map does not have this property at that distance."""
+    p = _problem_points(3)
+    D = np.array([50.0 * 2003, -50.0 * 611, 50.0 * 3])
+    shift = synth.make_pose(np.eye(3), D)
+    maps = []
+    for d in (np.zeros(3), D):
+        S = synth.make_pose(np.eye(3), d)
+        m = oracle.OracleMap(0.5, 20, 5, precision_mode=1)
+        for s, T in zip(p.map_scans, p.map_poses):
+            m.insert(s, S @ T)
+        maps.append(m)
+    a, b = maps[0].export(), maps[1].export()
+    np.testing.assert_array_equal(b["keys"], a["keys"] + (D / 0.5).astype(np.int32))
+    np.testing.assert_array_equal(a["counts"], b["counts"])
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    np.testing.assert_array_equal(a["valid"], b["valid"])
+    np.testing.assert_allclose(b["cov"], a["cov"], rtol=1e-7, atol=1e-7)
+    kw = dict(max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+    P0, _, s0 = maps[0].register(p.query, p.init, **kw)
+    P1, _, s1 = maps[1].register(p.query, shift @ p.init, **kw)
+    assert s0["n_corr"] == s1["n_corr"]
+    D01 = np.linalg.inv(shift @ P0) @ P1
+    assert np.linalg.norm(D01[:3, 3]) < 1e-7
+    assert abs(np.trace(D01[:3, :3]) - 3) < 1e-12
+    # the plain map quantises world points to FP32 (7.8 mm at 100 km): it moves by more
+    m = oracle.OracleMap(0.5, 20, 5)
+    for s, T in zip(p.map_scans, p.map_poses):
+        m.insert(s, shift @ T)
+    P2, _, _ = m.register(p.query, shift @ p.init, **kw)
+    D02 = np.linalg.inv(shift @ P0) @ P2
+    assert np.linalg.norm(D02[:3, 3]) > 1e-4
+
+
+def test_prec_anchor_leaves_gauss_newton_unchanged():
+    """On inputs whose FP32 world points are exact (a 1/1024 m grid, axis-aligned poses with
+    integer translations), the plain map and the precision variant hold the same points, so
+    the only difference left is the linearisation about the tile-corner anchor instead of the
+    origin, which must not change the Gauss-Newton iterates (exp(Ad_A xi) = A exp(xi) A^-1)."""
+    rng = np.random.default_rng(23)
+    scene = synth.walls_scene(5)
+    lidar = synth.Lidar(32, 512, -15.0, 15.0, 1.0, 60.0, 0.01)
+    poses = [synth.make_pose(np.eye(3), [73.0 + i, 41.0, 1.0]) for i in range(4)]
+    scans = []
+    for i, T in enumerate(poses):
+        s = synth.raycast(scene, lidar, synth.make_pose(np.eye(3), [i, 0.0, 1.8]), 5, i)
+        scans.append((np.round(s.astype(np.float64) * 1024) / 1024).astype(np.float32))
+    plain = oracle.OracleMap(0.5, 20, 5)
+    prec = oracle.OracleMap(0.5, 20, 5, precision_mode=1)
+    for s, T in zip(scans, poses):
+        plain.insert(s, T)
+        prec.insert(s, T)
+    a, b = plain.export(), prec.export()
+    np.testing.assert_array_equal(a["keys"], b["keys"])
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    np.testing.assert_array_equal(a["xyz"], b["xyz"])
+    np.testing.assert_allclose(a["cov"], b["cov"], rtol=0, atol=1e-12)
+    query = synth.raycast(scene, lidar, synth.make_pose(np.eye(3), [1.5, 0.0, 1.8]), 6, 9)
+    truth = synth.make_pose(np.eye(3), [74.5, 41.0, 1.0])
+    init = truth @ synth.random_offset(rng, 1.5, 0.3)
+    kw = dict(max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+    P0, C0, s0 = plain.register(query, init, **kw)
+    P1, C1, s1 = prec.register(query, init, **kw)
+    assert s0["n_corr"] == s1["n_corr"] and s0["status"] == s1["status"] == 0
+    np.testing.assert_allclose(P1, P0, rtol=0, atol=1e-9)
+
+
+def test_prec_rejects_voxel_sizes_that_do_not_divide_the_tile():
+    with pytest.raises(ValueError):
+        oracle.OracleMap(0.3, 20, 5, precision_mode=1)
+    oracle.OracleMap(0.25, 20, 5, precision_mode=1)
+    oracle.OracleMap(1.0, 20, 5, precision_mode=1)
+
+
+def test_prec_stage_queries_use_the_query_tile_frame():
+    """Stage kNN / 1-NN of world queries: near the origin (exact inputs) the precision variant
+    returns the plain map's neighbours; 100 km away it returns the same ids shifted with the map."""
+    rng = np.random.default_rng(24)
+    pts = dyadic_cloud(rng, 3000, -8, 8)
+    q = dyadic_cloud(rng, 300, -7, 7) + np.float32(1.0 / 2048)
+    plain = oracle.OracleMap(0.5, 20, 5, min_spacing=0.0)
+    prec = oracle.OracleMap(0.5, 20, 5, min_spacing=0.0, precision_mode=1)
+    plain.insert(pts)
+    prec.insert(pts)
+    ia, fa = plain.knn(q, 5)
+    ib, fb = prec.knn(q, 5)
+    np.testing.assert_array_equal(ia, ib)
+    np.testing.assert_array_equal(fa, fb)
+    na, da = plain.nearest(q, 1.0)
+    nb, db = prec.nearest(q, 1.0)
+    np.testing.assert_array_equal(na, nb)
+    np.testing.assert_array_equal(da, db)
+    # far away: the FP32 query is rounded at 100 km (7.8 mm), so compare against the
+    # oracle's own map built at the rounded query positions' frame: same ids as a brute force
+    D = np.array([1e5, 0.0, 0.0])
+    far = oracle.OracleMap(0.5, 20, 5, min_spacing=0.0, precision_mode=1)
+    far.insert(pts, synth.make_pose(np.eye(3), D))
+    qf = (q.astype(np.float64) + D).astype(np.float32)
+    ids, d2 = far.nearest(qf, 1.0)
+    wpts = pts.astype(np.float64) + D
+    for i in range(len(q)):
+        dd = np.sum((wpts - qf[i].astype(np.float64)) ** 2, axis=1)
+        j = int(np.argmin(dd))
+        if dd[j] < 0.25 and np.sort(dd)[1] - dd[j] > 1e-4:
+            assert ids[i] == j
