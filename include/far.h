@@ -59,7 +59,15 @@ typedef struct far_map_params {
     uint64_t max_voxels;        /* size of the bucket pool (live voxels) */
     float load_factor;          /* hash slots = next_pow2(max_voxels / load_factor), 0.05..0.95 */
     uint32_t max_scan_points;   /* largest scan accepted by insert / register */
-    uint32_t precision_mode;    /* 0: FP32 map coordinates (only mode of this version) */
+    uint32_t precision_mode;    /* 0: FP32 world coordinates, FP32 covariances.
+                                 * 1: mixed-precision storage: points FP32 relative to the origin of
+                                 *    their 50 m tile (tile T = floor(x / 50), key = T * 50/v +
+                                 *    clamp(floor(fp32(x - 50 T) * fp32(1/v)), 0, 50/v - 1), with the
+                                 *    world point in FP64), covariances FP16 with one power-of-two
+                                 *    exponent per voxel, Gauss-Newton linearised about the corner of
+                                 *    the tile holding the initial position (same iterates; the FP32
+                                 *    arithmetic runs on small numbers). v must divide 50 m, else
+                                 *    FAR_ERR_INVALID. */
 } far_map_params;
 
 /* Adaptive Submap Density cap of an insert (Sec. III-A.3). */
@@ -138,6 +146,8 @@ far_status far_map_size(const far_map* map, uint64_t* n_voxels, uint64_t* n_poin
  * keys[3 * voxels], counts[voxels], ids[points], xyz[3 * points],
  * cov[6 * points] (xx xy xz yy yz zz), valid[points]. Capacities are checked
  * against far_map_size(); any pointer except keys/counts may be NULL.
+ * precision_mode 1: xyz = fp32(50 T + tile-relative value) and the FP16
+ * covariances decoded to FP32.
  */
 far_status far_map_export(const far_map* map, int32_t* keys, uint32_t* counts, uint32_t* ids, float* xyz,
                           float* cov, uint8_t* valid, uint64_t cap_voxels, uint64_t cap_points);
@@ -145,6 +155,8 @@ far_status far_map_export(const far_map* map, int32_t* keys, uint32_t* counts, u
 /*
  * 1-NN over the 27 voxels around each query point's voxel (Sec. III-A.2):
  * smallest FP32 d^2 = ((dx*dx + dy*dy) + dz*dz), ties to the smaller id.
+ * precision_mode 1: the distance is taken in the frame of the query's tile
+ * (query fp32(q - 50 T_q), map point fp32(p_tile + 50 (T_p - T_q))).
  * out_ids[i] = id, or -1 when there is no candidate or d^2 > fp32(tau)^2.
  * out_d2 (may be NULL) receives d^2 (+inf without a candidate).
  * Outputs may be host or device pointers.
@@ -172,7 +184,8 @@ far_status far_scan_sources(far_map* map, const float* xyz, uint64_t n, uint32_t
 
 /*
  * One Gauss-Newton linearisation of Eq. 4 at `pose` without the update:
- * H (36, row-major) and g (6) as defined by J = [[q]x, -I], IRLS Cauchy weights
+ * H (36, row-major) and g (6) as defined by J = [[q - A]x, -I] with the anchor A
+ * (the origin; precision_mode 1: 50 floor(t / 50) of the pose's translation), IRLS Cauchy weights
  * w = 1 / (1 + e^2 / kappa^2), e^2 = d^T M d, M = (Sigma_r + R Sigma_s R^T)^-1
  * or I when either covariance is invalid. out_corr[n_src] (may be NULL) receives
  * the map id matched by each source point or -1. Host outputs.

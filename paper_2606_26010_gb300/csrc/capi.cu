@@ -92,6 +92,7 @@ struct far_map {
     bool ev_used[EV_COUNT_FIXED] = {};
     u32 gn_launched = 0;
     far_stage_times last{};
+    GnArgs last_gn{};                // arguments of the last registration (footprint diagnostics)
 };
 
 namespace {
@@ -108,7 +109,15 @@ far_status validate_params(const far_map_params* p) {
         return fail(FAR_ERR_INVALID, "load_factor must be in [0.05, 0.95]");
     if (p->max_scan_points < 1 || p->max_scan_points > (1u << 26))
         return fail(FAR_ERR_INVALID, "max_scan_points must be in 1..2^26");
-    if (p->precision_mode != 0) return fail(FAR_ERR_INVALID, "precision_mode %u is not supported", p->precision_mode);
+    if (p->precision_mode > 1) return fail(FAR_ERR_INVALID, "precision_mode %u is not supported", p->precision_mode);
+    if (p->precision_mode == 1) {
+        // 50 m tiles: the voxel size must divide the tile
+        const double r = 50.0 / (double)p->voxel_size;
+        const long tv = std::lround(r);
+        if (tv < 1 || std::fabs(r - (double)tv) > 1e-9 * r || tv > (1 << 20))
+            return fail(FAR_ERR_INVALID, "precision_mode 1 needs a voxel size that divides 50 m (got %g)",
+                        (double)p->voxel_size);
+    }
     if ((double)p->max_voxels * p->max_pts_per_voxel >= 4294967295.0)
         return fail(FAR_ERR_INVALID, "max_voxels * max_pts_per_voxel must stay below 2^32");
     if ((double)p->max_voxels / p->load_factor > 2147483648.0)
@@ -139,7 +148,15 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     add((void**)&t->map.slots, (size_t)pl.cap * sizeof(Slot));
     add((void**)&t->map.slots_alt, (size_t)pl.cap * sizeof(Slot));
     add((void**)&t->map.pts, (size_t)pl.max_buckets * pl.nmax * sizeof(float4));
-    add((void**)&t->map.cov, (size_t)pl.max_buckets * pl.nmax * 2 * sizeof(float4));
+    const bool prec = p.precision_mode == 1;
+    if (prec) {
+        // FP16 covariances (12 B per point) and one exponent per voxel
+        add((void**)&t->map.cov_h4, (size_t)pl.max_buckets * pl.nmax * sizeof(uint2));
+        add((void**)&t->map.cov_h2, (size_t)pl.max_buckets * pl.nmax * sizeof(u32));
+        add((void**)&t->map.cexp, (size_t)pl.max_buckets * sizeof(int));
+    } else {
+        add((void**)&t->map.cov, (size_t)pl.max_buckets * pl.nmax * 2 * sizeof(float4));
+    }
     add((void**)&t->map.ring, (size_t)pl.max_buckets * sizeof(u32));
     add((void**)&t->map.ctr, sizeof(MapCounters));
     // scan-local map
@@ -171,6 +188,16 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     add((void**)&t->d_cov36, 36 * sizeof(double));
     add((void**)&t->s.touched, (size_t)pl.cap * sizeof(u32));
     add((void**)&t->s.foot, 2 * sizeof(unsigned long long));
+    if (prec) {
+        add((void**)&t->s.cov_tmp, n * 2 * sizeof(float4));
+        add((void**)&t->s.added_key, n * sizeof(u64));
+        add((void**)&t->s.grp_bucket, (n + 1) * sizeof(u32));
+        add((void**)&t->s.grp_cnt0, (n + 1) * sizeof(u32));
+        add((void**)&t->s.grp_exp0, (n + 1) * sizeof(int));
+        add((void**)&t->s.src_h4, n * sizeof(uint2));
+        add((void**)&t->s.src_h2, n * sizeof(u32));
+        add((void**)&t->s.src_exp, n);
+    }
     return pl;
 }
 
@@ -303,6 +330,7 @@ void collect_times(far_map* m, u32 iters_done, u32 status) {
 // Launch the Gauss-Newton chain (max_iters iterations of linearise + solve), marking the
 // start, the end of each linearisation and the end of each solve when profiling.
 far_status run_gn(far_map* m, const GnArgs& a, u32 n_upper, u32 iters) {
+    m->last_gn = a;
     mark(m, EV_GN0);
     for (u32 it = 0; it < iters; ++it) {
         u32 nb = 0;
@@ -330,10 +358,24 @@ far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
     return FAR_OK;
 }
 
-GnArgs gn_args(far_map* m, u32 n, float tau, float kappa, double conv_eps, int update, int32_t* corr,
-               double budget_s, int tpp = 0) {
+// pose: the initial pose; for the precision variant it fixes the linearisation anchor, the
+// corner A = 50 floor(t / 50) of the tile holding the initial position.
+GnArgs gn_args(far_map* m, const double* pose, u32 n, float tau, float kappa, double conv_eps, int update,
+               int32_t* corr, double budget_s, int tpp = 0) {
     GnArgs a;
     a.tpp = tpp;
+    for (int j = 0; j < 3; ++j) {
+        a.anchor[j] = 0.0;
+        a.ftile[j] = 0;
+        if (m->map.tv > 0) {
+            const double T = std::floor(pose[4 * j + 3] / 50.0);
+            a.ftile[j] = (int)T;
+            a.anchor[j] = 50.0 * T;
+        }
+    }
+    a.src_h4 = m->s.src_h4;
+    a.src_h2 = m->s.src_h2;
+    a.src_exp = m->s.src_exp;
     a.map = m->map.view();
     a.src = m->s.src;
     a.src_cov = m->s.src_cov;
@@ -425,6 +467,7 @@ far_status far_map_create(const far_map_params* params, void* cuda_stream, far_m
         d->inv_v = 1.0f / v;
         d->dmin2 = dmin * dmin;
     }
+    if (params->precision_mode == 1) m->map.tv = (int)std::lround(50.0 / (double)v);
     m->map.cap = pl.cap;
     m->map.mask = pl.cap - 1;
     m->map.key_bits = log2_u32(pl.cap) + 1;
@@ -569,10 +612,12 @@ far_status far_map_export(const far_map* cmap, int32_t* keys, uint32_t* counts, 
         return x[2] < y[2];
     });
     std::vector<u32> sb(hn), sc(hn), so(hn);
+    std::vector<u64> sk(hn);
     u32 total = 0;
     for (u32 i = 0; i < hn; ++i) {
         sb[i] = hb[order[i]];
         sc[i] = hc[order[i]];
+        sk[i] = hk[order[i]];
         so[i] = total;
         total += sc[i];
         std::memcpy(keys + 3 * (size_t)i, &kk[3 * (size_t)order[i]], 3 * sizeof(int32_t));
@@ -586,7 +631,8 @@ far_status far_map_export(const far_map* cmap, int32_t* keys, uint32_t* counts, 
     e = cudaMemcpy(d_buckets, sb.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_counts, sc.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_off, so.data(), hn * sizeof(u32), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = map_gather(map->map, d_buckets, d_counts, d_off, hn, d_pts, d_cov, map->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(d_keys, sk.data(), hn * sizeof(u64), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = map_gather(map->map, d_buckets, d_counts, d_off, d_keys, hn, d_pts, d_cov, map->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(map->stream);
     if (e == cudaSuccess && total) e = cudaMemcpy(hp.data(), d_pts, total * sizeof(float4), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && total)
@@ -690,7 +736,7 @@ far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t st
         CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
     }
     CK(gn_begin(map->s.st, pose, map->s.scal + SCAL_NADMIT, map->stream));
-    GnArgs a = gn_args(map, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0);
+    GnArgs a = gn_args(map, pose, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0);
     reset_marks(map);
     if ((st = run_gn(map, a, std::max(nn, 1u), 1)) != FAR_OK) return st;
     mark(map, EV_END);
@@ -735,7 +781,7 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
         CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
     }
     CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
-    GnArgs a = gn_args(map, std::max(nn, 1u), params->tau, params->kappa, params->conv_eps, 1, nullptr,
+    GnArgs a = gn_args(map, init_pose, std::max(nn, 1u), params->tau, params->kappa, params->conv_eps, 1, nullptr,
                        params->time_budget_s, (int)params->threads_per_point);
     if ((st = run_gn(map, a, std::max(nn, 1u), params->max_iters)) != FAR_OK) return st;
     mark(map, EV_END);
@@ -792,8 +838,8 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
         CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
     }
     CK(gn_begin(map->s.st, init_pose, map->s.scal + SCAL_NADMIT, map->stream));
-    GnArgs a = gn_args(map, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr, reg->time_budget_s,
-                       (int)reg->threads_per_point);
+    GnArgs a = gn_args(map, init_pose, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr,
+                       reg->time_budget_s, (int)reg->threads_per_point);
     if ((st = run_gn(map, a, std::max(nn, 1u), reg->max_iters)) != FAR_OK) return st;
     if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
     mark(map, EV_INSERT);
@@ -975,7 +1021,8 @@ far_status batch_enqueue(far_batch* b, const float* const* xyz, const uint64_t* 
     }
     CK(gn_batch_begin(b->d_probs, np, b->d_init, b->stream));
     for (u32 it = 0; it < iters; ++it)
-        CK(gn_batch_iteration(b->d_probs, b->d_block_prob, b->total_blocks, np, tpp, b->stream));
+        CK(gn_batch_iteration(b->d_probs, b->d_block_prob, b->total_blocks, np, tpp, b->maps[0]->map.tv > 0,
+                              b->stream));
     if (ins) {
         CK(cudaEventRecord(b->ev_fork2, b->stream));
         for (cudaStream_t s : b->side) CK(cudaStreamWaitEvent(s, b->ev_fork2, 0));
@@ -1062,7 +1109,8 @@ void batch_set_args(far_batch* b, const uint64_t* n, const double* init_poses, c
     for (u32 p = 0; p < np; ++p) {
         const u32 n_up = (u32)std::max<uint64_t>(n[p], 1);
         const far_reg_params& q = params[params_count == 1 ? 0 : p];
-        b->h_probs[p].args = gn_args(b->maps[p], n_up, q.tau, q.kappa, q.conv_eps, 1, nullptr, q.time_budget_s, tpp);
+        b->h_probs[p].args = gn_args(b->maps[p], init_poses + 16 * (size_t)p, n_up, q.tau, q.kappa, q.conv_eps, 1,
+                                     nullptr, q.time_budget_s, tpp);
     }
     std::memcpy(b->h_init, init_poses, np * 16 * sizeof(double));
 }
@@ -1106,6 +1154,8 @@ far_status far_batch_create(far_map* const* maps, uint32_t count, void* cuda_str
         if (!maps[i]) return fail(FAR_ERR_INVALID, "maps[%u] is NULL", i);
         for (uint32_t j = 0; j < i; ++j)
             if (maps[j] == maps[i]) return fail(FAR_ERR_INVALID, "a map appears twice in the batch");
+        if (maps[i]->p.precision_mode != maps[0]->p.precision_mode)
+            return fail(FAR_ERR_INVALID, "all maps of a batch must use the same precision_mode");
     }
     far_batch* b = new far_batch();
     b->maps.assign(maps, maps + count);
@@ -1238,8 +1288,11 @@ far_status far_get_stage_times(const far_map* map, far_stage_times* out) {
 
 far_status far_gn_footprint(far_map* map, uint64_t out[3]) {
     if (!map || !out) return fail(FAR_ERR_INVALID, "NULL argument");
-    CK(gn_footprint(map->map.view(), map->s.src, map->s.st, map->s.touched, map->map.cap, map->s.foot,
-                    map->p.max_scan_points, map->stream));
+    GnArgs a = map->last_gn;
+    a.map = map->map.view();
+    a.src = map->s.src;
+    a.st = map->s.st;
+    CK(gn_footprint(a, map->s.touched, map->map.cap, map->s.foot, map->p.max_scan_points, map->stream));
     unsigned long long f[2];
     CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
     CK(cudaMemcpyAsync(f, map->s.foot, sizeof(f), cudaMemcpyDeviceToHost, map->stream));

@@ -9,9 +9,18 @@
 //                 bucket b occupies pts[b * N, b * N + N).
 //   cov[2 B N]    two float4 per point {c00 c01 c02 c11} {c12 c22 valid 0}.
 //   ring[B]       free-bucket ring (allocation at head, eviction returns at tail).
+//
+// Precision variant (precision_mode = 1, 50 m tiles):
+//   pts           {x, y, z} relative to the origin of the voxel's 50 m tile, id bits.
+//   cov_h4[B N]   FP16 {c00 c01 c02 c11} per point,
+//   cov_h2[B N]   FP16 {c12 c22} per point: the values are Sigma / 2^E with E the
+//                 voxel's exponent; a zero c00 marks an invalid covariance.
+//   cexp[B]       per-voxel exponent E (the largest entry of any point of the voxel
+//                 is below 2^E), raised as points arrive (older entries rescaled).
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace far {
@@ -39,6 +48,9 @@ constexpr int KEY_BIAS = 1 << 20;         // keys lie in [-2^20, 2^20)
 constexpr float KEY_LIMIT = 1048576.0f;
 constexpr int KMAX = 16;                  // largest k of the kNN kernels
 constexpr int NMAX_LIMIT = 64;            // largest N_max
+constexpr float TILE_M = 50.0f;           // tile side of the precision variant
+constexpr double TILE_D = 50.0;
+constexpr int EXP_NONE = -1000;           // voxel without a valid FP16 covariance yet
 
 enum ErrFlag : u32 {
     ERR_TABLE_FULL = 1u,
@@ -75,12 +87,16 @@ struct MapCounters {
 struct MapView {
     const Slot* slots;
     const float4* pts;
-    const float4* cov;   // may be null (scan-local map)
+    const float4* cov;   // may be null (scan-local map, precision variant)
     const MapCounters* ctr;
     u32 mask;
     u32 nmax;
     float inv_v;
     float v;
+    int tv;              // voxels per tile side (precision variant), else 0
+    const uint2* cov_h4; // precision variant covariances (see above)
+    const u32* cov_h2;
+    const int* cexp;
 };
 
 // Registration state kept on the device between Gauss-Newton launches.
@@ -169,6 +185,61 @@ __device__ __forceinline__ bool find_slot(const Slot* __restrict__ slots, u32 ma
 // (d2, id) lexicographic "better than"
 __device__ __forceinline__ bool better(float d2, u32 id, float bd2, u32 bid) {
     return d2 < bd2 || (d2 == bd2 && id < bid);
+}
+
+// ----------------------------------------------------------------------------- precision variant
+__device__ __forceinline__ int floor_div(int k, int tv) { return k >= 0 ? k / tv : -((-k + tv - 1) / tv); }
+
+// Tile reading: T = floor(x / 50) (FP64), x_t = fp32(x - 50 T), key = T tv + clamp(floor(fp32(x_t * inv_v)),
+// 0, tv - 1). Returns false when x is not finite or the key leaves [-2^20, 2^20).
+__device__ __forceinline__ bool tile_key_axis(double x, float inv_v, int tv, int& key, float& local) {
+    if (!isfinite(x)) return false;
+    const double T = floor(__ddiv_rn(x, TILE_D));
+    if (!(fabs(T) * (double)tv < (double)KEY_BIAS)) return false;
+    const float xt = __double2float_rn(__dsub_rn(x, __dmul_rn(TILE_D, T)));
+    int kin = (int)floorf(__fmul_rn(xt, inv_v));
+    kin = kin < 0 ? 0 : (kin > tv - 1 ? tv - 1 : kin);
+    const long long k = (long long)T * tv + kin;
+    if (k < -(long long)KEY_BIAS || k >= (long long)KEY_BIAS) return false;
+    key = (int)k;
+    local = xt;
+    return true;
+}
+
+// 2^e as a float for |e| <= 126 (exact power of two).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// Exponent E with every |c_j| < 2^E (frexp of the largest magnitude); EXP_NONE for all zeros.
+__device__ __forceinline__ int cov_exponent(const float (&c)[6]) {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) m = fmaxf(m, fabsf(c[j]));
+    if (!(m > 0.f) || !isfinite(m)) return EXP_NONE;
+    int e;
+    frexpf(m, &e);
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// FP16 record of c / 2^E (round to nearest).
+__device__ __forceinline__ void cov16_encode(const float (&c)[6], int E, uint2& h4, u32& h2) {
+    const float s = pow2f(-E);
+    const __half h[6] = {__float2half_rn(c[0] * s), __float2half_rn(c[1] * s), __float2half_rn(c[2] * s),
+                         __float2half_rn(c[3] * s), __float2half_rn(c[4] * s), __float2half_rn(c[5] * s)};
+    h4.x = (u32)__half_as_ushort(h[0]) | ((u32)__half_as_ushort(h[1]) << 16);
+    h4.y = (u32)__half_as_ushort(h[2]) | ((u32)__half_as_ushort(h[3]) << 16);
+    h2 = (u32)__half_as_ushort(h[4]) | ((u32)__half_as_ushort(h[5]) << 16);
+}
+
+// Decode; returns false for an invalid record (c00 == 0).
+__device__ __forceinline__ bool cov16_decode(uint2 h4, u32 h2, int E, float (&c)[6]) {
+    const float s = pow2f(E < -100 ? -100 : E);
+    c[0] = __half2float(__ushort_as_half((unsigned short)(h4.x & 0xFFFFu))) * s;
+    c[1] = __half2float(__ushort_as_half((unsigned short)(h4.x >> 16))) * s;
+    c[2] = __half2float(__ushort_as_half((unsigned short)(h4.y & 0xFFFFu))) * s;
+    c[3] = __half2float(__ushort_as_half((unsigned short)(h4.y >> 16))) * s;
+    c[4] = __half2float(__ushort_as_half((unsigned short)(h2 & 0xFFFFu))) * s;
+    c[5] = __half2float(__ushort_as_half((unsigned short)(h2 >> 16))) * s;
+    return (h4.x & 0xFFFFu) != 0u;
 }
 
 }  // namespace far

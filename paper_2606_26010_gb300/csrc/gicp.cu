@@ -132,16 +132,18 @@ __device__ __forceinline__ u32 warp_sum_u(u32 v) {
 // TPP (lane sl takes entry round * TPP + sl); after each round the group shares its best
 // packed key (d2 bits << 32 | id, ordered like (d2, id) since d2 >= 0), and a voxel whose
 // box distance exceeds min(best, tau^2) is skipped. Candidates are loaded four at a time.
-// Every lane of the warp must call this (full-warp shuffles).
-template <int TPP>
-__device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, float qx, float qy, float qz,
-                                              float limit2, bool active, int sl, unsigned long long& best_key,
-                                              u32& best_pos) {
+// best_v is the c_nb_order index of the winner's voxel (its frame offset in the precision
+// variant). Every lane of the warp must call this (full-warp shuffles).
+template <int TPP, bool PREC>
+__device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
+                                              float limit2, int sl, unsigned long long& best_key, u32& best_pos,
+                                              int& best_v) {
     best_key = ~0ull;
     best_pos = 0;
-    int kx = 0, ky = 0, kz = 0;
-    const bool keyed = active && voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz);
-    const FaceDist fd = face_distances(qx, qy, qz, kx, ky, kz, m.v);
+    best_v = 0;
+    const float qx = f.q[0], qy = f.q[1], qz = f.q[2];
+    const int kx = f.k[0], ky = f.k[1], kz = f.k[2];
+    const FaceDist fd = face_distances(qx, qy, qz, f.lk[0], f.lk[1], f.lk[2], m.v);
     constexpr int kRounds = (27 + TPP - 1) / TPP;
     for (int round = 0; round < kRounds; ++round) {
         const int v = round * TPP + sl;
@@ -154,11 +156,18 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, f
             if (!(box_lb2(fd, dx, dy, dz) > bound) && key_in_range(nx) && key_in_range(ny) && key_in_range(nz) &&
                 find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) {
                 const u32 base = bucket * m.nmax;
+                const float ox = f.off(0, dx), oy = f.off(1, dy), oz = f.off(2, dz);
                 for (u32 j0 = 0; j0 < count; j0 += 4) {
                     float4 c[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < 4; ++u) {
                         c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if constexpr (PREC) {
+                            c[u].x = __fadd_rn(c[u].x, ox);
+                            c[u].y = __fadd_rn(c[u].y, oy);
+                            c[u].z = __fadd_rn(c[u].z, oz);
+                        }
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         if (j0 + u < count) {
@@ -168,6 +177,7 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, f
                             if (key < best_key) {
                                 best_key = key;
                                 best_pos = base + j0 + u;
+                                if constexpr (PREC) best_v = v;
                             }
                         }
                     }
@@ -178,9 +188,12 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, f
         for (int o = TPP / 2; o > 0; o >>= 1) {
             const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best_key, o);
             const u32 op = __shfl_xor_sync(0xffffffffu, best_pos, o);
+            int ov = 0;
+            if constexpr (PREC) ov = __shfl_xor_sync(0xffffffffu, best_v, o);
             if (ok < best_key) {
                 best_key = ok;
                 best_pos = op;
+                if constexpr (PREC) best_v = ov;
             }
         }
     }
@@ -189,14 +202,20 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, f
 // Linearisation half of a Gauss-Newton iteration: TPP lanes cooperate on each source
 // point's search, the group's first lane linearises it, and every block writes its
 // partial sums (FP32 within warps, FP64 across the block's warps).
-template <int TPP>
+template <int TPP, bool PREC>
 __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vgrid) {
     __shared__ float red[GN_THREADS / 32][NACC + 2];
     __shared__ float pose_f[12];
     __shared__ u32 s_flag;
     RegState* st = a.st;
     if (threadIdx.x == 0) s_flag = *reinterpret_cast<volatile u32*>(&st->done);
-    if (threadIdx.x < 12) pose_f[threadIdx.x] = (float)st->T[threadIdx.x];
+    if (threadIdx.x < 12) {
+        // the pose relative to the anchor (translation column minus A, in FP64, then rounded)
+        const int j = threadIdx.x;
+        double t = st->T[j];
+        if ((j & 3) == 3) t = __dsub_rn(t, a.anchor[j >> 2]);
+        pose_f[j] = (float)t;
+    }
     __syncthreads();
     if (s_flag) return;
 
@@ -227,29 +246,57 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
         const float qz = fmaf(R20, s.x, fmaf(R21, s.y, fmaf(R22, s.z, tz)));
         unsigned long long bkey = ~0ull;
         u32 bpos = 0;
+        int bv = 0;
+        QFrame<PREC> f;
+        const bool keyed = active && make_qframe<PREC>(m, qx, qy, qz, a.ftile, f);
         if constexpr (TPP == 1) {
             float d2b;
             u32 idb;
-            if (active && nearest27(m, max_probe, qx, qy, qz, a.tau2, d2b, idb, bpos))
+            if (keyed && nearest27q<PREC>(m, max_probe, f, a.tau2, d2b, idb, bpos, bv))
                 bkey = ((unsigned long long)__float_as_uint(d2b) << 32) | idb;
         } else {
-            group_nearest<TPP>(m, max_probe, qx, qy, qz, a.tau2, active, sl, bkey, bpos);
+            group_nearest<TPP, PREC>(m, max_probe, f, keyed, a.tau2, sl, bkey, bpos, bv);
         }
         if (!active || sl != 0) continue;
         const float bd2 = __uint_as_float((u32)(bkey >> 32));
         const bool ok = bkey != ~0ull && !(bd2 > a.tau2);
         if (a.corr_out) a.corr_out[__float_as_uint(s.w)] = ok ? (int32_t)(u32)bkey : -1;
         if (!ok) continue;
-        const float4 r = __ldg(m.pts + bpos);
-        const float4 rc0 = __ldg(m.cov + 2 * (size_t)bpos);
-        const float4 rc1 = __ldg(m.cov + 2 * (size_t)bpos + 1);
-        const float4 sc0 = a.src_cov[2 * (size_t)i];
-        const float4 sc1 = a.src_cov[2 * (size_t)i + 1];
+        float4 r = __ldg(m.pts + bpos);
+        float rc[6], sc[6];
+        bool r_ok, s_ok;
+        if constexpr (PREC) {
+            // the winner's frame offset; TPP == 1 reports its voxel as (dx+1)*9+(dy+1)*3+(dz+1)
+            int dx, dy, dz;
+            if constexpr (TPP == 1) {
+                dx = bv / 9 - 1;
+                dy = (bv / 3) % 3 - 1;
+                dz = bv % 3 - 1;
+            } else {
+                dx = c_nb_order[bv][0];
+                dy = c_nb_order[bv][1];
+                dz = c_nb_order[bv][2];
+            }
+            r.x = __fadd_rn(r.x, f.off(0, dx));
+            r.y = __fadd_rn(r.y, f.off(1, dy));
+            r.z = __fadd_rn(r.z, f.off(2, dz));
+            r_ok = cov16_decode(__ldg(m.cov_h4 + bpos), __ldg(m.cov_h2 + bpos), __ldg(m.cexp + bpos / m.nmax), rc);
+            s_ok = cov16_decode(a.src_h4[i], a.src_h2[i], (int)a.src_exp[i], sc);
+        } else {
+            const float4 rc0 = __ldg(m.cov + 2 * (size_t)bpos);
+            const float4 rc1 = __ldg(m.cov + 2 * (size_t)bpos + 1);
+            const float4 sc0 = a.src_cov[2 * (size_t)i];
+            const float4 sc1 = a.src_cov[2 * (size_t)i + 1];
+            rc[0] = rc0.x; rc[1] = rc0.y; rc[2] = rc0.z; rc[3] = rc0.w; rc[4] = rc1.x; rc[5] = rc1.y;
+            sc[0] = sc0.x; sc[1] = sc0.y; sc[2] = sc0.z; sc[3] = sc0.w; sc[4] = sc1.x; sc[5] = sc1.y;
+            r_ok = rc1.z > 0.5f;
+            s_ok = sc1.z > 0.5f;
+        }
         // M: (Sigma_r + R Sigma_s R^T)^-1, or I when a covariance is invalid (SA GICP)
         float M00 = 1.f, M01 = 0.f, M02 = 0.f, M11 = 1.f, M12 = 0.f, M22 = 1.f;
-        const bool p2p = !(rc1.z > 0.5f && sc1.z > 0.5f);
+        const bool p2p = !(r_ok && s_ok);
         if (!p2p) {
-            const float S00 = sc0.x, S01 = sc0.y, S02 = sc0.z, S11 = sc0.w, S12 = sc1.x, S22 = sc1.y;
+            const float S00 = sc[0], S01 = sc[1], S02 = sc[2], S11 = sc[3], S12 = sc[4], S22 = sc[5];
             // A = R S
             const float A00 = R00 * S00 + R01 * S01 + R02 * S02, A01 = R00 * S01 + R01 * S11 + R02 * S12,
                         A02 = R00 * S02 + R01 * S12 + R02 * S22;
@@ -258,12 +305,12 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
             const float A20 = R20 * S00 + R21 * S01 + R22 * S02, A21 = R20 * S01 + R21 * S11 + R22 * S12,
                         A22 = R20 * S02 + R21 * S12 + R22 * S22;
             // C = Sigma_r + A R^T (symmetric)
-            const float a_ = rc0.x + A00 * R00 + A01 * R01 + A02 * R02;
-            const float b_ = rc0.y + A00 * R10 + A01 * R11 + A02 * R12;
-            const float c_ = rc0.z + A00 * R20 + A01 * R21 + A02 * R22;
-            const float d_ = rc0.w + A10 * R10 + A11 * R11 + A12 * R12;
-            const float e_ = rc1.x + A10 * R20 + A11 * R21 + A12 * R22;
-            const float f_ = rc1.y + A20 * R20 + A21 * R21 + A22 * R22;
+            const float a_ = rc[0] + A00 * R00 + A01 * R01 + A02 * R02;
+            const float b_ = rc[1] + A00 * R10 + A01 * R11 + A02 * R12;
+            const float c_ = rc[2] + A00 * R20 + A01 * R21 + A02 * R22;
+            const float d_ = rc[3] + A10 * R10 + A11 * R11 + A12 * R12;
+            const float e_ = rc[4] + A10 * R20 + A11 * R21 + A12 * R22;
+            const float f_ = rc[5] + A20 * R20 + A21 * R21 + A22 * R22;
             const float C00 = d_ * f_ - e_ * e_, C01 = c_ * e_ - b_ * f_, C02 = b_ * e_ - c_ * d_;
             const float C11 = a_ * f_ - c_ * c_, C12 = b_ * c_ - a_ * e_, C22 = a_ * d_ - b_ * b_;
             const float idet = 1.0f / (a_ * C00 + b_ * C01 + c_ * C02);
@@ -335,18 +382,18 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
     }
 }
 
-template <int TPP>
+template <int TPP, bool PREC>
 __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs a) {
-    gn_lin_block<TPP>(a, blockIdx.x, gridDim.x);
+    gn_lin_block<TPP, PREC>(a, blockIdx.x, gridDim.x);
 }
 
 // Batched linearisation: the grid is shared by all problems; block b works for problem
 // block_prob[b] as its (b - block_begin)-th block of nblocks.
-template <int TPP>
+template <int TPP, bool PREC>
 __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(const BatchProblem* __restrict__ probs,
                                                                                 const u32* __restrict__ block_prob) {
     const BatchProblem& p = probs[block_prob[blockIdx.x]];
-    gn_lin_block<TPP>(p.args, blockIdx.x - p.block_begin, p.nblocks);
+    gn_lin_block<TPP, PREC>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
 
 // Solve half: one block reduces the block partials in a fixed order (FP64), then one
@@ -401,18 +448,21 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
         for (int j = 0; j < 6; ++j) mg[j] = -g[j];
         if (ok) ok = chol6_solve(H, mg, xi);
         if (ok) {
-            // Eq. 6: T <- exp(xi) T, written before the bookkeeping (the next launch waits on it)
+            // Eq. 6: T <- exp(xi) T about the anchor A (t - A is updated, then A is added back),
+            // written before the bookkeeping (the next launch waits on it)
             double E[12];
             se3_exp_dev(xi, E);
             double T[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) T[j] = st->T[j];
+            const double tr[3] = {T[3] - a.anchor[0], T[7] - a.anchor[1], T[11] - a.anchor[2]};
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
                     st->T[4 * r + c] = E[4 * r + 0] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c];
-                st->T[4 * r + 3] = E[4 * r + 0] * T[3] + E[4 * r + 1] * T[7] + E[4 * r + 2] * T[11] + E[4 * r + 3];
+                st->T[4 * r + 3] =
+                    (E[4 * r + 0] * tr[0] + E[4 * r + 1] * tr[1] + E[4 * r + 2] * tr[2] + E[4 * r + 3]) + a.anchor[r];
             }
             double nx = 0.0;
 #pragma unroll
@@ -521,19 +571,25 @@ __global__ void k_gn_cov(RegState* st, double* cov) {
 // Map footprint of one Gauss-Newton launch at the current pose: the distinct
 // voxels probed by the 27-neighbourhoods of all source points and the points
 // they hold (the unique data a launch must read at least once).
-__global__ void k_footprint(MapView m, const float4* __restrict__ src, const RegState* __restrict__ st,
-                            u32* __restrict__ touched, unsigned long long* __restrict__ out) {
+__global__ void k_footprint(GnArgs a, u32* __restrict__ touched, unsigned long long* __restrict__ out) {
+    const MapView m = a.map;
+    const RegState* st = a.st;
     const u32 n = st->n_src;
     const u32 max_probe = m.ctr->max_probe;
     float T[12];
-    for (int j = 0; j < 12; ++j) T[j] = (float)st->T[j];
+    for (int j = 0; j < 12; ++j) T[j] = (float)((j & 3) == 3 ? st->T[j] - a.anchor[j >> 2] : st->T[j]);
     for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 s = src[i];
+        const float4 s = a.src[i];
         const float qx = fmaf(T[0], s.x, fmaf(T[1], s.y, fmaf(T[2], s.z, T[3])));
         const float qy = fmaf(T[4], s.x, fmaf(T[5], s.y, fmaf(T[6], s.z, T[7])));
         const float qz = fmaf(T[8], s.x, fmaf(T[9], s.y, fmaf(T[10], s.z, T[11])));
         int kx, ky, kz;
         if (!voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz)) continue;
+        if (m.tv > 0) {
+            kx += a.ftile[0] * m.tv;
+            ky += a.ftile[1] * m.tv;
+            kz += a.ftile[2] * m.tv;
+        }
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dz = -1; dz <= 1; ++dz) {
@@ -559,13 +615,13 @@ __global__ void k_footprint(MapView m, const float4* __restrict__ src, const Reg
 
 }  // namespace
 
-cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st, u32* touched, u32 cap,
-                         unsigned long long* out2, u32 n_upper, cudaStream_t s) {
+cudaError_t gn_footprint(const GnArgs& a, u32* touched, u32 cap, unsigned long long* out2, u32 n_upper,
+                         cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(touched, 0, (size_t)cap * sizeof(u32), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    FAR_LAUNCH(k_footprint, gn_grid(n_upper, 1), GN_THREADS, 0, s, m, src, st, touched, out2);
+    FAR_LAUNCH(k_footprint, gn_grid(n_upper, 1), GN_THREADS, 0, s, a, touched, out2);
     return cudaGetLastError();
 }
 
@@ -580,12 +636,14 @@ constexpr u32 kMaxGnBlocks = 152u * 8u;
 // Blocks of k_gn_lin<TPP> that fit on the device at once (one wave), at most kMaxGnBlocks.
 template <int TPP>
 u32 resident_gn_blocks() {
+    // the grid must not depend on the map's precision mode (a batch may mix modes); both
+    // kernels are compiled for FAR_GN_MIN_BLOCKS resident blocks, the plain one is measured
     static u32 cached = 0;
     if (cached) return cached;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gn_lin<TPP>, GN_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gn_lin<TPP, false>, GN_THREADS, 0) != cudaSuccess ||
         sms <= 0 || per_sm <= 0) {
         cudaGetLastError();
         return kMaxGnBlocks;
@@ -640,11 +698,20 @@ cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cuda
 
 cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks) {
     const u32 g = gn_grid(n_upper, a.tpp);
+    const bool prec = a.map.tv > 0;
     switch (gn_tpp(a.tpp)) {
-        case 4: FAR_LAUNCH(k_gn_lin<4>, g, GN_THREADS, 0, s, a); break;
-        case 8: FAR_LAUNCH(k_gn_lin<8>, g, GN_THREADS, 0, s, a); break;
-        case 32: FAR_LAUNCH(k_gn_lin<32>, g, GN_THREADS, 0, s, a); break;
-        default: FAR_LAUNCH(k_gn_lin<1>, g, GN_THREADS, 0, s, a); break;
+        case 4: if (prec) FAR_LAUNCH((k_gn_lin<4, true>), g, GN_THREADS, 0, s, a);
+                else FAR_LAUNCH((k_gn_lin<4, false>), g, GN_THREADS, 0, s, a);
+                break;
+        case 8: if (prec) FAR_LAUNCH((k_gn_lin<8, true>), g, GN_THREADS, 0, s, a);
+                else FAR_LAUNCH((k_gn_lin<8, false>), g, GN_THREADS, 0, s, a);
+                break;
+        case 32: if (prec) FAR_LAUNCH((k_gn_lin<32, true>), g, GN_THREADS, 0, s, a);
+                 else FAR_LAUNCH((k_gn_lin<32, false>), g, GN_THREADS, 0, s, a);
+                 break;
+        default: if (prec) FAR_LAUNCH((k_gn_lin<1, true>), g, GN_THREADS, 0, s, a);
+                 else FAR_LAUNCH((k_gn_lin<1, false>), g, GN_THREADS, 0, s, a);
+                 break;
     }
     *nblocks = g;
     return cudaGetLastError();
@@ -662,12 +729,20 @@ cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* i
 }
 
 cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob, u32 total_blocks, u32 nprob,
-                               int tpp, cudaStream_t s) {
+                               int tpp, bool prec, cudaStream_t s) {
     switch (gn_tpp(tpp)) {
-        case 4: FAR_LAUNCH(k_gn_lin_batch<4>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
-        case 8: FAR_LAUNCH(k_gn_lin_batch<8>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
-        case 32: FAR_LAUNCH(k_gn_lin_batch<32>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
-        default: FAR_LAUNCH(k_gn_lin_batch<1>, total_blocks, GN_THREADS, 0, s, probs, block_prob); break;
+        case 4: if (prec) FAR_LAUNCH((k_gn_lin_batch<4, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                else FAR_LAUNCH((k_gn_lin_batch<4, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                break;
+        case 8: if (prec) FAR_LAUNCH((k_gn_lin_batch<8, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                else FAR_LAUNCH((k_gn_lin_batch<8, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                break;
+        case 32: if (prec) FAR_LAUNCH((k_gn_lin_batch<32, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 else FAR_LAUNCH((k_gn_lin_batch<32, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 break;
+        default: if (prec) FAR_LAUNCH((k_gn_lin_batch<1, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 else FAR_LAUNCH((k_gn_lin_batch<1, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 break;
     }
     FAR_LAUNCH(k_gn_solve_batch, nprob, SOLVE_THREADS, 0, s, probs);
     return cudaGetLastError();

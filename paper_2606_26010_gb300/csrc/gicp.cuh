@@ -21,6 +21,15 @@ struct GnArgs {
     int32_t* corr_out;           // optional per-source correspondence ids
     unsigned long long budget_ns;  // 0: no time cap
     int tpp;                     // lanes per source point in the search: 1, 4, 8 or 32 (other: default)
+    // Linearisation anchor A (world): J = [[q - A]x, -I] and T <- exp(xi) T about A. Zero for plain
+    // maps; for the precision variant the corner of the tile holding the initial position,
+    // with ftile that tile (the search frame of the iteration).
+    double anchor[3];
+    int ftile[3];
+    // precision variant source covariances (FP16 with the scan-local voxel's exponent)
+    const uint2* src_h4;
+    const u32* src_h2;
+    const signed char* src_exp;
 };
 
 // One problem of a batched registration: its arguments and its share of the shared grid.
@@ -35,7 +44,7 @@ struct BatchProblem {
 u32 gn_threads_per_block();
 cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* init, cudaStream_t s);
 cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob, u32 total_blocks, u32 nprob,
-                               int tpp, cudaStream_t s);
+                               int tpp, bool prec, cudaStream_t s);   // prec: every problem's map is precision mode
 cudaError_t gn_batch_gather(const BatchProblem* probs, u32 nprob, RegState* out, cudaStream_t s);
 
 // Supported lanes-per-point value for a request (unsupported values map to the default).
@@ -51,9 +60,10 @@ cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cuda
 cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s);
 cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks);
 cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s);
-// Distinct map voxels (out2[0]) and their points (out2[1]) probed by the source points at st->T.
-cudaError_t gn_footprint(const MapView& m, const float4* src, const RegState* st, u32* touched, u32 cap,
-                         unsigned long long* out2, u32 n_upper, cudaStream_t s);
+// Distinct map voxels (out2[0]) and their points (out2[1]) probed by the source points at st->T
+// (searched in the frame of a.anchor / a.ftile as the linearisation does).
+cudaError_t gn_footprint(const GnArgs& a, u32* touched, u32 cap, unsigned long long* out2, u32 n_upper,
+                         cudaStream_t s);
 // cov36 = H^-1 of the last linearisation in st (zeros when H is not positive definite).
 cudaError_t gn_covariance(RegState* st, double* cov36, cudaStream_t s);
 

@@ -29,8 +29,10 @@ __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* 
 }
 
 // a11: x_w = fp32(((R0 x + R1 y) + R2 z) + t) in FP64 without contraction; then the key.
+// Precision variant (tv > 0): x_w stays FP64, the key follows the tile reading and `world`
+// receives the coordinates relative to the tile origin.
 __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
-                             float inv_v, float4* __restrict__ world, u64* __restrict__ keys) {
+                             float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (dp.T) {
@@ -40,6 +42,25 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
     const float4 p = in[i];
     float w[3] = {p.x, p.y, p.z};
     const bool finite = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && !(dp.status && *dp.status != 0);
+    if (tv > 0) {
+        u64 key = KEY_INVALID;
+        int k[3];
+        bool ok = finite;
+        for (int r = 0; r < 3 && ok; ++r) {
+            double x = (&p.x)[r];
+            if (has_pose) {
+                const double px = p.x, py = p.y, pz = p.z;
+                double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], px), __dmul_rn(T.m[4 * r + 1], py));
+                s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], pz));
+                x = __dadd_rn(s, T.m[4 * r + 3]);
+            }
+            ok = tile_key_axis(x, inv_v, tv, k[r], w[r]);
+        }
+        if (ok) key = pack_key(k[0], k[1], k[2]);
+        world[i] = make_float4(w[0], w[1], w[2], p.w);
+        keys[i] = key;
+        return;
+    }
     if (has_pose && finite) {
         const double x = p.x, y = p.y, z = p.z;
 #pragma unroll
@@ -179,6 +200,11 @@ struct AdmitArgs {
     u32* a_ord;
     u32* a_j;
     u32* pos;
+    // precision variant: per-voxel FP16 exponents and the state of each touched voxel
+    int* cexp;          // null for plain maps
+    u32* grp_bucket;
+    u32* grp_cnt0;
+    int* grp_exp0;
 };
 
 // a11 admission: one warp per voxel group. Candidates are walked in input order;
@@ -215,6 +241,7 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
                     b = a.ring[h % a.max_buckets];
                     sp->bucket = b;
                     sp->count = 0;
+                    if (a.cexp) a.cexp[b] = EXP_NONE;  // a recycled bucket starts without an exponent
                     atomicAdd(&a.ctr->n_voxels, 1u);
                 } else {
                     atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
@@ -277,6 +304,11 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
         if (lane == 0) {
             if (cnt != cnt0) sp->count = cnt;
             a.grp_cnt[ord] = cnt - cnt0;
+            if (a.cexp) {
+                a.grp_bucket[ord] = bucket;
+                a.grp_cnt0[ord] = cnt0;
+                a.grp_exp0[ord] = a.cexp[bucket];
+            }
         }
     }
 }
@@ -305,12 +337,13 @@ __global__ void k_mark_heads(const u32* __restrict__ gstart, const u32* __restri
 __global__ void k_grouped_dest(const u32* __restrict__ admitted, const u32* __restrict__ a_ord,
                                const u32* __restrict__ a_j, const u32* __restrict__ grp_base,
                                const u32* __restrict__ pos, u32 n, u32* __restrict__ dest,
-                               u32* __restrict__ added) {
+                               u32* __restrict__ added, const u64* __restrict__ keys, u64* __restrict__ added_key) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
     const u32 d = grp_base[a_ord[i]] + a_j[i];
     dest[i] = d;
     if (added) added[d] = pos[i];
+    if (added_key) added_key[d] = keys[i];
 }
 
 __global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal) {
@@ -344,6 +377,118 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
             const size_t row = __float_as_uint(p.w);
 #pragma unroll
             for (int j = 0; j < K; ++j) knn_ids[row * K + j] = (j < found) ? bid[j] : NO_ID;
+        }
+    }
+}
+
+// Precision variant, a12: Eq. 1 covariances of the added map points (grouped order r,
+// map position qpos[r], voxel key qkey[r]) in the frame of each point's tile, kept in FP32
+// in cov_tmp; each valid covariance raises its voxel's exponent.
+template <int K>
+__global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __restrict__ qpos,
+                                                      const u64* __restrict__ qkey, u32 n,
+                                                      const u32* __restrict__ n_dev, float4* __restrict__ cov_tmp,
+                                                      int* __restrict__ cexp) {
+    const u32 nn = min(n, *n_dev);
+    const u32 max_probe = m.ctr->max_probe;
+    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
+        const u32 pos = qpos[r];
+        const float4 p = m.pts[pos];
+        int kx, ky, kz;
+        unpack_key(qkey[r], kx, ky, kz);
+        QFrame<true> f;
+        own_qframe(m, p.x, p.y, p.z, kx, ky, kz, f);
+        float bd[K];
+        u32 bid[K], bpos[K];
+        knn_init<K>(bd, bid, bpos);
+        const int found = knn27q<K, true>(m, max_probe, f, bd, bid, bpos);
+        float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool valid = false;
+        if (found >= K) {
+            valid = true;
+            covariance_from_neighbours_f<K>(m.pts, bpos, p.x, p.y, p.z, TileOffset(), c);
+        }
+        cov_tmp[2 * (size_t)r] = make_float4(c[0], c[1], c[2], c[3]);
+        cov_tmp[2 * (size_t)r + 1] = make_float4(c[4], c[5], valid ? 1.0f : 0.0f, 0.0f);
+        if (valid) atomicMax(cexp + pos / m.nmax, cov_exponent(c));
+    }
+}
+
+// Precision variant: one warp per touched voxel (ordinal g). If the voxel's exponent rose,
+// the FP16 entries of its older points are rescaled by the power of two (exact unless they
+// become subnormal); then the added points of the voxel (grouped positions base[g] ..) are
+// written as FP16 at the final exponent. The result does not depend on thread timing.
+__global__ void k_cov_encode(const u32* __restrict__ grp_base, const u32* __restrict__ scal,
+                             const u32* __restrict__ grp_bucket, const u32* __restrict__ grp_cnt0,
+                             const int* __restrict__ grp_exp0, const int* __restrict__ cexp,
+                             const u32* __restrict__ added, const float4* __restrict__ cov_tmp, u32 nmax,
+                             uint2* __restrict__ cov_h4, u32* __restrict__ cov_h2) {
+    const int lane = threadIdx.x & 31;
+    const u32 ng = scal[SCAL_NGROUPS];
+    const u32 n_add = scal[SCAL_NADMIT];
+    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += (gridDim.x * blockDim.x) >> 5) {
+        const u32 b0 = grp_base[g];
+        const u32 b1 = (g + 1 < ng) ? grp_base[g + 1] : n_add;
+        if (b1 == b0) continue;
+        const u32 bucket = grp_bucket[g];
+        const int E = cexp[bucket], E0 = grp_exp0[g];
+        if (E0 != EXP_NONE && E > E0) {
+            const float s = pow2f(E0 - E);
+            for (u32 j = lane; j < grp_cnt0[g]; j += 32) {
+                const size_t o = (size_t)bucket * nmax + j;
+                float c[6];
+                if (!cov16_decode(cov_h4[o], cov_h2[o], 0, c)) continue;
+#pragma unroll
+                for (int t = 0; t < 6; ++t) c[t] *= s;
+                cov16_encode(c, 0, cov_h4[o], cov_h2[o]);
+            }
+        }
+        for (u32 r = b0 + lane; r < b1; r += 32) {
+            const float4 c0 = cov_tmp[2 * (size_t)r], c1 = cov_tmp[2 * (size_t)r + 1];
+            const u32 o = added[r];
+            if (c1.z > 0.5f) {
+                const float c[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+                cov16_encode(c, E, cov_h4[o], cov_h2[o]);
+            } else {
+                cov_h4[o] = make_uint2(0u, 0u);
+                cov_h2[o] = 0u;
+            }
+        }
+    }
+}
+
+// Precision variant sources: the FP32 covariances of each scan-local voxel (grouped
+// positions base[g] ..) are stored as FP16 with the voxel's exponent, kept per point.
+__global__ void k_src_encode(const u32* __restrict__ grp_base, const u32* __restrict__ scal,
+                             const float4* __restrict__ src_cov, uint2* __restrict__ h4, u32* __restrict__ h2,
+                             signed char* __restrict__ e_out) {
+    const int lane = threadIdx.x & 31;
+    const u32 ng = scal[SCAL_NGROUPS];
+    const u32 n_add = scal[SCAL_NADMIT];
+    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += (gridDim.x * blockDim.x) >> 5) {
+        const u32 b0 = grp_base[g];
+        const u32 b1 = (g + 1 < ng) ? grp_base[g + 1] : n_add;
+        if (b1 == b0) continue;
+        int E = EXP_NONE;
+        for (u32 r = b0 + lane; r < b1; r += 32) {
+            const float4 c0 = src_cov[2 * (size_t)r], c1 = src_cov[2 * (size_t)r + 1];
+            if (c1.z > 0.5f) {
+                const float c[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+                E = max(E, cov_exponent(c));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+        for (u32 r = b0 + lane; r < b1; r += 32) {
+            const float4 c0 = src_cov[2 * (size_t)r], c1 = src_cov[2 * (size_t)r + 1];
+            if (c1.z > 0.5f) {
+                const float c[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+                cov16_encode(c, E, h4[r], h2[r]);
+            } else {
+                h4[r] = make_uint2(0u, 0u);
+                h2[r] = 0u;
+            }
+            e_out[r] = (signed char)(E == EXP_NONE ? 0 : E);
         }
     }
 }
@@ -442,21 +587,59 @@ __global__ void k_list_slots(const Slot* __restrict__ slots, u32 cap, u64* keys,
     }
 }
 
-__global__ void k_gather(const float4* __restrict__ pts, const float4* __restrict__ cov, u32 nmax,
-                         const u32* __restrict__ buckets, const u32* __restrict__ counts,
-                         const u32* __restrict__ offsets, u32 nvox, float4* __restrict__ pts_out,
-                         float4* __restrict__ cov_out) {
+__global__ void k_gather(MapView m, const u32* __restrict__ buckets, const u32* __restrict__ counts,
+                         const u32* __restrict__ offsets, const u64* __restrict__ keys, u32 nvox,
+                         float4* __restrict__ pts_out, float4* __restrict__ cov_out) {
     const int lane = threadIdx.x & 31;
+    const u32 nmax = m.nmax;
     for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nvox; g += (gridDim.x * blockDim.x) >> 5) {
         const u32 b = buckets[g], c = counts[g], o = offsets[g];
+        int tile[3] = {0, 0, 0};
+        if (m.tv > 0) {
+            int k[3];
+            unpack_key(keys[g], k[0], k[1], k[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) tile[a] = floor_div(k[a], m.tv);
+        }
         for (u32 j = lane; j < c; j += 32) {
-            pts_out[o + j] = pts[(size_t)b * nmax + j];
-            if (cov) {
-                cov_out[2 * (size_t)(o + j)] = cov[2 * ((size_t)b * nmax + j)];
-                cov_out[2 * (size_t)(o + j) + 1] = cov[2 * ((size_t)b * nmax + j) + 1];
+            const size_t src = (size_t)b * nmax + j;
+            float4 p = m.pts[src];
+            if (m.tv > 0) {
+                // world FP32 = fp32(50 T + tile-relative value), exact in FP64 before the rounding
+                p.x = __double2float_rn(__dadd_rn(TILE_D * (double)tile[0], (double)p.x));
+                p.y = __double2float_rn(__dadd_rn(TILE_D * (double)tile[1], (double)p.y));
+                p.z = __double2float_rn(__dadd_rn(TILE_D * (double)tile[2], (double)p.z));
+            }
+            pts_out[o + j] = p;
+            if (!cov_out) continue;
+            if (m.tv > 0) {
+                float cv[6];
+                const bool ok = cov16_decode(m.cov_h4[src], m.cov_h2[src], m.cexp[b], cv);
+                cov_out[2 * (size_t)(o + j)] = ok ? make_float4(cv[0], cv[1], cv[2], cv[3]) : make_float4(0, 0, 0, 0);
+                cov_out[2 * (size_t)(o + j) + 1] = ok ? make_float4(cv[4], cv[5], 1.0f, 0.0f) : make_float4(0, 0, 0, 0);
+            } else {
+                cov_out[2 * (size_t)(o + j)] = m.cov[2 * src];
+                cov_out[2 * (size_t)(o + j) + 1] = m.cov[2 * src + 1];
             }
         }
     }
+}
+
+// Precision variant: frame of a world query = its own tile, T = floor(q / 50), q_F = fp32(q - 50 T).
+__device__ __forceinline__ bool world_query_frame(const MapView& m, float qx, float qy, float qz, QFrame<true>& f) {
+    const float q[3] = {qx, qy, qz};
+    int ft[3];
+    float qf[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double x = (double)q[a];
+        if (!isfinite(x)) return false;
+        const double T = floor(__ddiv_rn(x, TILE_D));
+        if (!(fabs(T) * (double)m.tv < (double)KEY_BIAS)) return false;
+        ft[a] = (int)T;
+        qf[a] = __double2float_rn(__dsub_rn(x, __dmul_rn(TILE_D, T)));
+    }
+    return make_qframe<true>(m, qf[0], qf[1], qf[2], ft, f);
 }
 
 template <int K>
@@ -467,7 +650,14 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
         const float4 p = q[r];
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
+        int found;
+        if (m.tv > 0) {
+            knn_init<K>(bd, bid, bpos);
+            QFrame<true> f;
+            found = world_query_frame(m, p.x, p.y, p.z, f) ? knn27q<K, true>(m, max_probe, f, bd, bid, bpos) : 0;
+        } else {
+            found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
+        }
         found_out[r] = found;
 #pragma unroll
         for (int j = 0; j < K; ++j) ids[(size_t)r * K + j] = (j < found) ? bid[j] : NO_ID;
@@ -479,9 +669,16 @@ __global__ void __launch_bounds__(TPB) k_nearest_stage(MapView m, const float4* 
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const float4 p = q[r];
-        float bd2;
-        u32 bid, bpos;
-        const bool any = nearest27(m, max_probe, p.x, p.y, p.z, F_INF, bd2, bid, bpos);
+        float bd2 = F_INF;
+        u32 bid = NO_ID, bpos = 0;
+        bool any = false;
+        if (m.tv > 0) {
+            QFrame<true> f;
+            int bv;
+            if (world_query_frame(m, p.x, p.y, p.z, f)) any = nearest27q<true>(m, max_probe, f, F_INF, bd2, bid, bpos, bv);
+        } else {
+            any = nearest27(m, max_probe, p.x, p.y, p.z, F_INF, bd2, bid, bpos);
+        }
         d2_out[r] = bd2;
         ids[r] = (any && !(bd2 > tau2)) ? (int64_t)bid : (int64_t)-1;
     }
@@ -529,6 +726,20 @@ cudaError_t knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n,
     FAR_K_CASES(launch_knn_cov, m, q, qpos, n, n_dev, cov_out, out_pos, knn_ids, st)
 }
 
+template <int K>
+cudaError_t launch_knn_cov_tile(const DeviceMap& m, const u32* qpos, const u64* qkey, u32 n, const u32* n_dev,
+                                float4* cov_tmp, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_knn_cov_tile<K>, blocks_for(n), TPB, 0, st, m.view(), qpos, qkey, n, n_dev, cov_tmp, m.cexp);
+    return cudaGetLastError();
+}
+
+cudaError_t knn_cov_tile(const DeviceMap& m, const u32* qpos, const u64* qkey, u32 n, const u32* n_dev,
+                         float4* cov_tmp, cudaStream_t st) {
+    const u32 k = m.k;
+    FAR_K_CASES(launch_knn_cov_tile, m, qpos, qkey, n, n_dev, cov_tmp, st)
+}
+
 }  // namespace
 
 #define FAR_TRY(x)                                  \
@@ -554,7 +765,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     Pose12 T{};
     if (pose) T = *pose;
     FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
-                                                m.inv_v, s.world, s.keys);
+                                                m.inv_v, m.tv, s.world, s.keys);
     FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr);
     bool alt = false;
     FAR_TRY(radix_sort_pairs(s.sk, s.sv, s.sk_alt, s.sv_alt, n, m.key_bits, s.hist, s.partials, st, &alt));
@@ -594,6 +805,10 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     a.a_ord = s.a_ord;
     a.a_j = s.a_j;
     a.pos = s.pos;
+    a.cexp = m.tv > 0 ? m.cexp : nullptr;
+    a.grp_bucket = s.grp_bucket;
+    a.grp_cnt0 = s.grp_cnt0;
+    a.grp_exp0 = s.grp_exp0;
     // one warp per group; groups <= n
     const u32 warps = min(n, 152u * 64u);
     FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
@@ -601,17 +816,32 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     FAR_TRY(scan_exclusive(s.grp_cnt, s.grp_cnt, n, s.scal + SCAL_NGROUPS, nullptr, s.partials, st));
     FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.scal, m.ctr);
     FAR_LAUNCH(k_finalize_insert, 1, 1, 0, st, m.ctr, s.scal);
+    const bool prec = m.tv > 0;
+    const bool covs = covariances && (m.cov || prec);
     FAR_LAUNCH(k_grouped_dest, blocks_for(n), TPB, 0, st, s.admitted, s.a_ord, s.a_j, s.grp_cnt, s.pos, n, s.dest,
-               (covariances && m.cov) ? s.added : nullptr);
-    if (covariances && m.cov)
+               covs ? s.added : nullptr, s.keys, (covs && prec) ? s.added_key : nullptr);
+    if (covs && !prec)
         FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));
+    if (covs && prec) {
+        FAR_TRY(knn_cov_tile(m, s.added, s.added_key, n, s.scal + SCAL_NADMIT, s.cov_tmp, st));
+        const u32 warps = min(n, 152u * 64u);
+        FAR_LAUNCH(k_cov_encode, blocks_for(warps * 32u), TPB, 0, st, s.grp_cnt, s.scal, s.grp_bucket, s.grp_cnt0,
+                   s.grp_exp0, m.cexp, s.added, s.cov_tmp, m.nmax, m.cov_h4, m.cov_h2);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     FAR_LAUNCH(k_make_sources, blocks_for(n), TPB, 0, st, s.admitted, s.dest, s.rank, s.in4, n, s.src, s.src_index);
-    return knn_cov(local, s.src, nullptr, n, s.scal + SCAL_NADMIT, s.src_cov, nullptr, knn_ids_out, st);
+    FAR_TRY(knn_cov(local, s.src, nullptr, n, s.scal + SCAL_NADMIT, s.src_cov, nullptr, knn_ids_out, st));
+    if (s.src_h4) {
+        // precision variant: FP16 copies with one exponent per scan-local voxel
+        const u32 warps = min(n, 152u * 64u);
+        FAR_LAUNCH(k_src_encode, blocks_for(warps * 32u), TPB, 0, st, s.grp_cnt, s.scal, s.src_cov, s.src_h4,
+                   s.src_h2, s.src_exp);
+    }
+    return cudaGetLastError();
 }
 
 __global__ void k_clear_counters(MapCounters* ctr, u32 ring_tail) {
@@ -657,11 +887,11 @@ cudaError_t map_list_slots(const DeviceMap& m, u64* keys, u32* buckets, u32* cou
     return cudaGetLastError();
 }
 
-cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets, u32 nvox,
-                       float4* pts_out, float4* cov_out, cudaStream_t st) {
+cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets,
+                       const u64* keys, u32 nvox, float4* pts_out, float4* cov_out, cudaStream_t st) {
     if (nvox == 0) return cudaSuccess;
-    FAR_LAUNCH(k_gather, blocks_for(nvox * 32u), TPB, 0, st, m.pts, m.cov, m.nmax, buckets, counts, offsets, nvox, pts_out,
-                                                     cov_out);
+    FAR_LAUNCH(k_gather, blocks_for(nvox * 32u), TPB, 0, st, m.view(), buckets, counts, offsets, keys, nvox, pts_out,
+               (m.cov || m.tv > 0) ? cov_out : nullptr);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,11 @@ struct DeviceMap {
     MapCounters* ctr = nullptr;
     u32 nmax = 0, k = 0;
     float v = 0, inv_v = 0, dmin2 = 0;
+    // precision variant (registration map only): tv > 0, FP16 covariances, cov == null
+    int tv = 0;
+    uint2* cov_h4 = nullptr;
+    u32* cov_h2 = nullptr;
+    int* cexp = nullptr;
 
     MapView view() const {
         MapView mv;
@@ -28,6 +33,10 @@ struct DeviceMap {
         mv.nmax = nmax;
         mv.inv_v = inv_v;
         mv.v = v;
+        mv.tv = tv;
+        mv.cov_h4 = cov_h4;
+        mv.cov_h2 = cov_h2;
+        mv.cexp = cexp;
         return mv;
     }
 };
@@ -67,6 +76,15 @@ struct Scratch {
     // diagnostics
     u32* touched = nullptr;              // one flag per registration-map slot
     unsigned long long* foot = nullptr;  // footprint counters
+    // precision variant only (null otherwise)
+    float4* cov_tmp = nullptr;           // FP32 covariances of added points, 2 per point (grouped order)
+    u64* added_key = nullptr;            // voxel key of each added point (grouped order)
+    u32* grp_bucket = nullptr;           // by voxel ordinal: bucket, count before the insert, old exponent
+    u32* grp_cnt0 = nullptr;
+    int* grp_exp0 = nullptr;
+    uint2* src_h4 = nullptr;             // FP16 source covariances (see far_internal.cuh)
+    u32* src_h2 = nullptr;
+    signed char* src_exp = nullptr;      // exponent of each source's scan-local voxel
 };
 
 enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_COUNT = 8 };
@@ -119,8 +137,10 @@ cudaError_t map_list_slots(const DeviceMap& m, u64* keys, u32* buckets, u32* cou
                            cudaStream_t st);
 
 // Gather points of the listed buckets into contiguous arrays (offsets = exclusive prefix of counts).
-cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets, u32 nvox,
-                       float4* pts_out, float4* cov_out, cudaStream_t st);
+// keys[g] is the voxel key of buckets[g] (precision variant: world coordinates and FP32
+// covariances are restored from the tile-relative / FP16 records).
+cudaError_t map_gather(const DeviceMap& m, const u32* buckets, const u32* counts, const u32* offsets,
+                       const u64* keys, u32 nvox, float4* pts_out, float4* cov_out, cudaStream_t st);
 
 // k-NN and 1-NN of packed queries (stage entry points).
 cudaError_t map_knn(const DeviceMap& m, const float4* q, u32 n, u32 k, u32* ids, int32_t* found, cudaStream_t st);

@@ -49,16 +49,91 @@ __device__ __forceinline__ float box_lb2(const FaceDist& f, int dx, int dy, int 
     return ax * ax + ay * ay + az * az;
 }
 
+// A query in search coordinates. Plain maps search in world coordinates. In the precision
+// variant the search runs in the frame of a tile F (coordinates relative to its origin): a
+// map point of tile T_p enters as fp32(p + 50 (T_p - F)), one FP32 addition of an exact
+// multiple of 50. k is the centre voxel (global key), lk the centre relative to the frame
+// origin (face distances), ct / cin its tile relative to F and its index inside that tile.
+template <bool PREC>
+struct QFrame {
+    float q[3];
+    int k[3], lk[3];
+    int ct[3], cin[3];
+    int tv;
+    // offset of neighbour voxel lk + d along axis a (0 for plain maps)
+    __device__ __forceinline__ float off(int a, int d) const {
+        if constexpr (!PREC) {
+            return 0.0f;
+        } else {
+            const int c = cin[a] + d;
+            const int t = ct[a] + (c < 0 ? -1 : (c >= tv ? 1 : 0));
+            return TILE_M * (float)t;
+        }
+    }
+};
+
+// Query given in frame coordinates (world for plain maps; frame tile ftile otherwise):
+// centre = K_F + floor(fp32(q * inv_v)).
+template <bool PREC>
+__device__ __forceinline__ bool make_qframe(const MapView& m, float qx, float qy, float qz, const int (&ftile)[3],
+                                            QFrame<PREC>& f) {
+    f.q[0] = qx;
+    f.q[1] = qy;
+    f.q[2] = qz;
+    f.tv = m.tv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f.k[a] = f.lk[a] = f.ct[a] = f.cin[a] = 0;
+    if (!voxel_key3(qx, qy, qz, m.inv_v, f.lk[0], f.lk[1], f.lk[2])) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (PREC) {
+            const long long k = (long long)f.lk[a] + (long long)ftile[a] * m.tv;
+            if (k < -(long long)KEY_BIAS || k >= (long long)KEY_BIAS) return false;
+            f.k[a] = (int)k;
+            f.ct[a] = floor_div(f.lk[a], m.tv);
+            f.cin[a] = f.lk[a] - f.ct[a] * m.tv;
+        } else {
+            f.k[a] = f.lk[a];
+            f.ct[a] = 0;
+            f.cin[a] = 0;
+        }
+    }
+    return true;
+}
+
+// Query that is a map point: centre = its own voxel key, frame = that voxel's tile,
+// coordinates = its stored (tile-relative) coordinates.
+__device__ __forceinline__ void own_qframe(const MapView& m, float qx, float qy, float qz, int kx, int ky, int kz,
+                                           QFrame<true>& f) {
+    f.q[0] = qx;
+    f.q[1] = qy;
+    f.q[2] = qz;
+    f.tv = m.tv;
+    const int k[3] = {kx, ky, kz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f.k[a] = k[a];
+        f.lk[a] = k[a] - floor_div(k[a], m.tv) * m.tv;
+        f.ct[a] = 0;
+        f.cin[a] = f.lk[a];
+    }
+}
+
 // Merge the points of voxel (nx, ny, nz) into the sorted K best of q.
-template <int K>
+template <int K, bool PREC = false>
 __device__ __forceinline__ void knn_scan_voxel(const MapView& m, u32 max_probe, int nx, int ny, int nz, float qx,
                                                float qy, float qz, int& found, float (&bd)[K], u32 (&bid)[K],
-                                               u32 (&bpos)[K]) {
+                                               u32 (&bpos)[K], float ox = 0.f, float oy = 0.f, float oz = 0.f) {
     u32 bucket, count;
     if (!find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) return;
     const u32 base = bucket * m.nmax;
     for (u32 j = 0; j < count; ++j) {
-        const float4 p = __ldg(m.pts + base + j);
+        float4 p = __ldg(m.pts + base + j);
+        if constexpr (PREC) {
+            p.x = __fadd_rn(p.x, ox);
+            p.y = __fadd_rn(p.y, oy);
+            p.z = __fadd_rn(p.z, oz);
+        }
         const float d2 = dist2_rn(qx, qy, qz, p.x, p.y, p.z);
         const u32 id = __float_as_uint(p.w);
         ++found;
@@ -84,16 +159,25 @@ __device__ __forceinline__ void knn_scan_voxel(const MapView& m, u32 max_probe, 
 // Merge the points of voxel (nx, ny, nz) into the nearest of q, kept as the packed key
 // (d2 bits << 32 | id): for d2 >= 0 the integer order is the (d2, id) order. Points are
 // loaded four at a time so that several loads are in flight.
-__device__ __forceinline__ void nn_scan_voxel(const MapView& m, u32 max_probe, int nx, int ny, int nz, float qx,
-                                              float qy, float qz, unsigned long long& best_key, u32& best_pos) {
+template <bool PREC = false>
+__device__ __forceinline__ bool nn_scan_voxel(const MapView& m, u32 max_probe, int nx, int ny, int nz, float qx,
+                                              float qy, float qz, unsigned long long& best_key, u32& best_pos,
+                                              float ox = 0.f, float oy = 0.f, float oz = 0.f) {
     u32 bucket, count;
-    if (!find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) return;
+    if (!find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) return false;
     const u32 base = bucket * m.nmax;
+    const unsigned long long before = best_key;
     for (u32 j0 = 0; j0 < count; j0 += 4) {
         float4 c[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u) {
             c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (PREC) {
+                c[u].x = __fadd_rn(c[u].x, ox);
+                c[u].y = __fadd_rn(c[u].y, oy);
+                c[u].z = __fadd_rn(c[u].z, oz);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (j0 + u < count) {
@@ -106,6 +190,7 @@ __device__ __forceinline__ void nn_scan_voxel(const MapView& m, u32 max_probe, i
             }
         }
     }
+    return best_key != before;
 }
 
 __device__ __forceinline__ float nn_bound(unsigned long long best_key, float limit2) {
@@ -113,23 +198,18 @@ __device__ __forceinline__ float nn_bound(unsigned long long best_key, float lim
     return fminf(b, limit2);
 }
 
-// K nearest of q (K is the exact k: a run-time k would push the arrays to local
+// K nearest of the query (K is the exact k: a run-time k would push the arrays to local
 // memory); arrays sorted ascending by (d2, id). Returns the number found (<= K).
-template <int K>
-__device__ __forceinline__ int knn27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
-                                     float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        bd[j] = F_INF;
-        bid[j] = NO_ID;
-        bpos[j] = 0;
-    }
-    int kx, ky, kz;
-    if (!voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz)) return 0;
+template <int K, bool PREC>
+__device__ __forceinline__ int knn27q(const MapView& m, u32 max_probe, const QFrame<PREC>& f, float (&bd)[K],
+                                      u32 (&bid)[K], u32 (&bpos)[K]) {
+    const float qx = f.q[0], qy = f.q[1], qz = f.q[2];
+    const int kx = f.k[0], ky = f.k[1], kz = f.k[2];
     int found = 0;
-    const FaceDist fd = face_distances(qx, qy, qz, kx, ky, kz, m.v);
+    const FaceDist fd = face_distances(qx, qy, qz, f.lk[0], f.lk[1], f.lk[2], m.v);
     // own voxel first, then only the neighbours on the sides within reach of the k-th distance
-    knn_scan_voxel<K>(m, max_probe, kx, ky, kz, qx, qy, qz, found, bd, bid, bpos);
+    knn_scan_voxel<K, PREC>(m, max_probe, kx, ky, kz, qx, qy, qz, found, bd, bid, bpos, f.off(0, 0), f.off(1, 0),
+                            f.off(2, 0));
     const float b0 = (found >= K) ? bd[K - 1] : F_INF;
     bool reach[3][2];
 #pragma unroll
@@ -145,28 +225,54 @@ __device__ __forceinline__ int knn27(const MapView& m, u32 max_probe, float qx, 
                 if ((dz < 0 && !reach[2][0]) || (dz > 0 && !reach[2][1]) || !key_in_range(kz + dz)) continue;
                 if (dx == 0 && dy == 0 && dz == 0) continue;
                 if (found >= K && box_lb2(fd, dx, dy, dz) > bd[K - 1]) continue;
-                knn_scan_voxel<K>(m, max_probe, kx + dx, ky + dy, kz + dz, qx, qy, qz, found, bd, bid, bpos);
+                knn_scan_voxel<K, PREC>(m, max_probe, kx + dx, ky + dy, kz + dz, qx, qy, qz, found, bd, bid, bpos,
+                                        f.off(0, dx), f.off(1, dy), f.off(2, dz));
             }
         }
     }
     return found < K ? found : K;
 }
 
-// Nearest map point of q over the 27 voxels (smallest (d^2, id)). Voxels whose box
-// distance exceeds the best so far, or limit2, are skipped: with limit2 = tau^2 a
-// nearest point beyond tau is not reported, which is the rejection rule anyway.
+template <int K>
+__device__ __forceinline__ void knn_init(float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        bd[j] = F_INF;
+        bid[j] = NO_ID;
+        bpos[j] = 0;
+    }
+}
+
+// K nearest of a world-coordinate query of a plain map.
+template <int K>
+__device__ __forceinline__ int knn27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
+                                     float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+    knn_init<K>(bd, bid, bpos);
+    QFrame<false> f;
+    const int zero[3] = {0, 0, 0};
+    if (!make_qframe<false>(m, qx, qy, qz, zero, f)) return 0;
+    return knn27q<K, false>(m, max_probe, f, bd, bid, bpos);
+}
+
+// Nearest map point of the query over the 27 voxels (smallest (d^2, id)). Voxels whose box
+// distance exceeds the best so far, or limit2, are skipped: with limit2 = tau^2 a nearest
+// point beyond tau is not reported, which is the rejection rule anyway. best_v is the
+// index (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1) of the voxel holding the winner.
 // Returns false when no candidate was found.
-__device__ __forceinline__ bool nearest27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
-                                          float limit2, float& best_d2, u32& best_id, u32& best_pos) {
+template <bool PREC>
+__device__ __forceinline__ bool nearest27q(const MapView& m, u32 max_probe, const QFrame<PREC>& f, float limit2,
+                                           float& best_d2, u32& best_id, u32& best_pos, int& best_v) {
     best_d2 = F_INF;
     best_id = NO_ID;
     best_pos = 0;
-    int kx, ky, kz;
-    if (!voxel_key3(qx, qy, qz, m.inv_v, kx, ky, kz)) return false;
-    const FaceDist fd = face_distances(qx, qy, qz, kx, ky, kz, m.v);
+    best_v = 13;
+    const float qx = f.q[0], qy = f.q[1], qz = f.q[2];
+    const int kx = f.k[0], ky = f.k[1], kz = f.k[2];
+    const FaceDist fd = face_distances(qx, qy, qz, f.lk[0], f.lk[1], f.lk[2], m.v);
     unsigned long long best_key = ~0ull;
     // own voxel first, then only the neighbours on the sides within reach of the bound
-    nn_scan_voxel(m, max_probe, kx, ky, kz, qx, qy, qz, best_key, best_pos);
+    nn_scan_voxel<PREC>(m, max_probe, kx, ky, kz, qx, qy, qz, best_key, best_pos, f.off(0, 0), f.off(1, 0),
+                        f.off(2, 0));
     const float b0 = nn_bound(best_key, limit2);
     bool reach[3][2];
 #pragma unroll
@@ -182,7 +288,9 @@ __device__ __forceinline__ bool nearest27(const MapView& m, u32 max_probe, float
                 if ((dz < 0 && !reach[2][0]) || (dz > 0 && !reach[2][1]) || !key_in_range(kz + dz)) continue;
                 if (dx == 0 && dy == 0 && dz == 0) continue;
                 if (box_lb2(fd, dx, dy, dz) > nn_bound(best_key, limit2)) continue;
-                nn_scan_voxel(m, max_probe, kx + dx, ky + dy, kz + dz, qx, qy, qz, best_key, best_pos);
+                if (nn_scan_voxel<PREC>(m, max_probe, kx + dx, ky + dy, kz + dz, qx, qy, qz, best_key, best_pos,
+                                        f.off(0, dx), f.off(1, dy), f.off(2, dz)))
+                    best_v = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
             }
         }
     }
@@ -195,20 +303,38 @@ __device__ __forceinline__ bool nearest27(const MapView& m, u32 max_probe, float
     return true;
 }
 
+// Nearest map point of a world-coordinate query of a plain map.
+__device__ __forceinline__ bool nearest27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
+                                          float limit2, float& best_d2, u32& best_id, u32& best_pos) {
+    best_d2 = F_INF;
+    best_id = NO_ID;
+    best_pos = 0;
+    QFrame<false> f;
+    const int zero[3] = {0, 0, 0};
+    if (!make_qframe<false>(m, qx, qy, qz, zero, f)) return false;
+    int bv;
+    return nearest27q<false>(m, max_probe, f, limit2, best_d2, best_id, best_pos, bv);
+}
+
 // Eq. 1 from k neighbour positions: Sigma-hat (1/k, about the neighbour mean),
 // C = Sigma-hat + 1e-3 I, Sigma = ||C^-1||_F C (equal to (C^-1 / ||C^-1||_F)^-1).
 // Coordinates are taken relative to the query point for FP32 accuracy.
-template <int K>
-__device__ __forceinline__ void covariance_from_neighbours(const float4* __restrict__ pts, const u32 (&bpos)[K],
-                                                           float qx, float qy, float qz, float4& c0, float4& c1) {
+// pts are the neighbours' stored coordinates; off_of(p, ...) gives the frame offset of a
+// neighbour (zero for plain maps; see TileOffset).
+template <int K, class Off>
+__device__ __forceinline__ void covariance_from_neighbours_f(const float4* __restrict__ pts, const u32 (&bpos)[K],
+                                                             float qx, float qy, float qz, const Off& off_of,
+                                                             float (&c)[6]) {
     float mx = 0.f, my = 0.f, mz = 0.f;
     float rx[K], ry[K], rz[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const float4 p = __ldg(pts + bpos[j]);
-        rx[j] = p.x - qx;
-        ry[j] = p.y - qy;
-        rz[j] = p.z - qz;
+        float ox, oy, oz;
+        off_of(p, qx, qy, qz, ox, oy, oz);
+        rx[j] = __fadd_rn(p.x, ox) - qx;
+        ry[j] = __fadd_rn(p.y, oy) - qy;
+        rz[j] = __fadd_rn(p.z, oz) - qz;
         mx += rx[j];
         my += ry[j];
         mz += rz[j];
@@ -228,16 +354,48 @@ __device__ __forceinline__ void covariance_from_neighbours(const float4* __restr
         syz = fmaf(dy, dz, syz);
         szz = fmaf(dz, dz, szz);
     }
-    const float a = fmaf(sxx, ik, 1e-3f), b = sxy * ik, c = sxz * ik;
+    const float a = fmaf(sxx, ik, 1e-3f), b = sxy * ik, c_ = sxz * ik;
     const float d = fmaf(syy, ik, 1e-3f), e = syz * ik, f = fmaf(szz, ik, 1e-3f);
     // adjugate of the symmetric C
-    const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
-    const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
-    const float det = a * A00 + b * A01 + c * A02;
+    const float A00 = d * f - e * e, A01 = c_ * e - b * f, A02 = b * e - c_ * d;
+    const float A11 = a * f - c_ * c_, A12 = b * c_ - a * e, A22 = a * d - b * b;
+    const float det = a * A00 + b * A01 + c_ * A02;
     const float fro2 = A00 * A00 + A11 * A11 + A22 * A22 + 2.f * (A01 * A01 + A02 * A02 + A12 * A12);
     const float s = sqrtf(fro2) / fabsf(det);  // ||C^-1||_F
-    c0 = make_float4(a * s, b * s, c * s, d * s);
-    c1 = make_float4(e * s, f * s, 1.0f, 0.0f);
+    c[0] = a * s;
+    c[1] = b * s;
+    c[2] = c_ * s;
+    c[3] = d * s;
+    c[4] = e * s;
+    c[5] = f * s;
+}
+
+struct NoOffset {
+    __device__ __forceinline__ void operator()(const float4&, float, float, float, float& x, float& y,
+                                               float& z) const {
+        x = y = z = 0.f;
+    }
+};
+
+// Frame offset of a neighbour of the precision variant: the neighbour lies within two voxels
+// of the query, while the candidate offsets differ by 50 m, so the multiple of 50 nearest to
+// q - p is the one the search added.
+struct TileOffset {
+    __device__ __forceinline__ void operator()(const float4& p, float qx, float qy, float qz, float& x, float& y,
+                                               float& z) const {
+        x = TILE_M * rintf((qx - p.x) * (1.0f / TILE_M));
+        y = TILE_M * rintf((qy - p.y) * (1.0f / TILE_M));
+        z = TILE_M * rintf((qz - p.z) * (1.0f / TILE_M));
+    }
+};
+
+template <int K>
+__device__ __forceinline__ void covariance_from_neighbours(const float4* __restrict__ pts, const u32 (&bpos)[K],
+                                                           float qx, float qy, float qz, float4& c0, float4& c1) {
+    float c[6];
+    covariance_from_neighbours_f<K>(pts, bpos, qx, qy, qz, NoOffset(), c);
+    c0 = make_float4(c[0], c[1], c[2], c[3]);
+    c1 = make_float4(c[4], c[5], 1.0f, 0.0f);
 }
 
 }  // namespace far
