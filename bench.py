@@ -74,6 +74,13 @@ def parse_args():
                     help="sequence: the 128x2048 high-speed sequence (default); batched: 64 uneven problems; "
                          "serving: 16 vehicles streaming scans")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
+                    help="1 = tile-relative points, FP16 covariances (precision_mode 1); default: 0 for the "
+                         "sequence, 1 for the batched workload")
+    ap.add_argument("--world-offset", type=str, default="0,0,0",
+                    help="sequence: metres added to every pose (x,y,z), e.g. 2000,1500,0 for km-scale coordinates")
+    ap.add_argument("--accuracy-scans", type=int, default=None,
+                    help="per-scan pose error vs the FP64 oracle over this many scans (default 6 with --precision 1)")
     ap.add_argument("--autotune", action="store_true", help="batched: tune v, lanes per point and load factor first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -89,16 +96,21 @@ def rank_env():
 
 # --------------------------------------------------------------------------------------- inputs
 class Vehicle:
-    """One simulated vehicle on the oval: scans, true poses and the motion prior."""
+    """One simulated vehicle on the oval: scans, true poses (optionally moved by a world
+    offset) and the motion prior."""
 
-    def __init__(self, rank: int):
+    def __init__(self, rank: int, offset=(0.0, 0.0, 0.0)):
         self.seq = synth.TrackSequence(seed=42 + rank, s0=300.0 * rank)
         self.rng = np.random.default_rng(1000 + rank)
+        self.shift = synth.make_pose(np.eye(3), np.asarray(offset, float))
 
-    def prior(self, t: int, prev_est: np.ndarray) -> np.ndarray:
+    def pose(self, t: int) -> np.ndarray:
+        return self.shift @ self.seq.pose(t)
+
+    def prior(self, t: int, prev_est: np.ndarray, rng=None) -> np.ndarray:
         """IMU-like prediction: previous estimate times the true motion, with seeded noise."""
         d = np.linalg.inv(self.seq.pose(t - 1)) @ self.seq.pose(t)
-        return prev_est @ d @ synth.random_offset(self.rng, PRIOR_NOISE[1], PRIOR_NOISE[0])
+        return prev_est @ d @ synth.random_offset(rng or self.rng, PRIOR_NOISE[1], PRIOR_NOISE[0])
 
 
 def rot_angle(R):
@@ -190,7 +202,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     far_build.build()
     stream = torch.cuda.Stream()
-    veh = Vehicle(rank)
+    offset = [float(x) for x in args.world_offset.split(",")]
+    args.precision = args.precision or 0
+    veh = Vehicle(rank, offset)
     n_total = 1 + args.warmup + args.steps
     scans = [veh.seq.scan(t) for t in range(n_total)]
     dev = [torch.from_numpy(s).cuda() for s in scans]
@@ -200,8 +214,8 @@ def run_ours(args):
     def make_map():
         with torch.cuda.stream(stream):
             m = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=args.max_voxels, load_factor=0.5,
-                             max_scan_points=MAX_SCAN, stream=stream.cuda_stream)
-            m.insert(dev[0], veh.seq.pose(0), asmd=True, r_near=R_NEAR, r_max=R_MAX)
+                             max_scan_points=MAX_SCAN, precision_mode=args.precision, stream=stream.cuda_stream)
+            m.insert(dev[0], veh.pose(0), asmd=True, r_near=R_NEAR, r_max=R_MAX)
         return m
 
     def step(m, thr, t, est, inp):
@@ -216,7 +230,7 @@ def run_ours(args):
     m = make_map()
     m.set_profiling(True)
     thr = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-    est = veh.seq.pose(0)
+    est = veh.pose(0)
     with torch.cuda.stream(stream):
         for t in range(1, 1 + args.warmup):
             est, _ = step(m, thr, t, est, dev[t])
@@ -243,15 +257,17 @@ def run_ours(args):
                 for k_, v_ in st.items():
                     stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
                 n_src, u_v, p_touched = m.gn_footprint()
-                nblk = min((scans[t].shape[0] + 255) // 256, 152 * 8)
-                # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B),
-                # each probed voxel's slot (16 B), its points (12 B xyz + 4 B id + 24 B covariance),
-                # and the FP64 block partials (28 doubles per block)
-                gn_bytes.append(36.0 * n_src + 16.0 * u_v + 40.0 * p_touched + 224.0 * nblk)
+                nblk = min((scans[t].shape[0] * 4 + 127) // 128, 152 * 4)
+                # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B; 12 + 12 + 1
+                # in precision mode), each probed voxel's slot (16 B; + 4 B exponent), its points (12 B xyz
+                # + 4 B id + 24 B covariance; 12 B FP16 covariance), the FP64 block partials (28 doubles)
+                if args.precision:
+                    gn_bytes.append(29.0 * n_src + 20.0 * u_v + 28.0 * p_touched + 224.0 * nblk)
+                else:
+                    gn_bytes.append(36.0 * n_src + 16.0 * u_v + 40.0 * p_touched + 224.0 * nblk)
                 gn_ms.append(st["gn_launch_ms"])
                 gn_launches.append(st["gn_launches"])
                 results.append(res)
-                err = np.linalg.inv(veh.seq.pose(t)) @ est
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     pts = float(sum(scans[t].shape[0] for t in range(1 + args.warmup, n_total)))
@@ -288,7 +304,7 @@ def run_ours(args):
         pinned = [torch.from_numpy(s).pin_memory() for s in scans]
         m2 = make_map()
         thr2 = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-        est2 = veh.seq.pose(0)
+        est2 = veh.pose(0)
         with torch.cuda.stream(stream):
             for t in range(1, 1 + args.warmup):
                 est2, _ = step(m2, thr2, t, est2, pinned[t])
@@ -317,6 +333,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_steps)
+    accuracy = None
+    n_acc = args.accuracy_scans if args.accuracy_scans is not None else (6 if args.precision else 0)
+    if rank == 0 and n_acc > 0:
+        accuracy = precision_accuracy(n_acc, stream)
 
     n_iter = np.mean([r["iters"] for r in results])
     st_mean = {k_: round(v_ / args.steps, 4) for k_, v_ in stage_acc.items()}
@@ -325,7 +345,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s_all / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast LiDAR; the paper's datasets are not available)",
-        "config": workload_config(args.steps, args.warmup, world),
+        "config": dict(workload_config(args.steps, args.warmup, world), precision_mode=args.precision,
+                       world_offset_m=offset),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                        "p99": round(float(np.percentile(lat, 99)), 4),
                        "max": round(float(lat.max()), 4), "mean": round(float(lat.mean()), 4)},
@@ -341,11 +362,68 @@ def run_ours(args):
         "clocks": clk.summary(),
         "wall_s_timed_region": round(wall, 3),
     }
+    if accuracy is not None:
+        out["accuracy_vs_fp64_oracle"] = accuracy
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------------------- precision report
+def precision_accuracy(n_scans: int, stream):
+    """Per-scan pose error of the precision mode and of plain FP32 against the FP64 oracle
+    (precision variant): every side holds the same map history (frames inserted at their true
+    poses, ASMD on) and registers scan t from the same IMU-like prior, at the track's own
+    coordinates and with the track moved 2.5 km and 100 km from the origin."""
+    import torch
+    import oracle
+    from paper_2606_26010_gb300 import far
+    rows = {}
+    for name, off in (("track", (0.0, 0.0, 0.0)), ("2.5km", (2000.0, 1500.0, 0.0)),
+                      ("100km", (1e5 + 13.37, -3.1e4 - 7.9, 212.6))):
+        veh = Vehicle(0, off)
+        rng = np.random.default_rng(77)
+        with torch.cuda.stream(stream):
+            gp = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=1 << 19, max_scan_points=MAX_SCAN, precision_mode=1,
+                              stream=stream.cuda_stream)
+            g0 = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=1 << 19, max_scan_points=MAX_SCAN,
+                              stream=stream.cuda_stream)
+            om = oracle.OracleMap(V, NMAX, K_COV, precision_mode=1)
+            e_p, e_0, e_p0 = [], [], []
+            for t in range(n_scans + 1):
+                scan = veh.seq.scan(t)
+                if t > 0:
+                    init = veh.prior(t, veh.pose(t - 1), rng)
+                    kw = dict(max_iters=MAX_ITERS, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+                    Tp, _, _ = gp.register(scan, init, **kw)
+                    T0, _, _ = g0.register(scan, init, **kw)
+                    To, _, _ = om.register(scan, init, **kw)
+                    e_p.append(pose_error(To, Tp))
+                    e_0.append(pose_error(To, T0))
+                    e_p0.append(pose_error(T0, Tp))
+                T = veh.pose(t)
+                gp.insert(scan, T, asmd=True, r_near=R_NEAR, r_max=R_MAX)
+                g0.insert(scan, T, asmd=True, r_near=R_NEAR, r_max=R_MAX)
+                om.insert(scan, T, asmd=True, r_c=R_NEAR, r_max=R_MAX)
+            gp.close()
+            g0.close()
+
+        def summ(e):
+            a = np.array(e)
+            return {"trans_m_max": float(a[:, 0].max()), "trans_m_median": float(np.median(a[:, 0])),
+                    "rot_rad_max": float(a[:, 1].max())}
+        rows[name] = {"world_offset_m": list(off), "precision_vs_oracle": summ(e_p),
+                      "plain_fp32_vs_oracle": summ(e_0), "precision_vs_plain_fp32": summ(e_p0),
+                      "per_scan_precision_vs_oracle_m": [round(x[0], 8) for x in e_p],
+                      "per_scan_plain_vs_oracle_m": [round(x[0], 8) for x in e_0]}
+    return {"scans": n_scans, "gn_iters": MAX_ITERS, "target": "1e-4 m / 1e-5 rad", "cases": rows}
+
+
+def pose_error(A, B):
+    D = np.linalg.inv(A) @ B
+    return float(np.linalg.norm(D[:3, 3])), rot_angle(D[:3, :3])
 
 
 # --------------------------------------------------------------------------------------- CPU oracle
@@ -410,12 +488,16 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------------------- batched workload
 def run_batched(args):
+    """64 uneven problems in one CUDA graph with the mixed-precision maps (precision_mode 1 unless
+    --precision 0), against the same problems registered one after the other with plain FP32
+    maps through far_register_scan (the single-scan form)."""
     import torch
     from paper_2606_26010_gb300 import autotune as at
     from paper_2606_26010_gb300 import build as far_build
     from paper_2606_26010_gb300 import far
 
     far_build.build()
+    prec = 1 if args.precision is None else args.precision
     seq, specs = synth.batched_problems(7, 64)
     cache = {}
 
@@ -430,12 +512,14 @@ def run_batched(args):
     trials = None
     if args.autotune:
         idx = list(range(0, len(specs), 8))
-        best, tr = at.autotune(scan_dev, seq.pose, [specs[i] for i in idx], [queries[i] for i in idx], reps=3, **reg)
+        best, tr = at.autotune(scan_dev, seq.pose, [specs[i] for i in idx], [queries[i] for i in idx], reps=3,
+                               precision_mode=prec, **reg)
         choice = {"voxel_size": best.voxel_size, "threads_per_point": best.threads_per_point,
                   "load_factor": best.load_factor, "source": "autotuned on 8 of the 64 problems"}
         trials = [t.__dict__ for t in tr]
     max_scan = at.max_points(scan_dev, specs, queries)
-    maps = at.build_maps(scan_dev, seq.pose, specs, choice["voxel_size"], choice["load_factor"], max_scan)
+    maps = at.build_maps(scan_dev, seq.pose, specs, choice["voxel_size"], choice["load_factor"], max_scan,
+                         precision_mode=prec)
     reg["threads_per_point"] = choice["threads_per_point"]
     batch = far.Batch(maps)
     inits = [sp.init for sp in specs]
@@ -449,16 +533,19 @@ def run_batched(args):
             t0 = time.perf_counter()
             poses, stats = batch.register(queries, inits, **reg)
             times.append(time.perf_counter() - t0)
-    # the same problems one at a time through far_register_scan
+    # the plain FP32 single-scan form: the same problems one at a time through far_register_scan
+    reg_single = dict(reg, threads_per_point=0)
+    plain_maps = maps if prec == 0 else at.build_maps(scan_dev, seq.pose, specs, V, 0.5, max_scan)
+    for m, q, ini in zip(plain_maps, queries, inits):
+        m.register(q, ini, **reg_single)
     seq_t = []
-    for m, q, ini in zip(maps, queries, inits):
-        m.register(q, ini, **reg)
     for _ in range(2):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for m, q, ini in zip(maps, queries, inits):
-            m.register(q, ini, **reg)
+        plain_poses = [m.register(q, ini, **reg_single)[0] for m, q, ini in zip(plain_maps, queries, inits)]
         seq_t.append(time.perf_counter() - t0)
     errs = [at.pose_error(sp.truth, P) for sp, P in zip(specs, poses)]
+    errs_plain = [at.pose_error(sp.truth, P) for sp, P in zip(specs, plain_poses)]
     t_b = float(np.median(times))
     t_s = float(min(seq_t))
     ns = sorted(int(q.shape[0]) for q in queries)
@@ -470,13 +557,20 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ray-cast LiDAR)",
         "config": {"workload": "64 problems on the walled oval: scans 5k-300k points log-uniform from mixed "
                                "16/32/64/128-beam sensors, maps 0.1-3 M points log-uniform from prior frames",
-                   "problems": len(specs), "points_per_batch": int(n_pts),
+                   "precision_mode": prec, "problems": len(specs), "points_per_batch": int(n_pts),
                    "scan_points_min_median_max": [ns[0], ns[len(ns) // 2], ns[-1]],
                    "map_points_min_median_max": [mp[0], mp[len(mp) // 2], mp[-1]],
+                   "map_bytes_total": int(sum(far.map_bytes(voxel_size=m.params.voxel_size,
+                                                            max_voxels=m.params.max_voxels,
+                                                            load_factor=m.params.load_factor,
+                                                            max_scan_points=m.params.max_scan_points,
+                                                            precision_mode=prec) for m in maps)),
                    "gn_max_iters": MAX_ITERS, "conv_eps": CONV_EPS, "params": choice},
-        "sequential_same_gpu": {"value": round(n_pts / t_s / 1e6, 3), "unit": UNIT, "ms_per_batch": round(1e3 * t_s, 3),
-                                "api": "far_register_scan, one problem after the other"},
-        "batched_over_sequential": round(t_s / t_b, 3),
+        "plain_fp32_single_scan_same_gpu": {
+            "value": round(n_pts / t_s / 1e6, 3), "unit": UNIT, "ms_per_batch": round(1e3 * t_s, 3),
+            "api": "far_register_scan, plain FP32 maps, one problem after the other",
+            "median_trans_err_vs_truth_m": round(float(np.median([e[0] for e in errs_plain])), 5)},
+        "batched_over_plain_single_scan": round(t_s / t_b, 3),
         "accuracy_vs_truth": {"median_trans_m": round(float(np.median([e[0] for e in errs])), 5),
                               "median_rot_rad": round(float(np.median([e[1] for e in errs])), 7),
                               "registered": int(sum(1 for s_ in stats if s_["status"] == 0))},

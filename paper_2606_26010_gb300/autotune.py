@@ -40,13 +40,13 @@ def pose_error(A: np.ndarray, B: np.ndarray):
 
 
 def build_maps(scan_fn, pose_fn, specs, voxel_size, load_factor, max_scan_points, n_max=20, k_cov=5, r_near=10.0,
-               r_max=200.0, max_voxels_cap=1 << 22):
+               r_max=200.0, max_voxels_cap=1 << 22, precision_mode=0):
     """One map per problem from its prior frames (ASMD insert) until it reaches its target size."""
     maps = []
     for sp in specs:
         voxels = int(min(max_voxels_cap, max(1 << 14, sp.target_map_points // 2 * (0.5 / voxel_size) ** 2)))
         m = far.VoxelMap(voxel_size, n_max, k_cov, -1.0, max_voxels=voxels, load_factor=load_factor,
-                         max_scan_points=max_scan_points)
+                         max_scan_points=max_scan_points, precision_mode=precision_mode)
         for idx in sp.map_idx:
             try:
                 m.insert(scan_fn(idx), pose_fn(idx), asmd=True, r_near=r_near, r_max=r_max)
@@ -82,7 +82,7 @@ def time_batch(batch, queries, inits, reps=5, **reg):
 
 
 def autotune(scan_fn, pose_fn, specs, queries, grid=None, err_margin=1.5, err_floor_m=0.02, reps=5, log=None,
-             **reg):
+             precision_mode=0, **reg):
     """Search the grid on `specs` (a sample of problems). Returns (best Trial, all trials)."""
     grid = grid or DEFAULT_GRID
     max_scan = max_points(scan_fn, specs, queries)
@@ -90,7 +90,7 @@ def autotune(scan_fn, pose_fn, specs, queries, grid=None, err_margin=1.5, err_fl
     inits = [sp.init for sp in specs]
     trials = []
     for v, lf in itertools.product(grid["voxel_size"], grid["load_factor"]):
-        maps = build_maps(scan_fn, pose_fn, specs, v, lf, max_scan)
+        maps = build_maps(scan_fn, pose_fn, specs, v, lf, max_scan, precision_mode=precision_mode)
         batch = far.Batch(maps)
         map_pts = sum(m.size()[1] for m in maps)
         for tpp in grid["threads_per_point"]:
