@@ -29,11 +29,29 @@ namespace far {
 void note_launch();
 // Set the message far_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
-// Launch a kernel and count it.
-#define FAR_LAUNCH(kernel, grid, block, smem, stream, ...)              \
-    do {                                                                \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);     \
-        ::far::note_launch();                                           \
+// Launch a kernel and count it. Every kernel of the library begins with pdl_wait() and is
+// launched with programmatic dependent launch (FAR_LAUNCH_PDL below).
+#define FAR_LAUNCH(kernel_, grid_, block_, smem_, stream_, ...) \
+    FAR_LAUNCH_PDL(kernel_, grid_, block_, smem_, stream_, __VA_ARGS__)
+
+// Programmatic dependent launch: the kernel may start while the previous kernel of its stream
+// still runs (hiding the launch latency); it must call pdl_wait() before it touches anything
+// that kernel wrote, and pdl_wait() returns once that kernel has completed and its writes are
+// visible. Kernels launched this way call pdl_wait() first.
+#define FAR_LAUNCH_PDL(kernel_, grid_, block_, smem_, stream_, ...)                     \
+    do {                                                                                 \
+        cudaLaunchConfig_t cfg__ = {};                                                   \
+        cfg__.gridDim = dim3(grid_);                                                     \
+        cfg__.blockDim = dim3(block_);                                                   \
+        cfg__.dynamicSmemBytes = (smem_);                                                \
+        cfg__.stream = (stream_);                                                        \
+        cudaLaunchAttribute at__[1];                                                     \
+        at__[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                 \
+        at__[0].val.programmaticStreamSerializationAllowed = 1;                          \
+        cfg__.attrs = at__;                                                              \
+        cfg__.numAttrs = 1;                                                              \
+        (void)cudaLaunchKernelEx(&cfg__, kernel_, __VA_ARGS__);                          \
+        ::far::note_launch();                                                            \
     } while (0)
 
 typedef unsigned long long u64;
@@ -106,7 +124,7 @@ struct RegState {
     double g[6];
     double xi[6];
     double chi2;
-    double xi_norm;
+    double xi_norm2;     // squared norm of the last increment
     u32 n_corr, n_p2p;
     u32 iters;           // updates applied
     u32 converged;
@@ -116,6 +134,12 @@ struct RegState {
     u32 n_src;           // source points of this registration
     unsigned long long t_start_ns;  // %globaltimer at the start of the registration
 };
+
+// Wait for the previous kernel of the stream (programmatic dependent launch); a no-op for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Allow the next programmatically dependent kernel of the stream to begin launching.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ----------------------------------------------------------------------------- keys
 __device__ __forceinline__ bool voxel_key3(float x, float y, float z, float inv_v, int& kx, int& ky, int& kz) {

@@ -18,12 +18,12 @@ namespace far {
 namespace {
 
 // Threads per block and minimum resident blocks per SM of the linearisation kernel
-// (compile-time tuning knobs; 128 x 4 keeps the kernel free of register spills).
+// (compile-time tuning knobs; 128 x 5 keeps the kernel free of register spills).
 #ifndef FAR_GN_THREADS
 #define FAR_GN_THREADS 128
 #endif
 #ifndef FAR_GN_MIN_BLOCKS
-#define FAR_GN_MIN_BLOCKS 4
+#define FAR_GN_MIN_BLOCKS 5
 #endif
 constexpr int GN_THREADS = FAR_GN_THREADS;
 constexpr int NACC = 28;   // 21 H + 6 g + chi2
@@ -204,7 +204,14 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, c
 // partial sums (FP32 within warps, FP64 across the block's warps).
 template <int TPP, bool PREC>
 __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vgrid) {
-    __shared__ float red[GN_THREADS / 32][NACC + 2];
+    // Each group of TPP lanes accumulates its 28 values in shared memory (its first lane
+    // adds; an odd row stride keeps the adding lanes of a warp on distinct banks), which
+    // keeps the accumulators out of the registers of every lane.
+    constexpr int kGroups = GN_THREADS / TPP;
+    constexpr int ACC_STRIDE = NACC + 3;
+    constexpr int kParts = GN_THREADS / 32;
+    __shared__ float gacc[kGroups * ACC_STRIDE];
+    __shared__ float red[kParts][NACC + 2];
     __shared__ float pose_f[12];
     __shared__ u32 s_flag;
     RegState* st = a.st;
@@ -216,6 +223,7 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
         if ((j & 3) == 3) t = __dsub_rn(t, a.anchor[j >> 2]);
         pose_f[j] = (float)t;
     }
+    for (int j = threadIdx.x; j < kGroups * ACC_STRIDE; j += GN_THREADS) gacc[j] = 0.f;
     __syncthreads();
     if (s_flag) return;
 
@@ -231,9 +239,6 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
     const u32 warp_first = vblock * kGroupsPerBlock + (threadIdx.x & ~31u) / TPP;
     const u32 stride = vgrid * kGroupsPerBlock;
 
-    float acc[NACC];
-#pragma unroll
-    for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
     u32 n_corr = 0, n_p2p = 0;
 
     for (u32 off = 0; warp_first + off < n; off += stride) {   // warp-uniform trip count
@@ -333,7 +338,7 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
         const float T00 = qz * MQ10 - qy * MQ20, T01 = qz * MQ11 - qy * MQ21, T02 = qz * MQ12 - qy * MQ22;
         const float T11 = -qz * MQ01 + qx * MQ21, T12 = -qz * MQ02 + qx * MQ22;
         const float T22 = qy * MQ02 - qx * MQ12;
-        float* h = acc;
+        float* h = gacc + (threadIdx.x / TPP) * ACC_STRIDE;
         // row 0..2 rotational block, cross block -MQ^T, translational block M
         h[0] = fmaf(w, T00, h[0]);   h[1] = fmaf(w, T01, h[1]);   h[2] = fmaf(w, T02, h[2]);
         h[3] = fmaf(w, -MQ00, h[3]); h[4] = fmaf(w, -MQ10, h[4]); h[5] = fmaf(w, -MQ20, h[5]);
@@ -356,34 +361,43 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
         if (p2p) ++n_p2p;
     }
 
-    // ---- reduction: FP32 within the warp, FP64 across warps and blocks ----
+    // ---- reduction: FP32 over the groups of each part, FP64 across parts and blocks ----
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < NACC; ++j) {
-        const float v = warp_sum(acc[j]);
-        if (lane == 0) red[warp][j] = v;
-    }
     n_corr = warp_sum_u(n_corr);
     n_p2p = warp_sum_u(n_p2p);
-    if (lane == 0) {
-        red[warp][NACC] = __uint_as_float(n_corr);
-        red[warp][NACC + 1] = __uint_as_float(n_p2p);
+    __syncthreads();
+    {
+        // thread (part, j): FP32 sum of value j over groups part * G/P .. in order
+        constexpr int kPer = kGroups / kParts;
+        if (lane < NACC) {
+            float v = 0.f;
+#pragma unroll 4
+            for (int g = 0; g < kPer; ++g) v += gacc[(warp * kPer + g) * ACC_STRIDE + lane];
+            red[warp][lane] = v;
+        } else if (lane == NACC) {
+            red[warp][NACC] = __uint_as_float(n_corr);
+            red[warp][NACC + 1] = __uint_as_float(n_p2p);
+        }
     }
     __syncthreads();
     if (threadIdx.x < NPART) {
         double s = 0.0;
         if (threadIdx.x < NACC) {
-            for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)red[w][threadIdx.x];
+            for (int w = 0; w < kParts; ++w) s += (double)red[w][threadIdx.x];
         } else if (threadIdx.x < NACC + 2) {
-            for (int w = 0; w < GN_THREADS / 32; ++w) s += (double)__float_as_uint(red[w][threadIdx.x]);
+            for (int w = 0; w < kParts; ++w) s += (double)__float_as_uint(red[w][threadIdx.x]);
         }
         // value-major: partials[v * blocks + block], read coalesced by the solve kernel
         a.partials[(size_t)threadIdx.x * vgrid + vblock] = s;
     }
 }
 
+// The Gauss-Newton chain (lin, solve, lin, ...) is launched with programmatic dependent launch:
+// each kernel waits for its predecessor first and immediately lets its successor launch.
 template <int TPP, bool PREC>
 __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs a) {
+    pdl_wait();
+    pdl_trigger();
     gn_lin_block<TPP, PREC>(a, blockIdx.x, gridDim.x);
 }
 
@@ -392,43 +406,61 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin(GnArgs
 template <int TPP, bool PREC>
 __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(const BatchProblem* __restrict__ probs,
                                                                                 const u32* __restrict__ block_prob) {
+    pdl_wait();
+    pdl_trigger();
     const BatchProblem& p = probs[block_prob[blockIdx.x]];
     gn_lin_block<TPP, PREC>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
 
 // Solve half: one block reduces the block partials in a fixed order (FP64), then one
 // thread solves H xi = -g by Cholesky and applies T <- exp(xi) T (Eq. 6) in FP64.
-constexpr int SOLVE_THREADS = 256;
+constexpr int SOLVE_THREADS = 256;   // 8 warps; the single solving thread keeps up to 255 registers
 __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
     __shared__ double tot[NPART];
     __shared__ u32 s_flag;
     RegState* st = a.st;
-    if (threadIdx.x == 0) s_flag = *reinterpret_cast<volatile u32*>(&st->done);
-    __syncthreads();
-    if (s_flag) return;
+    // the stop flag, the pose and the partials are loaded together: when the flag is set the
+    // loaded values are simply not used (the partial buffer is always allocated)
+    double T[12];
+    if (threadIdx.x == 0) {
+        s_flag = *reinterpret_cast<volatile u32*>(&st->done);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) T[j] = st->T[j];
+    }
     {
-        // warp w reduces values w, w + 8, ...: lane l sums blocks l, l + 32, ... (coalesced,
-        // four loads in flight), then a fixed shuffle tree; the order never depends on timing
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int v = warp; v < NPART; v += SOLVE_THREADS / 32) {
-            const double* col = a.partials + (size_t)v * nblocks;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            u32 b = lane;
-            for (; b + 96 < nblocks; b += 128) {
-                s0 += col[b];
-                s1 += col[b + 32];
-                s2 += col[b + 64];
-                s3 += col[b + 96];
+        // warp w reduces values w, w + 8, w + 16, w + 24 at once: lane l sums blocks l, l + 32, ...
+        // into two chains per value (eight loads per step, unrolled so that 32 are in flight),
+        // then a fixed shuffle tree; the order never depends on timing
+        constexpr int W = SOLVE_THREADS / 32, VPW = NPART / W;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const double* col = a.partials + (size_t)w * nblocks;
+        const size_t vs = (size_t)W * nblocks;
+        double c0[VPW], c1[VPW];
+#pragma unroll
+        for (int j = 0; j < VPW; ++j) c0[j] = c1[j] = 0.0;
+        u32 b = lane;
+#pragma unroll 4
+        for (; b + 32 < nblocks; b += 64) {
+#pragma unroll
+            for (int j = 0; j < VPW; ++j) {
+                c0[j] += col[j * vs + b];
+                c1[j] += col[j * vs + b + 32];
             }
-            for (; b < nblocks; b += 32) s0 += col[b];
-            double s = (s0 + s1) + (s2 + s3);
+        }
+        if (b < nblocks) {
+#pragma unroll
+            for (int j = 0; j < VPW; ++j) c0[j] += col[j * vs + b];
+        }
+#pragma unroll
+        for (int j = 0; j < VPW; ++j) {
+            double s = c0[j] + c1[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) tot[v] = s;
+            if (lane == 0) tot[w + j * W] = s;
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (s_flag || threadIdx.x != 0) return;
 
     double H[6][6], g[6];
 #pragma unroll
@@ -452,9 +484,6 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
             // written before the bookkeeping (the next launch waits on it)
             double E[12];
             se3_exp_dev(xi, E);
-            double T[12];
-#pragma unroll
-            for (int j = 0; j < 12; ++j) T[j] = st->T[j];
             const double tr[3] = {T[3] - a.anchor[0], T[7] - a.anchor[1], T[11] - a.anchor[2]};
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -470,7 +499,7 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
                 st->xi[j] = xi[j];
                 nx += xi[j] * xi[j];
             }
-            st->xi_norm = sqrt(nx);
+            st->xi_norm2 = nx;
             st->iters += 1;
             if (nx <= a.conv_eps * a.conv_eps) {
                 st->converged = 1;
@@ -498,16 +527,24 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
     st->n_p2p = (u32)tot[29];
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) { gn_solve_block(a, nblocks); }
+__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) {
+    pdl_wait();
+    pdl_trigger();
+    gn_solve_block(a, nblocks);
+}
 
 // Batched solve: block p reduces and solves problem p.
 __global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_batch(const BatchProblem* __restrict__ probs) {
+    pdl_wait();
+    pdl_trigger();
     const BatchProblem& p = probs[blockIdx.x];
     gn_solve_block(p.args, p.nblocks);
 }
 
 // Reset every problem's state to its initial pose (init: 16 doubles per problem).
 __global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 nprob, const double* __restrict__ init) {
+    pdl_wait();
+    pdl_trigger();
     const u32 p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nprob) return;
     RegState* st = probs[p].args.st;
@@ -518,7 +555,7 @@ __global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 npr
         st->xi[j] = 0.0;
     }
     st->chi2 = 0.0;
-    st->xi_norm = 0.0;
+    st->xi_norm2 = 0.0;
     st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
     st->block_counter = 0;
     st->n_src = *probs[p].args.n_src;
@@ -527,6 +564,8 @@ __global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 npr
 
 // Copy every problem's state into one array (one device-to-host copy afterwards).
 __global__ void k_gather_states(const BatchProblem* __restrict__ probs, u32 nprob, RegState* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const u32 p = blockIdx.x;
     if (p >= nprob) return;
     const u32* src = reinterpret_cast<const u32*>(probs[p].args.st);
@@ -535,6 +574,8 @@ __global__ void k_gather_states(const BatchProblem* __restrict__ probs, u32 npro
 }
 
 __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
+    pdl_wait();
+    pdl_trigger();
     st->n_src = n_src ? *n_src : 0u;
     for (int j = 0; j < 16; ++j) st->T[j] = init.m[j];
     for (int j = 0; j < 36; ++j) st->H[j] = 0.0;
@@ -543,7 +584,7 @@ __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
         st->xi[j] = 0.0;
     }
     st->chi2 = 0.0;
-    st->xi_norm = 0.0;
+    st->xi_norm2 = 0.0;
     st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
     st->block_counter = 0;
     st->t_start_ns = globaltimer_ns();
@@ -551,6 +592,8 @@ __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
 
 // Output covariance: H^-1 of the last linearisation (FP64, single thread).
 __global__ void k_gn_cov(RegState* st, double* cov) {
+    pdl_wait();
+    pdl_trigger();
     double H[6][6], e[6], x[6];
 #pragma unroll
     for (int r = 0; r < 6; ++r)
@@ -572,6 +615,8 @@ __global__ void k_gn_cov(RegState* st, double* cov) {
 // voxels probed by the 27-neighbourhoods of all source points and the points
 // they hold (the unique data a launch must read at least once).
 __global__ void k_footprint(GnArgs a, u32* __restrict__ touched, unsigned long long* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const MapView m = a.map;
     const RegState* st = a.st;
     const u32 n = st->n_src;
@@ -700,17 +745,17 @@ cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblo
     const u32 g = gn_grid(n_upper, a.tpp);
     const bool prec = a.map.tv > 0;
     switch (gn_tpp(a.tpp)) {
-        case 4: if (prec) FAR_LAUNCH((k_gn_lin<4, true>), g, GN_THREADS, 0, s, a);
-                else FAR_LAUNCH((k_gn_lin<4, false>), g, GN_THREADS, 0, s, a);
+        case 4: if (prec) FAR_LAUNCH_PDL((k_gn_lin<4, true>), g, GN_THREADS, 0, s, a);
+                else FAR_LAUNCH_PDL((k_gn_lin<4, false>), g, GN_THREADS, 0, s, a);
                 break;
-        case 8: if (prec) FAR_LAUNCH((k_gn_lin<8, true>), g, GN_THREADS, 0, s, a);
-                else FAR_LAUNCH((k_gn_lin<8, false>), g, GN_THREADS, 0, s, a);
+        case 8: if (prec) FAR_LAUNCH_PDL((k_gn_lin<8, true>), g, GN_THREADS, 0, s, a);
+                else FAR_LAUNCH_PDL((k_gn_lin<8, false>), g, GN_THREADS, 0, s, a);
                 break;
-        case 32: if (prec) FAR_LAUNCH((k_gn_lin<32, true>), g, GN_THREADS, 0, s, a);
-                 else FAR_LAUNCH((k_gn_lin<32, false>), g, GN_THREADS, 0, s, a);
+        case 32: if (prec) FAR_LAUNCH_PDL((k_gn_lin<32, true>), g, GN_THREADS, 0, s, a);
+                 else FAR_LAUNCH_PDL((k_gn_lin<32, false>), g, GN_THREADS, 0, s, a);
                  break;
-        default: if (prec) FAR_LAUNCH((k_gn_lin<1, true>), g, GN_THREADS, 0, s, a);
-                 else FAR_LAUNCH((k_gn_lin<1, false>), g, GN_THREADS, 0, s, a);
+        default: if (prec) FAR_LAUNCH_PDL((k_gn_lin<1, true>), g, GN_THREADS, 0, s, a);
+                 else FAR_LAUNCH_PDL((k_gn_lin<1, false>), g, GN_THREADS, 0, s, a);
                  break;
     }
     *nblocks = g;
@@ -718,7 +763,7 @@ cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblo
 }
 
 cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s) {
-    FAR_LAUNCH(k_gn_solve, 1, SOLVE_THREADS, 0, s, a, nblocks);
+    FAR_LAUNCH_PDL(k_gn_solve, 1, SOLVE_THREADS, 0, s, a, nblocks);
     return cudaGetLastError();
 }
 
@@ -731,20 +776,20 @@ cudaError_t gn_batch_begin(const BatchProblem* probs, u32 nprob, const double* i
 cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob, u32 total_blocks, u32 nprob,
                                int tpp, bool prec, cudaStream_t s) {
     switch (gn_tpp(tpp)) {
-        case 4: if (prec) FAR_LAUNCH((k_gn_lin_batch<4, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
-                else FAR_LAUNCH((k_gn_lin_batch<4, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+        case 4: if (prec) FAR_LAUNCH_PDL((k_gn_lin_batch<4, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                else FAR_LAUNCH_PDL((k_gn_lin_batch<4, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
                 break;
-        case 8: if (prec) FAR_LAUNCH((k_gn_lin_batch<8, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
-                else FAR_LAUNCH((k_gn_lin_batch<8, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+        case 8: if (prec) FAR_LAUNCH_PDL((k_gn_lin_batch<8, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                else FAR_LAUNCH_PDL((k_gn_lin_batch<8, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
                 break;
-        case 32: if (prec) FAR_LAUNCH((k_gn_lin_batch<32, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
-                 else FAR_LAUNCH((k_gn_lin_batch<32, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+        case 32: if (prec) FAR_LAUNCH_PDL((k_gn_lin_batch<32, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 else FAR_LAUNCH_PDL((k_gn_lin_batch<32, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
                  break;
-        default: if (prec) FAR_LAUNCH((k_gn_lin_batch<1, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
-                 else FAR_LAUNCH((k_gn_lin_batch<1, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+        default: if (prec) FAR_LAUNCH_PDL((k_gn_lin_batch<1, true>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
+                 else FAR_LAUNCH_PDL((k_gn_lin_batch<1, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
                  break;
     }
-    FAR_LAUNCH(k_gn_solve_batch, nprob, SOLVE_THREADS, 0, s, probs);
+    FAR_LAUNCH_PDL(k_gn_solve_batch, nprob, SOLVE_THREADS, 0, s, probs);
     return cudaGetLastError();
 }
 

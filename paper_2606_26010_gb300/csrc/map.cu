@@ -22,6 +22,8 @@ inline u32 blocks_for(u32 n, u32 tpb = TPB) {
 }
 
 __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float* p = reinterpret_cast<const float*>(src + (size_t)i * stride);
@@ -33,6 +35,8 @@ __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* 
 // receives the coordinates relative to the tile origin.
 __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
                              float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (dp.T) {
@@ -80,6 +84,8 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
 
 __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slots, u32 mask,
                                  u32* __restrict__ out_slot, u32* __restrict__ out_idx, MapCounters* ctr) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out_idx[i] = i;
@@ -115,6 +121,8 @@ __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slot
 }
 
 __global__ void k_group_heads(const u32* __restrict__ sk, u32 n, u32 sentinel, u32* __restrict__ flags) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const u32 k = sk[i];
@@ -124,6 +132,8 @@ __global__ void k_group_heads(const u32* __restrict__ sk, u32 n, u32 sentinel, u
 __global__ void k_group_starts(const u32* __restrict__ sk, const u32* __restrict__ flags,
                                const u32* __restrict__ gidx, u32 n, u32 sentinel, u32* __restrict__ gstart,
                                const u32* __restrict__ scal) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (flags[i]) gstart[gidx[i]] = i;
@@ -143,6 +153,8 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
 __global__ void k_asmd_near(const u32* __restrict__ gstart, const u32* __restrict__ scal,
                             const u32* __restrict__ sk, const Slot* __restrict__ slots, double v, InsertCfg cfg,
                             const double* __restrict__ dev_T, MapCounters* ctr) {
+    pdl_wait();
+    pdl_trigger();
     if (dev_T) {
         cfg.sx = dev_T[3];
         cfg.sy = dev_T[7];
@@ -213,6 +225,8 @@ struct AdmitArgs {
 // (lane j: points j and j + 32) and test a candidate against all of them at once;
 // windows of 32 candidates are prefetched one per lane.
 __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
+    pdl_wait();
+    pdl_trigger();
     if (a.dev_T) {
         a.cfg.sx = a.dev_T[3];
         a.cfg.sy = a.dev_T[7];
@@ -316,6 +330,8 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
 __global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __restrict__ rank,
                              const u32* __restrict__ pos, u32 n, float4* pts, const u32* __restrict__ scal,
                              MapCounters* ctr) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
     const u32 base = ctr->next_id;
@@ -328,6 +344,8 @@ __global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __rest
 // Group heads: the first (smallest) input index of every voxel of the batch.
 __global__ void k_mark_heads(const u32* __restrict__ gstart, const u32* __restrict__ sv,
                              const u32* __restrict__ scal, u32* __restrict__ head_flag) {
+    pdl_wait();
+    pdl_trigger();
     const u32 ng = scal[SCAL_NGROUPS];
     for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
         head_flag[sv[gstart[g]]] = 1u;
@@ -338,6 +356,8 @@ __global__ void k_grouped_dest(const u32* __restrict__ admitted, const u32* __re
                                const u32* __restrict__ a_j, const u32* __restrict__ grp_base,
                                const u32* __restrict__ pos, u32 n, u32* __restrict__ dest,
                                u32* __restrict__ added, const u64* __restrict__ keys, u64* __restrict__ added_key) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
     const u32 d = grp_base[a_ord[i]] + a_j[i];
@@ -347,6 +367,8 @@ __global__ void k_grouped_dest(const u32* __restrict__ admitted, const u32* __re
 }
 
 __global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal) {
+    pdl_wait();
+    pdl_trigger();
     const u32 t = scal[SCAL_NADMIT];
     ctr->next_id += t;
     ctr->n_points += t;
@@ -361,6 +383,8 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
                                                  const u32* __restrict__ qpos, u32 n, const u32* __restrict__ n_dev,
                                                  float4* __restrict__ cov_out, const u32* __restrict__ out_pos,
                                                  u32* __restrict__ knn_ids) {
+    pdl_wait();
+    pdl_trigger();
     const u32 nn = n_dev ? min(n, *n_dev) : n;
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
@@ -389,6 +413,8 @@ __global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __re
                                                       const u64* __restrict__ qkey, u32 n,
                                                       const u32* __restrict__ n_dev, float4* __restrict__ cov_tmp,
                                                       int* __restrict__ cexp) {
+    pdl_wait();
+    pdl_trigger();
     const u32 nn = min(n, *n_dev);
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
@@ -423,6 +449,8 @@ __global__ void k_cov_encode(const u32* __restrict__ grp_base, const u32* __rest
                              const int* __restrict__ grp_exp0, const int* __restrict__ cexp,
                              const u32* __restrict__ added, const float4* __restrict__ cov_tmp, u32 nmax,
                              uint2* __restrict__ cov_h4, u32* __restrict__ cov_h2) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const u32 ng = scal[SCAL_NGROUPS];
     const u32 n_add = scal[SCAL_NADMIT];
@@ -462,6 +490,8 @@ __global__ void k_cov_encode(const u32* __restrict__ grp_base, const u32* __rest
 __global__ void k_src_encode(const u32* __restrict__ grp_base, const u32* __restrict__ scal,
                              const float4* __restrict__ src_cov, uint2* __restrict__ h4, u32* __restrict__ h2,
                              signed char* __restrict__ e_out) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const u32 ng = scal[SCAL_NGROUPS];
     const u32 n_add = scal[SCAL_NADMIT];
@@ -498,6 +528,8 @@ __global__ void k_src_encode(const u32* __restrict__ grp_base, const u32* __rest
 __global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __restrict__ dest,
                                const u32* __restrict__ rank, const float4* __restrict__ in4, u32 n,
                                float4* __restrict__ src, u32* __restrict__ src_index) {
+    pdl_wait();
+    pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !admitted[i]) return;
     const u32 d = dest[i];
@@ -507,11 +539,15 @@ __global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __re
 }
 
 __global__ void k_iota(u32* a, u32 n) {
+    pdl_wait();
+    pdl_trigger();
     for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
 
 __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, double cz, double r2, u32* ring,
                         u32 max_buckets, MapCounters* ctr, const double* __restrict__ dev_T) {
+    pdl_wait();
+    pdl_trigger();
     if (dev_T) {
         cx = dev_T[3];
         cy = dev_T[7];
@@ -556,6 +592,8 @@ __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, do
 
 __global__ void k_rebuild(const Slot* __restrict__ old_slots, u32 old_cap, Slot* new_slots, u32 mask,
                           MapCounters* ctr) {
+    pdl_wait();
+    pdl_trigger();
     for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < old_cap; h += gridDim.x * blockDim.x) {
         const Slot s = old_slots[h];
         if (s.key >> 63) continue;
@@ -576,6 +614,8 @@ __global__ void k_rebuild(const Slot* __restrict__ old_slots, u32 old_cap, Slot*
 
 __global__ void k_list_slots(const Slot* __restrict__ slots, u32 cap, u64* keys, u32* buckets, u32* counts,
                              u32* n_out, u32 cap_out) {
+    pdl_wait();
+    pdl_trigger();
     for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
         const Slot s = slots[h];
         if ((s.key >> 63) || s.bucket == NO_BUCKET || s.count == 0) continue;
@@ -590,6 +630,8 @@ __global__ void k_list_slots(const Slot* __restrict__ slots, u32 cap, u64* keys,
 __global__ void k_gather(MapView m, const u32* __restrict__ buckets, const u32* __restrict__ counts,
                          const u32* __restrict__ offsets, const u64* __restrict__ keys, u32 nvox,
                          float4* __restrict__ pts_out, float4* __restrict__ cov_out) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const u32 nmax = m.nmax;
     for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nvox; g += (gridDim.x * blockDim.x) >> 5) {
@@ -645,6 +687,8 @@ __device__ __forceinline__ bool world_query_frame(const MapView& m, float qx, fl
 template <int K>
 __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __restrict__ q, u32 n,
                                                    u32* __restrict__ ids, int32_t* __restrict__ found_out) {
+    pdl_wait();
+    pdl_trigger();
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const float4 p = q[r];
@@ -666,6 +710,8 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
 
 __global__ void __launch_bounds__(TPB) k_nearest_stage(MapView m, const float4* __restrict__ q, u32 n, float tau2,
                                                        int64_t* __restrict__ ids, float* __restrict__ d2_out) {
+    pdl_wait();
+    pdl_trigger();
     const u32 max_probe = m.ctr->max_probe;
     for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const float4 p = q[r];
@@ -845,6 +891,8 @@ cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, 
 }
 
 __global__ void k_clear_counters(MapCounters* ctr, u32 ring_tail) {
+    pdl_wait();
+    pdl_trigger();
     MapCounters c{};
     c.ring_tail = ring_tail;
     *ctr = c;
@@ -916,6 +964,8 @@ namespace {
 __global__ void k_export_sources(const float4* __restrict__ src, const u32* __restrict__ src_index,
                                  const float4* __restrict__ src_cov, const u32* __restrict__ n_dev, u32 n,
                                  int64_t* __restrict__ index, float* __restrict__ cov6, uint8_t* __restrict__ valid) {
+    pdl_wait();
+    pdl_trigger();
     const u32 nn = min(n, *n_dev);
     for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < nn; j += gridDim.x * blockDim.x) {
         const u32 r = __float_as_uint(src[j].w);

@@ -41,6 +41,8 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* smem_warp, u32& total
 }
 
 __global__ void k_scan_reduce(const u32* __restrict__ in, u32 n, const u32* __restrict__ n_dev, u32* partials) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ u32 sw[33];
     if (n_dev) n = min(n, *n_dev);
     const u32 base = blockIdx.x * SCAN_TILE;
@@ -60,6 +62,8 @@ __global__ void k_scan_reduce(const u32* __restrict__ in, u32 n, const u32* __re
 // writes the total. Two launches per scan, no waiting between blocks.
 __global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u32 n, const u32* __restrict__ n_dev,
                             const u32* __restrict__ partials, u32 nb, u32* __restrict__ total_out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ u32 sw[33];
     __shared__ u32 s_off;
     if (n_dev) n = min(n, *n_dev);
@@ -96,6 +100,8 @@ constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
 constexpr int RS_BINS = 256;
 
 __global__ void k_radix_hist(const u32* __restrict__ keys, u32 n, int shift, u32* __restrict__ hist, u32 nblk) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ u32 h[RS_BINS];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -114,6 +120,8 @@ __global__ void k_radix_hist(const u32* __restrict__ keys, u32 n, int shift, u32
 __global__ void k_radix_scatter(const u32* __restrict__ keys, const u32* __restrict__ vals, u32 n, int shift,
                                 const u32* __restrict__ offs, u32 nblk, u32* __restrict__ keys_out,
                                 u32* __restrict__ vals_out) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ u32 wcnt[RS_THREADS / 32][RS_BINS];
     __shared__ u32 running[RS_BINS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
