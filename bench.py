@@ -237,7 +237,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    step_ms, results = [], []
+    step_ms, results, ests = [], [], {args.warmup: est}
     launches_in_steps = 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_wall0 = time.perf_counter()
@@ -253,8 +253,13 @@ def run_ours(args):
                 launches_in_steps += far.launch_count() - l0
                 step_ms.append(ev0.elapsed_time(ev1))
                 results.append(res)
+                ests[t] = est
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
+    rpe = []     # per-frame relative pose error of the estimates against the true motion
+    for t in range(1 + args.warmup, n_total):
+        D = np.linalg.inv(np.linalg.inv(veh.pose(t - 1)) @ veh.pose(t)) @ (np.linalg.inv(ests[t - 1]) @ ests[t])
+        rpe.append((float(np.linalg.norm(D[:3, 3])), rot_angle(D[:3, :3])))
 
     # ---- profiled pass over the same scans (stage times, per-launch k_gn_lin durations for the
     # roofline): the library records CUDA events between its kernels on the map's stream
@@ -354,7 +359,7 @@ def run_ours(args):
     if rank == 0 and n_acc > 0:
         accuracy = precision_accuracy(n_acc, stream)
 
-    n_iter = np.mean([r["iters"] for r in results])
+    n_iter = np.mean([r["reg"]["iters"] if "reg" in r else r["iters"] for r in results])
     st_mean = {k_: round(v_ / args.steps, 4) for k_, v_ in stage_acc.items()}
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -370,6 +375,9 @@ def run_ours(args):
         "gn_iters_mean": round(float(n_iter), 3),
         "points_per_scan": round(pts / args.steps),
         "n_src_mean": round(float(np.mean([r["n_src"] for r in results]))),
+        "relative_pose_error_per_frame": {"median_trans_m": round(float(np.median([e[0] for e in rpe])), 5),
+                                          "max_trans_m": round(float(np.max([e[0] for e in rpe])), 5),
+                                          "median_rot_rad": round(float(np.median([e[1] for e in rpe])), 7)},
         "map_points_end": int(results[-1]["n_points"]),
         "roofline": roofline,
         "cpu_baseline": cpu,

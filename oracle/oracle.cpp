@@ -990,8 +990,13 @@ int om_register(const OracleMap* m, const float* xyz, int64_t n, const double* i
         cholesky6_solve(Lc, mg, xi);
         apply_update(xi, A, T);  // Eq. 6: the increment is applied on the left, about the anchor
         st->iters = it + 1;
-        double nx = 0;
-        for (int i = 0; i < 6; ++i) nx += xi[i] * xi[i];
+        // termination reading: ||[phi; rho + phi x c]|| <= conv_eps, the increment expressed at the
+        // initial sensor position c (relative to the anchor), i.e. in the frame of the LiDAR whose
+        // transform the test is about, not at the world origin
+        double c[3] = {init[3] - A[0], init[7] - A[1], init[11] - A[2]};
+        double r[3] = {xi[3] + (xi[1] * c[2] - xi[2] * c[1]), xi[4] + (xi[2] * c[0] - xi[0] * c[2]),
+                       xi[5] + (xi[0] * c[1] - xi[1] * c[0])};
+        double nx = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] + r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
         if (std::sqrt(nx) <= prm->conv_eps) { st->converged = 1; break; }
     }
     std::memcpy(out_pose, T, sizeof(T));

@@ -372,6 +372,7 @@ GnArgs gn_args(far_map* m, const double* pose, u32 n, float tau, float kappa, do
             a.ftile[j] = (int)T;
             a.anchor[j] = 50.0 * T;
         }
+        a.conv_center[j] = pose[4 * j + 3] - a.anchor[j];
     }
     a.src_h4 = m->s.src_h4;
     a.src_h2 = m->s.src_h2;

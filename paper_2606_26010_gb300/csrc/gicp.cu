@@ -493,12 +493,16 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
                 st->T[4 * r + 3] =
                     (E[4 * r + 0] * tr[0] + E[4 * r + 1] * tr[1] + E[4 * r + 2] * tr[2] + E[4 * r + 3]) + a.anchor[r];
             }
-            double nx = 0.0;
+            // termination: the increment expressed at the initial sensor position c (relative to
+            // the anchor), [phi; rho + phi x c], so the test does not depend on where the world
+            // origin lies
+            const double* c = a.conv_center;
+            const double r0 = xi[3] + (xi[1] * c[2] - xi[2] * c[1]);
+            const double r1 = xi[4] + (xi[2] * c[0] - xi[0] * c[2]);
+            const double r2 = xi[5] + (xi[0] * c[1] - xi[1] * c[0]);
+            const double nx = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] + r0 * r0 + r1 * r1 + r2 * r2;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                st->xi[j] = xi[j];
-                nx += xi[j] * xi[j];
-            }
+            for (int j = 0; j < 6; ++j) st->xi[j] = xi[j];
             st->xi_norm2 = nx;
             st->iters += 1;
             if (nx <= a.conv_eps * a.conv_eps) {

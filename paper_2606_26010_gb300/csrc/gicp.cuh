@@ -26,6 +26,9 @@ struct GnArgs {
     // with ftile that tile (the search frame of the iteration).
     double anchor[3];
     int ftile[3];
+    // initial sensor position relative to the anchor: the termination test measures the
+    // increment there (see the solve)
+    double conv_center[3];
     // precision variant source covariances (FP16 with the scan-local voxel's exponent)
     const uint2* src_h4;
     const u32* src_h2;

@@ -654,3 +654,25 @@ def test_prec_stage_queries_use_the_query_tile_frame():
         j = int(np.argmin(dd))
         if dd[j] < 0.25 and np.sort(dd)[1] - dd[j] > 1e-4:
             assert ids[i] == j
+
+
+def test_termination_measures_the_increment_at_the_sensor():
+    """Termination reading: ||[phi; rho + phi x c]|| <= conv_eps with c the initial sensor position.
+    Moving the whole problem ~100 km (precision variant, exact translation equivariance) changes
+    neither the number of iterations nor the result; an origin-based test would stop later
+    far from the origin (rho picks up phi x t)."""
+    p = _problem_points(4)
+    D = np.array([50.0 * 2003, -50.0 * 611, 50.0 * 3])
+    shift = synth.make_pose(np.eye(3), D)
+    out = []
+    for S in (np.eye(4), shift):
+        m = oracle.OracleMap(0.5, 20, 5, precision_mode=1)
+        for s, T in zip(p.map_scans, p.map_poses):
+            m.insert(s, S @ T)
+        P, _, st = m.register(p.query, S @ p.init, max_iters=30, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+        out.append((P, st))
+    (P0, s0), (P1, s1) = out
+    assert s0["converged"] == s1["converged"] == 1
+    assert s0["iters"] == s1["iters"] < 30
+    D01 = np.linalg.inv(shift @ P0) @ P1
+    assert np.linalg.norm(D01[:3, 3]) < 1e-7
