@@ -93,6 +93,10 @@ struct far_map {
     u32 gn_launched = 0;
     far_stage_times last{};
     GnArgs last_gn{};                // arguments of the last registration (footprint diagnostics)
+    GnArgs* d_args = nullptr;        // device copy of the registration arguments (graph loop)
+    GnArgs* h_args = nullptr;        // pinned staging of d_args
+    std::vector<GnGraph> gn_graphs;  // instantiated Gauss-Newton loops (grid, lanes, precision)
+    bool gn_graph_used = false;      // the last registration ran the graph loop
 };
 
 namespace {
@@ -185,6 +189,7 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     add((void**)&t->s.i64_out, n * sizeof(int64_t));
     add((void**)&t->s.gn_partials, gn_partials_doubles(pl.max_n) * sizeof(double));
     add((void**)&t->s.st, sizeof(RegState));
+    add((void**)&t->d_args, sizeof(GnArgs));
     add((void**)&t->d_cov36, 36 * sizeof(double));
     add((void**)&t->s.touched, (size_t)pl.cap * sizeof(u32));
     add((void**)&t->s.foot, 2 * sizeof(unsigned long long));
@@ -208,6 +213,10 @@ void release(far_map* m) {
     m->ev.clear();
     for (void* p : m->allocs) cudaFree(p);
     m->allocs.clear();
+    for (GnGraph& g : m->gn_graphs) gn_graph_destroy(&g);
+    m->gn_graphs.clear();
+    if (m->h_args) cudaFreeHost(m->h_args);
+    m->h_args = nullptr;
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
     if (m->h_st) cudaFreeHost(m->h_st);
     if (m->h_scal) cudaFreeHost(m->h_scal);
@@ -327,10 +336,40 @@ void collect_times(far_map* m, u32 iters_done, u32 status) {
     m->last = t;
 }
 
-// Launch the Gauss-Newton chain (max_iters iterations of linearise + solve), marking the
-// start, the end of each linearisation and the end of each solve when profiling.
+// Launch the Gauss-Newton chain (max_iters iterations of linearise + solve). When the loop
+// can stop early (conv_eps > 0, or a time budget) and nothing is profiled, it is one launch
+// of an instantiated graph whose device-side loop ends at convergence, so no launch follows
+// it; a fixed iteration count runs as explicit launches, whose programmatic dependent
+// launches overlap better than graph nodes; with profiling, explicit launches marked by
+// events (start, the end of each linearisation, the end of each solve).
 far_status run_gn(far_map* m, const GnArgs& a, u32 n_upper, u32 iters) {
     m->last_gn = a;
+    if (!m->profiling && iters > 0 && (a.conv_eps > 0.0 || a.budget_ns > 0)) {
+        const bool prec = a.map.tv > 0;
+        const u32 grid = gn_grid(n_upper, a.tpp);
+        GnGraph* g = nullptr;
+        for (GnGraph& c : m->gn_graphs)
+            if (c.grid == grid && c.tpp == gn_tpp(a.tpp) && c.prec == prec) g = &c;
+        if (!g) {
+            if (m->gn_graphs.size() >= 8) {
+                gn_graph_destroy(&m->gn_graphs.front());
+                m->gn_graphs.erase(m->gn_graphs.begin());
+            }
+            GnGraph ng;
+            CK(gn_graph_build(m->d_args, n_upper, a.tpp, prec, &ng));
+            m->gn_graphs.push_back(ng);
+            g = &m->gn_graphs.back();
+        }
+        // the previous registration's copy has completed: every call ends with a stream sync
+        *m->h_args = a;
+        m->h_args->max_iters = iters;
+        CK(cudaMemcpyAsync(m->d_args, m->h_args, sizeof(GnArgs), cudaMemcpyHostToDevice, m->stream));
+        CK(cudaGraphLaunch(g->exec, m->stream));
+        m->gn_graph_used = true;
+        m->gn_launched = 0;
+        return FAR_OK;
+    }
+    m->gn_graph_used = false;
     mark(m, EV_GN0);
     for (u32 it = 0; it < iters; ++it) {
         u32 nb = 0;
@@ -341,6 +380,15 @@ far_status run_gn(far_map* m, const GnArgs& a, u32 n_upper, u32 iters) {
     }
     m->gn_launched = iters;
     return FAR_OK;
+}
+
+// Count the kernels the graph loop ran (one linearisation and one solve per trip: every
+// trip applies an update, except a final degenerate one).
+void account_gn_graph(far_map* m, const RegState& r) {
+    if (!m->gn_graph_used) return;
+    const u32 trips = r.iters + (r.status == 5 ? 1u : 0u);
+    for (u32 i = 0; i < 2 * trips; ++i) note_launch();
+    m->gn_graph_used = false;
 }
 
 Pose12 pose12(const double* T) {
@@ -364,6 +412,7 @@ GnArgs gn_args(far_map* m, const double* pose, u32 n, float tau, float kappa, do
                int32_t* corr, double budget_s, int tpp = 0) {
     GnArgs a;
     a.tpp = tpp;
+    a.max_iters = 0;
     for (int j = 0; j < 3; ++j) {
         a.anchor[j] = 0.0;
         a.ftile[j] = 0;
@@ -452,7 +501,8 @@ far_status far_map_create(const far_map_params* params, void* cuda_stream, far_m
     if (cudaMallocHost((void**)&m->h_ctr, sizeof(MapCounters)) != cudaSuccess ||
         cudaMallocHost((void**)&m->h_st, sizeof(RegState)) != cudaSuccess ||
         cudaMallocHost((void**)&m->h_scal, SCAL_COUNT * sizeof(u32)) != cudaSuccess ||
-        cudaMallocHost((void**)&m->h_cov36, 36 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost((void**)&m->h_cov36, 36 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_args, sizeof(GnArgs)) != cudaSuccess) {
         cudaGetLastError();
         release(m);
         delete m;
@@ -792,6 +842,7 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
     if (out_cov) CK(cudaMemcpyAsync(map->h_cov36, map->d_cov36, 36 * sizeof(double), cudaMemcpyDeviceToHost, map->stream));
     CK(cudaStreamSynchronize(map->stream));
     const RegState& r = *map->h_st;
+    account_gn_graph(map, r);
     collect_times(map, r.iters, r.status);
     std::memcpy(out_pose, r.T, 16 * sizeof(double));
     if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));
@@ -864,6 +915,7 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
         CK(cudaStreamSynchronize(map->stream));
     }
     const RegState& r = *map->h_st;
+    account_gn_graph(map, r);
     collect_times(map, r.iters, r.status);
     std::memcpy(out_pose, r.T, 16 * sizeof(double));
     if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));

@@ -545,6 +545,27 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_batch(const BatchPro
     gn_solve_block(p.args, p.nblocks);
 }
 
+// Kernels of the graph loop: the arguments come from device memory.
+template <int TPP, bool PREC>
+__global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_dev(const GnArgs* __restrict__ ap) {
+    pdl_wait();
+    pdl_trigger();
+    gn_lin_block<TPP, PREC>(*ap, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_dev(const GnArgs* __restrict__ ap, u32 nblocks,
+                                                                cudaGraphConditionalHandle loop) {
+    pdl_wait();
+    pdl_trigger();
+    gn_solve_block(*ap, nblocks);
+    if (threadIdx.x == 0) {
+        const RegState* st = ap->st;
+        const bool stop = *reinterpret_cast<const volatile u32*>(&st->done) != 0u ||
+                          *reinterpret_cast<const volatile u32*>(&st->iters) >= ap->max_iters;
+        cudaGraphSetConditional(loop, stop ? 0u : 1u);
+    }
+}
+
 // Reset every problem's state to its initial pose (init: 16 doubles per problem).
 __global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 nprob, const double* __restrict__ init) {
     pdl_wait();
@@ -809,6 +830,68 @@ cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s) {
     cudaError_t e = gn_linearise(a, n_upper, s, &nb);
     if (e != cudaSuccess) return e;
     return gn_solve(a, nb, s);
+}
+
+namespace {
+void* lin_dev_fn(int tpp, bool prec) {
+    switch (gn_tpp(tpp)) {
+        case 4: return prec ? (void*)k_gn_lin_dev<4, true> : (void*)k_gn_lin_dev<4, false>;
+        case 8: return prec ? (void*)k_gn_lin_dev<8, true> : (void*)k_gn_lin_dev<8, false>;
+        case 32: return prec ? (void*)k_gn_lin_dev<32, true> : (void*)k_gn_lin_dev<32, false>;
+        default: return prec ? (void*)k_gn_lin_dev<1, true> : (void*)k_gn_lin_dev<1, false>;
+    }
+}
+}  // namespace
+
+cudaError_t gn_graph_build(const GnArgs* d_args, u32 n_upper, int tpp, bool prec, GnGraph* out) {
+    u32 grid = gn_grid(n_upper, tpp);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle loop;
+    e = cudaGraphConditionalHandleCreate(&loop, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+    }
+    cudaGraphNode_t lin = nullptr, solve = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const GnArgs* ap = d_args;
+        void* largs[] = {(void*)&ap};
+        cudaKernelNodeParams lp = {};
+        lp.func = lin_dev_fn(tpp, prec);
+        lp.gridDim = dim3(grid);
+        lp.blockDim = dim3(GN_THREADS);
+        lp.kernelParams = largs;
+        e = cudaGraphAddKernelNode(&lin, body, nullptr, 0, &lp);
+        void* sargs[] = {(void*)&ap, (void*)&grid, (void*)&loop};
+        cudaKernelNodeParams sp = {};
+        sp.func = (void*)k_gn_solve_dev;
+        sp.gridDim = dim3(1);
+        sp.blockDim = dim3(SOLVE_THREADS);
+        sp.kernelParams = sargs;
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&solve, body, &lin, 1, &sp);
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    out->exec = exec;
+    out->grid = grid;
+    out->tpp = gn_tpp(tpp);
+    out->prec = prec;
+    return cudaSuccess;
+}
+
+void gn_graph_destroy(GnGraph* g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
 }
 
 }  // namespace far

@@ -33,6 +33,7 @@ struct GnArgs {
     const uint2* src_h4;
     const u32* src_h2;
     const signed char* src_exp;
+    u32 max_iters;               // updates at most (device-side loop of gn_graph)
 };
 
 // One problem of a batched registration: its arguments and its share of the shared grid.
@@ -63,6 +64,20 @@ cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cuda
 cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s);
 cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks);
 cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s);
+// The Gauss-Newton loop as a CUDA graph with a device-side while loop (conditional node): the
+// body is one linearisation and one solve, and the solve ends the loop once the state is done
+// or max_iters updates were applied, so no launch follows convergence. Both kernels read the
+// arguments from d_args (device memory), so one instantiated graph serves every registration
+// with the same grid, lanes per point and precision mode.
+struct GnGraph {
+    cudaGraphExec_t exec = nullptr;
+    u32 grid = 0;
+    int tpp = -1;
+    bool prec = false;
+};
+cudaError_t gn_graph_build(const GnArgs* d_args, u32 n_upper, int tpp, bool prec, GnGraph* out);
+void gn_graph_destroy(GnGraph* g);
+
 // Distinct map voxels (out2[0]) and their points (out2[1]) probed by the source points at st->T
 // (searched in the frame of a.anchor / a.ftile as the linearisation does).
 cudaError_t gn_footprint(const GnArgs& a, u32* touched, u32 cap, unsigned long long* out2, u32 n_upper,
