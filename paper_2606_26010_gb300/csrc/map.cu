@@ -375,6 +375,9 @@ __global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal
     ctr->n_added = t;
 }
 
+// Lanes cooperating on one k-NN query (group_knn); every grid-stride step is warp-uniform.
+constexpr int KNN_TPP = 4;
+
 // Eq. 1 covariances of query points against map m. Queries are either q[r]
 // (q != null) or m.pts[qpos[r]]; output index is out_pos[r] (map points) or r.
 // With knn_ids, the output row of a query is its rank, taken from q[r].w.
@@ -387,11 +390,20 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
     pdl_trigger();
     const u32 nn = n_dev ? min(n, *n_dev) : n;
     const u32 max_probe = m.ctr->max_probe;
-    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
-        const float4 p = q ? q[r] : m.pts[qpos[r]];
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = threadIdx.x % KNN_TPP;
+    const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
+    const int zero[3] = {0, 0, 0};
+    for (u32 base = (t & ~31u) / KNN_TPP; base < nn; base += stride) {   // warp-uniform trip count
+        const u32 r = base + (threadIdx.x & 31u) / KNN_TPP;
+        const bool active = r < nn;
+        const float4 p = active ? (q ? q[r] : m.pts[qpos[r]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        QFrame<false> f;
+        const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
+        const int found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, bd, bid, bpos);
+        if (!active || sl != 0) continue;
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (found >= K) covariance_from_neighbours<K>(m.pts, bpos, p.x, p.y, p.z, c0, c1);
         const u32 o = out_pos ? out_pos[r] : r;
@@ -417,17 +429,22 @@ __global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __re
     pdl_trigger();
     const u32 nn = min(n, *n_dev);
     const u32 max_probe = m.ctr->max_probe;
-    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += gridDim.x * blockDim.x) {
-        const u32 pos = qpos[r];
-        const float4 p = m.pts[pos];
-        int kx, ky, kz;
-        unpack_key(qkey[r], kx, ky, kz);
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = threadIdx.x % KNN_TPP;
+    const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
+    for (u32 base = (t & ~31u) / KNN_TPP; base < nn; base += stride) {   // warp-uniform trip count
+        const u32 r = base + (threadIdx.x & 31u) / KNN_TPP;
+        const bool active = r < nn;
+        const u32 pos = active ? qpos[r] : 0u;
+        const float4 p = active ? m.pts[pos] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int kx = 0, ky = 0, kz = 0;
+        if (active) unpack_key(qkey[r], kx, ky, kz);
         QFrame<true> f;
         own_qframe(m, p.x, p.y, p.z, kx, ky, kz, f);
         float bd[K];
         u32 bid[K], bpos[K];
-        knn_init<K>(bd, bid, bpos);
-        const int found = knn27q<K, true>(m, max_probe, f, bd, bid, bpos);
+        const int found = group_knn<K, KNN_TPP, true>(m, max_probe, f, active, sl, bd, bid, bpos);
+        if (!active || sl != 0) continue;
         float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool valid = false;
         if (found >= K) {
@@ -690,18 +707,27 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
     pdl_wait();
     pdl_trigger();
     const u32 max_probe = m.ctr->max_probe;
-    for (u32 r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const float4 p = q[r];
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = threadIdx.x % KNN_TPP;
+    const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
+    const int zero[3] = {0, 0, 0};
+    for (u32 base = (t & ~31u) / KNN_TPP; base < n; base += stride) {   // warp-uniform trip count
+        const u32 r = base + (threadIdx.x & 31u) / KNN_TPP;
+        const bool active = r < n;
+        const float4 p = active ? q[r] : make_float4(0.f, 0.f, 0.f, 0.f);
         float bd[K];
         u32 bid[K], bpos[K];
         int found;
         if (m.tv > 0) {
-            knn_init<K>(bd, bid, bpos);
             QFrame<true> f;
-            found = world_query_frame(m, p.x, p.y, p.z, f) ? knn27q<K, true>(m, max_probe, f, bd, bid, bpos) : 0;
+            const bool keyed = active && world_query_frame(m, p.x, p.y, p.z, f);
+            found = group_knn<K, KNN_TPP, true>(m, max_probe, f, keyed, sl, bd, bid, bpos);
         } else {
-            found = knn27<K>(m, max_probe, p.x, p.y, p.z, bd, bid, bpos);
+            QFrame<false> f;
+            const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
+            found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, bd, bid, bpos);
         }
+        if (!active || sl != 0) continue;
         found_out[r] = found;
 #pragma unroll
         for (int j = 0; j < K; ++j) ids[(size_t)r * K + j] = (j < found) ? bid[j] : NO_ID;
@@ -730,17 +756,20 @@ __global__ void __launch_bounds__(TPB) k_nearest_stage(MapView m, const float4* 
     }
 }
 
+// Grid of the k-NN kernels: KNN_TPP lanes per query, at most 16 blocks per SM (grid-stride).
+inline u32 knn_blocks(u32 n) { return min(blocks_for(n * KNN_TPP), 152u * 16u); }
+
 template <int K>
 cudaError_t launch_knn_cov(const DeviceMap& m, const float4* q, const u32* qpos, u32 n, const u32* n_dev,
                            float4* cov_out, const u32* out_pos, u32* knn_ids, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_knn_cov<K>, blocks_for(n), TPB, 0, st, m.view(), q, qpos, n, n_dev, cov_out, out_pos, knn_ids);
+    FAR_LAUNCH(k_knn_cov<K>, knn_blocks(n), TPB, 0, st, m.view(), q, qpos, n, n_dev, cov_out, out_pos, knn_ids);
     return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t launch_knn_stage(const DeviceMap& m, const float4* q, u32 n, u32* ids, int32_t* found, cudaStream_t st) {
-    FAR_LAUNCH(k_knn_stage<K>, blocks_for(n), TPB, 0, st, m.view(), q, n, ids, found);
+    FAR_LAUNCH(k_knn_stage<K>, knn_blocks(n), TPB, 0, st, m.view(), q, n, ids, found);
     return cudaGetLastError();
 }
 
@@ -776,7 +805,7 @@ template <int K>
 cudaError_t launch_knn_cov_tile(const DeviceMap& m, const u32* qpos, const u64* qkey, u32 n, const u32* n_dev,
                                 float4* cov_tmp, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_knn_cov_tile<K>, blocks_for(n), TPB, 0, st, m.view(), qpos, qkey, n, n_dev, cov_tmp, m.cexp);
+    FAR_LAUNCH(k_knn_cov_tile<K>, knn_blocks(n), TPB, 0, st, m.view(), qpos, qkey, n, n_dev, cov_tmp, m.cexp);
     return cudaGetLastError();
 }
 

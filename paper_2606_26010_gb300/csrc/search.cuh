@@ -243,6 +243,73 @@ __device__ __forceinline__ void knn_init(float (&bd)[K], u32 (&bid)[K], u32 (&bp
     }
 }
 
+// Insert (d2, id, pos) into the sorted K best (the candidate bubbles past every worse entry;
+// registers only).
+template <int K>
+__device__ __forceinline__ void knn_insert(float d2, u32 id, u32 pos, float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+    if (!better(d2, id, bd[K - 1], bid[K - 1])) return;
+    float cd = d2;
+    u32 ci = id, cp = pos;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const bool sw = better(cd, ci, bd[s], bid[s]);
+        const float td = bd[s];
+        const u32 ti = bid[s], tp = bpos[s];
+        bd[s] = sw ? cd : td;
+        bid[s] = sw ? ci : ti;
+        bpos[s] = sw ? cp : tp;
+        cd = sw ? td : cd;
+        ci = sw ? ti : ci;
+        cp = sw ? tp : cp;
+    }
+}
+
+// K nearest of the query searched by a group of TPP consecutive lanes: lane sl scans the
+// voxels round * TPP + sl of the order own, faces, edges, corners into its own sorted K
+// best; after each round the group shares the smallest K-th distance of any lane (the K best
+// of the union are at least that close) and a voxel whose box distance exceeds it is
+// skipped. The lanes' lists are then merged pairwise, so every lane of the group ends with
+// the K best of the union in (d2, id) order (the lanes saw disjoint voxels). Returns the
+// number of candidates the group saw, capped at K. Every lane of the warp must call this.
+template <int K, int TPP, bool PREC>
+__device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
+                                         int sl, float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+    knn_init<K>(bd, bid, bpos);
+    int found = 0;
+    const FaceDist fd = face_distances(f.q[0], f.q[1], f.q[2], f.lk[0], f.lk[1], f.lk[2], m.v);
+    float bound = F_INF;
+    constexpr int kRounds = (27 + TPP - 1) / TPP;
+    for (int round = 0; round < kRounds; ++round) {
+        const int v = round * TPP + sl;
+        if (keyed && v < 27) {
+            const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
+            const int nx = f.k[0] + dx, ny = f.k[1] + dy, nz = f.k[2] + dz;
+            if (key_in_range(nx) && key_in_range(ny) && key_in_range(nz) && !(box_lb2(fd, dx, dy, dz) > bound))
+                knn_scan_voxel<K, PREC>(m, max_probe, nx, ny, nz, f.q[0], f.q[1], f.q[2], found, bd, bid, bpos,
+                                        f.off(0, dx), f.off(1, dy), f.off(2, dz));
+        }
+        float kth = bd[K - 1];
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1) kth = fminf(kth, __shfl_xor_sync(0xffffffffu, kth, o));
+        bound = kth;
+    }
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        found += __shfl_xor_sync(0xffffffffu, found, o);
+        float od[K];
+        u32 oi[K], op[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            od[j] = __shfl_xor_sync(0xffffffffu, bd[j], o);
+            oi[j] = __shfl_xor_sync(0xffffffffu, bid[j], o);
+            op[j] = __shfl_xor_sync(0xffffffffu, bpos[j], o);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) knn_insert<K>(od[j], oi[j], op[j], bd, bid, bpos);
+    }
+    return found < K ? found : K;
+}
+
 // K nearest of a world-coordinate query of a plain map.
 template <int K>
 __device__ __forceinline__ int knn27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
