@@ -34,11 +34,20 @@ __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* 
 // Precision variant (tv > 0): x_w stays FP64, the key follows the tile reading and `world`
 // receives the coordinates relative to the tile origin.
 __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
-                             float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys) {
+                             float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys,
+                             u32* __restrict__ scal, MapCounters* ctr, u32* __restrict__ admitted) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the insert's first kernel clears its per-insert state (scalars, ASMD sums, admitted flags)
+    if (i < SCAL_COUNT) scal[i] = 0u;
+    if (i == 0) {
+        ctr->near_sum = 0ull;
+        ctr->near_cnt = 0ull;
+        ctr->n_added = 0u;
+    }
     if (i >= n) return;
+    admitted[i] = 0u;
     if (dp.T) {
 #pragma unroll
         for (int j = 0; j < 12; ++j) T.m[j] = dp.T[j];
@@ -129,7 +138,7 @@ __global__ void k_group_heads(const u32* __restrict__ sk, u32 n, u32 sentinel, u
     flags[i] = (k != sentinel && (i == 0 || sk[i - 1] != k)) ? 1u : 0u;
 }
 
-__global__ void k_group_starts(const u32* __restrict__ sk, const u32* __restrict__ flags,
+__global__ void k_group_starts(const u32* __restrict__ sk, u32* __restrict__ flags,
                                const u32* __restrict__ gidx, u32 n, u32 sentinel, u32* __restrict__ gstart,
                                const u32* __restrict__ scal) {
     pdl_wait();
@@ -137,6 +146,7 @@ __global__ void k_group_starts(const u32* __restrict__ sk, const u32* __restrict
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (flags[i]) gstart[gidx[i]] = i;
+    flags[i] = 0u;   // cleared for the head marks that follow (each thread reads only its own)
     const u32 k = sk[i];
     if (k != sentinel && (i + 1 == n || sk[i + 1] == sentinel)) gstart[scal[SCAL_NGROUPS]] = i + 1;
 }
@@ -831,16 +841,18 @@ cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStr
 
 cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
                              bool covariances, cudaStream_t st, DevicePose dpose) {
-    FAR_TRY(cudaMemsetAsync(s.scal, 0, SCAL_COUNT * sizeof(u32), st));
-    // zero the per-insert counters (near_sum, near_cnt, n_added)
-    FAR_TRY(cudaMemsetAsync(&m.ctr->near_sum, 0, 2 * sizeof(unsigned long long), st));
-    FAR_TRY(cudaMemsetAsync(&m.ctr->n_added, 0, sizeof(u32), st));
-    if (n == 0) return cudaSuccess;
+    if (n == 0) {
+        // zero the per-insert scalars and counters (near_sum, near_cnt, n_added)
+        FAR_TRY(cudaMemsetAsync(s.scal, 0, SCAL_COUNT * sizeof(u32), st));
+        FAR_TRY(cudaMemsetAsync(&m.ctr->near_sum, 0, 2 * sizeof(unsigned long long), st));
+        FAR_TRY(cudaMemsetAsync(&m.ctr->n_added, 0, sizeof(u32), st));
+        return cudaSuccess;
+    }
     const u32 sentinel = m.cap;
     Pose12 T{};
     if (pose) T = *pose;
     FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
-                                                m.inv_v, m.tv, s.world, s.keys);
+               m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted);
     FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr);
     bool alt = false;
     FAR_TRY(radix_sort_pairs(s.sk, s.sv, s.sk_alt, s.sv_alt, n, m.key_bits, s.hist, s.partials, st, &alt));
@@ -852,9 +864,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     if (cfg.asmd)
         FAR_LAUNCH(k_asmd_near, blocks_for(n), TPB, 0, st, s.gstart, s.scal, sk, m.slots, (double)m.v, cfg, dpose.T,
                                                    m.ctr);
-    FAR_TRY(cudaMemsetAsync(s.admitted, 0, (size_t)n * sizeof(u32), st));
-    // voxel ordinals in first-input-index order
-    FAR_TRY(cudaMemsetAsync(s.flags, 0, (size_t)n * sizeof(u32), st));
+    // voxel ordinals in first-input-index order (flags were cleared by k_group_starts)
     FAR_LAUNCH(k_mark_heads, blocks_for(n), TPB, 0, st, s.gstart, sv, s.scal, s.flags);
     FAR_TRY(scan_exclusive(s.flags, s.head_ord, n, nullptr, nullptr, s.partials, st));
     AdmitArgs a;
