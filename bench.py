@@ -263,7 +263,7 @@ def run_ours(args):
 
     # ---- profiled pass over the same scans (stage times, per-launch k_gn_lin durations for the
     # roofline): the library records CUDA events between its kernels on the map's stream
-    gn_ms, gn_bytes, gn_launches, stage_acc = [], [], [], {}
+    gn_ms, gn_bytes, gn_launches, stage_acc, ins_acc = [], [], [], {}, {}
     mp = make_map()
     mp.set_profiling(True)
     thr_p = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
@@ -278,6 +278,9 @@ def run_ours(args):
             st = mp.stage_times()
             for k_, v_ in st.items():
                 stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
+            for w_, parts in mp.insert_times().items():
+                for k_, v_ in parts.items():
+                    ins_acc.setdefault(w_, {})[k_] = ins_acc.get(w_, {}).get(k_, 0.0) + v_
             n_src, u_v, p_touched = mp.gn_footprint()
             nblk = min((scans[t].shape[0] * 4 + 127) // 128, 152 * 5)
             # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B; 12 + 12 + 1
@@ -372,6 +375,7 @@ def run_ours(args):
                        "p99": round(float(np.percentile(lat, 99)), 4),
                        "max": round(float(lat.max()), 4), "mean": round(float(lat.mean()), 4)},
         "stages_ms_mean": st_mean,
+        "insert_parts_ms_mean": {w_: {k_: round(v_ / args.steps, 4) for k_, v_ in d_.items()} for w_, d_ in ins_acc.items()},
         "gn_iters_mean": round(float(n_iter), 3),
         "points_per_scan": round(pts / args.steps),
         "n_src_mean": round(float(np.mean([r["n_src"] for r in results]))),

@@ -310,6 +310,18 @@ far_status far_set_profiling(far_map* map, int enable);
 far_status far_get_stage_times(const far_map* map, far_stage_times* out);
 
 /*
+ * Parts of the two inserts of the last profiled scan (milliseconds, CUDA events on the
+ * map's stream): out[0] the scan-local map that yields the sources (cov_ms: their Eq. 1
+ * covariances), out[1] the insert into the map (cov_ms: covariances of the added points).
+ * keys: transform, keys and hash slots; sort: grouping by slot; group: group bounds, ASMD
+ * and voxel order; admit: capped spaced admission; ids: ids and the grouped order.
+ */
+typedef struct far_insert_times {
+    double keys_ms, sort_ms, group_ms, admit_ms, ids_ms, cov_ms;
+} far_insert_times;
+far_status far_get_insert_times(const far_map* map, far_insert_times out[2]);
+
+/*
  * Footprint of one Gauss-Newton launch at the last registration's final pose:
  * out[0] = source points, out[1] = distinct map voxels probed by their
  * 27-neighbourhoods, out[2] = points held by those voxels. Diagnostic only.

@@ -97,6 +97,12 @@ struct far_map {
     GnArgs* h_args = nullptr;        // pinned staging of d_args
     std::vector<GnGraph> gn_graphs;  // instantiated Gauss-Newton loops (grid, lanes, precision)
     bool gn_graph_used = false;      // the last registration ran the graph loop
+    // profiling of the two inserts of a scan: [0] the scan-local map (sources), [1] the map
+    InsertMarks ins_marks[2] = {};
+    cudaEvent_t ins_start[2] = {nullptr, nullptr};
+    cudaEvent_t src_end = nullptr;
+    bool ins_used[2] = {false, false};
+    far_insert_times ins_last[2] = {};
 };
 
 namespace {
@@ -211,6 +217,12 @@ void release(far_map* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     m->ev.clear();
+    for (int w = 0; w < 2; ++w) {
+        if (m->ins_start[w]) cudaEventDestroy(m->ins_start[w]);
+        for (cudaEvent_t e : m->ins_marks[w].ev)
+            if (e) cudaEventDestroy(e);
+    }
+    if (m->src_end) cudaEventDestroy(m->src_end);
     for (void* p : m->allocs) cudaFree(p);
     m->allocs.clear();
     for (GnGraph& g : m->gn_graphs) gn_graph_destroy(&g);
@@ -296,6 +308,34 @@ void mark(far_map* m, int e) {
 void reset_marks(far_map* m) {
     for (bool& u : m->ev_used) u = false;
     m->gn_launched = 0;
+    m->ins_used[0] = m->ins_used[1] = false;
+}
+
+// Events around one insert (profiling only); which = 0 scan-local map, 1 registration map.
+const InsertMarks* insert_marks(far_map* m, int which) {
+    if (!m->profiling) return nullptr;
+    cudaEventRecord(m->ins_start[which], m->stream);
+    m->ins_used[which] = true;
+    return &m->ins_marks[which];
+}
+
+void collect_insert_times(far_map* m) {
+    for (int w = 0; w < 2; ++w) {
+        if (!m->ins_used[w]) continue;
+        const InsertMarks& k = m->ins_marks[w];
+        float t[6] = {0, 0, 0, 0, 0, 0};
+        cudaEventElapsedTime(&t[0], m->ins_start[w], k.ev[0]);
+        for (int i = 1; i < 5; ++i) cudaEventElapsedTime(&t[i], k.ev[i - 1], k.ev[i]);
+        // the sources' covariances are computed after the local insert (make_sources)
+        cudaEventElapsedTime(&t[5], k.ev[4], w == 0 ? m->src_end : k.ev[5]);
+        far_insert_times& o = m->ins_last[w];
+        o.keys_ms = t[0];
+        o.sort_ms = t[1];
+        o.group_ms = t[2];
+        o.admit_ms = t[3];
+        o.ids_ms = t[4];
+        o.cov_ms = t[5];
+    }
 }
 
 float span_ms(far_map* m, int a, int b) {
@@ -401,8 +441,9 @@ Pose12 pose12(const double* T) {
 far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
     CK(map_clear(m->local, m->stream));
     InsertCfg cfg;
-    CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream));
+    CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream, DevicePose(), insert_marks(m, 0)));
     CK(make_sources(m->local, m->s, n, knn_ids, m->stream));
+    if (m->profiling) cudaEventRecord(m->src_end, m->stream);
     return FAR_OK;
 }
 
@@ -844,6 +885,7 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
     const RegState& r = *map->h_st;
     account_gn_graph(map, r);
     collect_times(map, r.iters, r.status);
+    if (map->profiling) collect_insert_times(map);
     std::memcpy(out_pose, r.T, 16 * sizeof(double));
     if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));
     far_status result = FAR_OK;
@@ -899,7 +941,7 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     DevicePose dp;
     dp.T = map->s.st->T;
     dp.status = &map->s.st->status;
-    CK(map_insert_batch(map->map, map->s, nn, nullptr, cfg, true, map->stream, dp));
+    CK(map_insert_batch(map->map, map->s, nn, nullptr, cfg, true, map->stream, dp, insert_marks(map, 1)));
     mark(map, EV_EVICT);
     if (evict_radius > 0.0 && std::isfinite(evict_radius))
         CK(map_evict(map->map, nullptr, evict_radius, map->stream, map->s.st->T));
@@ -917,6 +959,7 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     const RegState& r = *map->h_st;
     account_gn_graph(map, r);
     collect_times(map, r.iters, r.status);
+    if (map->profiling) collect_insert_times(map);
     std::memcpy(out_pose, r.T, 16 * sizeof(double));
     if (out_cov) std::memcpy(out_cov, map->h_cov36, 36 * sizeof(double));
     far_status res = FAR_OK;
@@ -1327,8 +1370,21 @@ far_status far_set_profiling(far_map* map, int enable) {
     if (enable && map->ev.empty()) {
         map->ev.resize(EV_COUNT_FIXED + 2 * MAX_ITERS + 1, nullptr);
         for (cudaEvent_t& e : map->ev) CK(cudaEventCreate(&e));
+        for (int w = 0; w < 2; ++w) {
+            CK(cudaEventCreate(&map->ins_start[w]));
+            for (cudaEvent_t& e : map->ins_marks[w].ev) CK(cudaEventCreate(&e));
+        }
+        CK(cudaEventCreate(&map->src_end));
     }
     map->profiling = enable != 0;
+    return FAR_OK;
+}
+
+far_status far_get_insert_times(const far_map* map, far_insert_times out[2]) {
+    if (!map || !out) return fail(FAR_ERR_INVALID, "NULL argument");
+    if (!map->profiling) return fail(FAR_ERR_INVALID, "profiling is off (far_set_profiling)");
+    out[0] = map->ins_last[0];
+    out[1] = map->ins_last[1];
     return FAR_OK;
 }
 

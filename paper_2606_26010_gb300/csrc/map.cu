@@ -840,7 +840,10 @@ cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStr
 }
 
 cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
-                             bool covariances, cudaStream_t st, DevicePose dpose) {
+                             bool covariances, cudaStream_t st, DevicePose dpose, const InsertMarks* marks) {
+    auto mark = [&](int i) {
+        if (marks) cudaEventRecord(marks->ev[i], st);
+    };
     if (n == 0) {
         // zero the per-insert scalars and counters (near_sum, near_cnt, n_added)
         FAR_TRY(cudaMemsetAsync(s.scal, 0, SCAL_COUNT * sizeof(u32), st));
@@ -854,8 +857,10 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
                m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted);
     FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr);
+    mark(0);
     bool alt = false;
     FAR_TRY(radix_sort_pairs(s.sk, s.sv, s.sk_alt, s.sv_alt, n, m.key_bits, s.hist, s.partials, st, &alt));
+    mark(1);
     const u32* sk = alt ? s.sk_alt : s.sk;
     const u32* sv = alt ? s.sv_alt : s.sv;
     FAR_LAUNCH(k_group_heads, blocks_for(n), TPB, 0, st, sk, n, sentinel, s.flags);
@@ -867,6 +872,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     // voxel ordinals in first-input-index order (flags were cleared by k_group_starts)
     FAR_LAUNCH(k_mark_heads, blocks_for(n), TPB, 0, st, s.gstart, sv, s.scal, s.flags);
     FAR_TRY(scan_exclusive(s.flags, s.head_ord, n, nullptr, nullptr, s.partials, st));
+    mark(2);
     AdmitArgs a;
     a.sk = sk;
     a.sv = sv;
@@ -897,6 +903,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     // one warp per group; groups <= n
     const u32 warps = min(n, 152u * 64u);
     FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
+    mark(3);
     FAR_TRY(scan_exclusive(s.admitted, s.rank, n, nullptr, s.scal + SCAL_NADMIT, s.partials, st));
     FAR_TRY(scan_exclusive(s.grp_cnt, s.grp_cnt, n, s.scal + SCAL_NGROUPS, nullptr, s.partials, st));
     FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.scal, m.ctr);
@@ -905,6 +912,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     const bool covs = covariances && (m.cov || prec);
     FAR_LAUNCH(k_grouped_dest, blocks_for(n), TPB, 0, st, s.admitted, s.a_ord, s.a_j, s.grp_cnt, s.pos, n, s.dest,
                covs ? s.added : nullptr, s.keys, (covs && prec) ? s.added_key : nullptr);
+    mark(4);
     if (covs && !prec)
         FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));
     if (covs && prec) {
@@ -913,6 +921,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
         FAR_LAUNCH(k_cov_encode, blocks_for(warps * 32u), TPB, 0, st, s.grp_cnt, s.scal, s.grp_bucket, s.grp_cnt0,
                    s.grp_exp0, m.cexp, s.added, s.cov_tmp, m.nmax, m.cov_h4, m.cov_h2);
     }
+    mark(5);
     return cudaGetLastError();
 }
 

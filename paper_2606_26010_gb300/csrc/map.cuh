@@ -111,11 +111,19 @@ struct Pose12 {
 // Pack `n` records of `stride` bytes (first 12 bytes xyz) into s.in4 (w = index).
 cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStream_t st);
 
+// Events recorded between the parts of an insert (profiling): [0] after keys and slots,
+// [1] after the sort, [2] after grouping (and ASMD), [3] after admission, [4] after ids and
+// the grouped order, [5] after the covariances of added points.
+struct InsertMarks {
+    cudaEvent_t ev[6];
+};
+
 // Insert the packed points s.in4[0..n) into m (Sec. III-A.3). pose == nullptr keys the
 // raw points (scan-local map). Ids start at m.ctr->next_id. With `covariances`, Eq. 1
 // covariances of the added points are computed against the updated map.
 cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
-                             bool covariances, cudaStream_t st, DevicePose dpose = DevicePose());
+                             bool covariances, cudaStream_t st, DevicePose dpose = DevicePose(),
+                             const InsertMarks* marks = nullptr);
 
 // Scan-local sources after map_insert_batch on the local map: s.src / s.src_index in
 // voxel-grouped order (s.src[j].w = admission rank), then their covariances from the

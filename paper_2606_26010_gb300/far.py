@@ -77,6 +77,14 @@ class StageTimes(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class InsertTimes(ctypes.Structure):
+    _fields_ = [("keys_ms", ctypes.c_double), ("sort_ms", ctypes.c_double), ("group_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("ids_ms", ctypes.c_double), ("cov_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ThresholdState(ctypes.Structure):
     _fields_ = [("sigma0", ctypes.c_double), ("min_motion", ctypes.c_double), ("r_max", ctypes.c_double),
                 ("sse", ctypes.c_double), ("n", ctypes.c_int64)]
@@ -113,6 +121,7 @@ _SIGS = {
     "far_batch_process": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, ctypes.c_double, _vp, _vp]),
     "far_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "far_get_stage_times": (ctypes.c_int, [_vp, _vp]),
+    "far_get_insert_times": (ctypes.c_int, [_vp, _vp]),
     "far_gn_footprint": (ctypes.c_int, [_vp, _vp]),
     "far_threshold_init": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "far_threshold_get": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -343,6 +352,12 @@ class VoxelMap:
         t = StageTimes()
         _check(self._L.far_get_stage_times(self._h, ctypes.byref(t)))
         return t.as_dict()
+
+    def insert_times(self) -> dict:
+        """Parts of the last profiled scan's two inserts: {'sources': ..., 'map': ...} (ms)."""
+        t = (InsertTimes * 2)()
+        _check(self._L.far_get_insert_times(self._h, t))
+        return {"sources": t[0].as_dict(), "map": t[1].as_dict()}
 
     def gn_footprint(self):
         """(source points, distinct map voxels probed, points in those voxels) at the last pose."""
