@@ -145,8 +145,8 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     pl.local_buckets = pl.max_n;
     pl.local_cap = next_pow2((uint64_t)pl.max_n * 2);
     const size_t n = pl.max_n;
-    const u32 rblk = radix_blocks(pl.max_n);
-    const size_t partials = std::max<size_t>(scan_blocks(pl.max_n), scan_blocks(256u * rblk)) + 2;
+    const size_t partials = scan_blocks(pl.max_n) + 2;
+    const size_t slots_max = std::max<size_t>(pl.cap, pl.local_cap) + 1;
     static far_map dummy;
     far_map* t = m ? m : &dummy;
     auto add = [&](void** ptr, size_t bytes) {
@@ -179,12 +179,13 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     add((void**)&t->s.in4, n * sizeof(float4));
     add((void**)&t->s.world, n * sizeof(float4));
     add((void**)&t->s.keys, n * sizeof(u64));
-    for (u32** a : {&t->s.sk, &t->s.sv, &t->s.sk_alt, &t->s.sv_alt, &t->s.flags, &t->s.gidx, &t->s.admitted,
+    for (u32** a : {&t->s.sk, &t->s.sv, &t->s.sk_alt, &t->s.sv_alt, &t->s.flags, &t->s.gsize, &t->s.gslot, &t->s.admitted,
                     &t->s.rank, &t->s.pos, &t->s.added, &t->s.src_index, &t->s.head_ord, &t->s.grp_cnt,
                     &t->s.a_ord, &t->s.a_j, &t->s.dest})
         add((void**)a, (n + 1) * sizeof(u32));
     add((void**)&t->s.gstart, (n + 2) * sizeof(u32));
-    add((void**)&t->s.hist, (size_t)256 * rblk * sizeof(u32));
+    add((void**)&t->s.slot_cnt, slots_max * sizeof(u32));
+    add((void**)&t->s.slot_base, slots_max * sizeof(u32));
     add((void**)&t->s.partials, partials * sizeof(u32));
     add((void**)&t->s.scal, SCAL_COUNT * sizeof(u32));
     add((void**)&t->s.src, n * sizeof(float4));
@@ -575,6 +576,9 @@ far_status far_map_create(const far_map_params* params, void* cuda_stream, far_m
     m->s.max_gn_blocks = (u32)(gn_partials_doubles(pl.max_n) / 32);
     cudaError_t e = map_clear(m->map, m->stream);
     if (e == cudaSuccess) e = map_clear(m->local, m->stream);
+    // per-slot batch counters start at zero (every insert leaves them zero)
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(m->s.slot_cnt, 0, (std::max<size_t>(pl.cap, pl.local_cap) + 1) * sizeof(u32), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) {
         release(m);

@@ -2,10 +2,12 @@
 // Submap Density cap, eviction, rebuild, export helpers and stage searches.
 // FAR-LIO Sec. III-A.2 (cuVoxelMap) and Sec. III-A.3 (submap update).
 //
-// Determinism: admission inside a voxel follows the input order because the
-// points of a batch are grouped by a stable radix sort on their slot index;
-// point ids are an exclusive scan of the admission flags in input order. Slot
-// and bucket placement depend on thread timing, but nothing visible does.
+// Determinism: the points of a batch are grouped by hash slot (a per-slot counter gives
+// each point its rank in its group and each group a contiguous range, placed in whatever
+// order the atomics happen to run); each group is then sorted by input index, so admission
+// inside a voxel follows the input order; point ids are an exclusive scan of the admission
+// flags in input order. Slot, bucket and group placement depend on thread timing, but
+// nothing visible does.
 #include "map.cuh"
 #include "primitives.cuh"
 #include "search.cuh"
@@ -35,7 +37,8 @@ __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* 
 // receives the coordinates relative to the tile origin.
 __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
                              float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys,
-                             u32* __restrict__ scal, MapCounters* ctr, u32* __restrict__ admitted) {
+                             u32* __restrict__ scal, MapCounters* ctr, u32* __restrict__ admitted,
+                             u32* __restrict__ flags) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,6 +51,7 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
     }
     if (i >= n) return;
     admitted[i] = 0u;
+    flags[i] = 0u;
     if (dp.T) {
 #pragma unroll
         for (int j = 0; j < 12; ++j) T.m[j] = dp.T[j];
@@ -91,13 +95,15 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
     keys[i] = key;
 }
 
+// Slot of each point's voxel (inserting new keys), and the point's arrival rank among the
+// points of this batch in that slot (out_rank, from the per-slot counter slot_cnt).
 __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slots, u32 mask,
-                                 u32* __restrict__ out_slot, u32* __restrict__ out_idx, MapCounters* ctr) {
+                                 u32* __restrict__ out_slot, u32* __restrict__ out_rank, MapCounters* ctr,
+                                 u32* __restrict__ slot_cnt) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out_idx[i] = i;
     const u64 key = keys[i];
     const u32 sentinel = mask + 1u;
     if (key == KEY_INVALID) {
@@ -111,6 +117,7 @@ __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slot
         const u64 k = *reinterpret_cast<volatile u64*>(&slots[h].key);
         if (k == key) {
             out_slot[i] = h;
+            out_rank[i] = atomicAdd(&slot_cnt[h], 1u);
             atomicMax(&ctr->max_probe, p);
             return;
         }
@@ -118,6 +125,7 @@ __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slot
             const u64 old = atomicCAS(&slots[h].key, KEY_EMPTY, key);
             if (old == KEY_EMPTY || old == key) {
                 out_slot[i] = h;
+                out_rank[i] = atomicAdd(&slot_cnt[h], 1u);
                 atomicMax(&ctr->max_probe, p);
                 return;
             }
@@ -129,26 +137,35 @@ __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slot
     atomicAdd(&ctr->n_dropped, 1u);
 }
 
-__global__ void k_group_heads(const u32* __restrict__ sk, u32 n, u32 sentinel, u32* __restrict__ flags) {
+// Groups: the first point of each slot (rank 0) opens the slot's group, a contiguous range
+// of its size taken from the running total, and records it under a group index.
+__global__ void k_group_alloc(const u32* __restrict__ slot_of, const u32* __restrict__ rank, u32 n, u32 sentinel,
+                              const u32* __restrict__ slot_cnt, u32* __restrict__ slot_base, u32* __restrict__ scal,
+                              u32* __restrict__ gstart, u32* __restrict__ gsize, u32* __restrict__ gslot) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const u32 k = sk[i];
-    flags[i] = (k != sentinel && (i == 0 || sk[i - 1] != k)) ? 1u : 0u;
+    const u32 h = slot_of[i];
+    if (h == sentinel || rank[i] != 0u) return;
+    const u32 size = slot_cnt[h];
+    const u32 g = atomicAdd(&scal[SCAL_NGROUPS], 1u);
+    const u32 base = atomicAdd(&scal[SCAL_NVALID], size);
+    slot_base[h] = base;
+    gstart[g] = base;
+    gsize[g] = size;
+    gslot[g] = h;
 }
 
-__global__ void k_group_starts(const u32* __restrict__ sk, u32* __restrict__ flags,
-                               const u32* __restrict__ gidx, u32 n, u32 sentinel, u32* __restrict__ gstart,
-                               const u32* __restrict__ scal) {
+// Every point to its place in its group (arrival order for now).
+__global__ void k_group_scatter(const u32* __restrict__ slot_of, const u32* __restrict__ rank, u32 n, u32 sentinel,
+                                const u32* __restrict__ slot_base, u32* __restrict__ members) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (flags[i]) gstart[gidx[i]] = i;
-    flags[i] = 0u;   // cleared for the head marks that follow (each thread reads only its own)
-    const u32 k = sk[i];
-    if (k != sentinel && (i + 1 == n || sk[i + 1] == sentinel)) gstart[scal[SCAL_NGROUPS]] = i + 1;
+    const u32 h = slot_of[i];
+    if (h != sentinel) members[slot_base[h] + rank[i]] = i;
 }
 
 __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v, double sx, double sy,
@@ -159,31 +176,169 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// a10: sum and count of the (uncapped) candidate counts of this batch's voxels within r_c.
-__global__ void k_asmd_near(const u32* __restrict__ gstart, const u32* __restrict__ scal,
-                            const u32* __restrict__ sk, const Slot* __restrict__ slots, double v, InsertCfg cfg,
-                            const double* __restrict__ dev_T, MapCounters* ctr) {
+// Sort of one group's input indices by one warp (values are distinct): up to 512 in
+// registers (bitonic network over 32 lanes x R values), larger groups as chunks of GS_SMEM
+// sorted in the warp's shared memory and merged through `tmp` (at most 32 chunks). Returns
+// false when the group is too large.
+constexpr int GS_SMEM = 1024;
+constexpr int GS_WARPS = TPB / 32;
+
+// Bitonic sort of 32 * R values held R per lane (element e = lane * R + r), registers only.
+template <int R>
+__device__ __forceinline__ void bitonic_regs(u32 (&v)[R], int lane) {
+    constexpr int N = 32 * R;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < R) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int p = r ^ j;
+                    if (p > r) {
+                        const bool up = (((lane * R + r) & k) == 0);
+                        const u32 a = v[r], b = v[p];
+                        v[r] = up ? min(a, b) : max(a, b);
+                        v[p] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+                const int lm = j / R;
+                const bool lower = (lane & lm) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u32 o = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                    const bool up = (((lane * R + r) & k) == 0);
+                    v[r] = (lower == up) ? min(v[r], o) : max(v[r], o);
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void sort_group_regs(u32* a, u32 size, int lane) {
+    u32 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const u32 e = (u32)(lane * R + r);
+        v[r] = e < size ? a[e] : 0xFFFFFFFFu;
+    }
+    bitonic_regs<R>(v, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const u32 e = (u32)(lane * R + r);
+        if (e < size) a[e] = v[r];
+    }
+}
+
+__device__ __forceinline__ void bitonic_smem(u32* buf, int len, int lane) {   // len a power of two <= GS_SMEM
+    for (int k = 2; k <= len; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < len; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const u32 a = buf[i], b = buf[p];
+                    const bool up = ((i & k) == 0);
+                    if ((a > b) == up) {
+                        buf[i] = b;
+                        buf[p] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf, int lane) {
+    if (size <= 1) return true;
+    if (size <= 32) {
+        sort_group_regs<1>(a, size, lane);
+        return true;
+    }
+    if (size <= 128) {
+        sort_group_regs<4>(a, size, lane);
+        return true;
+    }
+    if (size <= 512) {
+        sort_group_regs<16>(a, size, lane);
+        return true;
+    }
+    const u32 chunks = (size + GS_SMEM - 1) / GS_SMEM;
+    if (chunks > 32) return false;
+    for (u32 c = 0; c < chunks; ++c) {
+        const u32 c0 = c * GS_SMEM, len = min((u32)GS_SMEM, size - c0);
+        int p2 = 32;
+        while ((u32)p2 < len) p2 <<= 1;
+        for (int i = lane; i < p2; i += 32) buf[i] = (u32)i < len ? a[c0 + i] : 0xFFFFFFFFu;
+        __syncwarp();
+        bitonic_smem(buf, p2, lane);
+        for (u32 i = lane; i < len; i += 32) a[c0 + i] = buf[i];
+        __syncwarp();
+    }
+    if (chunks == 1) return true;
+    // merge: lane c follows chunk c; the warp takes the smallest head each step
+    u32 pc = (u32)lane < chunks ? (u32)lane * GS_SMEM : 0u;
+    const u32 ec = (u32)lane < chunks ? min((u32)(lane + 1) * GS_SMEM, size) : 0u;
+    for (u32 o = 0; o < size; ++o) {
+        const u32 head = pc < ec ? a[pc] : 0xFFFFFFFFu;
+        u32 m = head;
+#pragma unroll
+        for (int s2 = 16; s2 > 0; s2 >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, s2));
+        if (head == m && pc < ec) {
+            tmp[o] = m;
+            ++pc;
+        }
+    }
+    __syncwarp();
+    for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
+    __syncwarp();
+    return true;
+}
+
+// One warp per group: sort its members by input index, flag the group's first input index
+// (its voxel ordinal follows from a scan of the flags), clear the slot's counter for the
+// next insert and, with ASMD (a10), add the group to the near-voxel sums when its voxel
+// centre lies within r_c of the sensor.
+__global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u32* __restrict__ tmp,
+                                                    const u32* __restrict__ scal, const u32* __restrict__ gstart,
+                                                    const u32* __restrict__ gsize, const u32* __restrict__ gslot,
+                                                    u32* __restrict__ slot_cnt, u32* __restrict__ flags,
+                                                    const Slot* __restrict__ slots, double v, InsertCfg cfg,
+                                                    const double* __restrict__ dev_T, MapCounters* ctr) {
     pdl_wait();
     pdl_trigger();
-    if (dev_T) {
+    __shared__ u32 sbuf[GS_WARPS][GS_SMEM];
+    if (cfg.asmd && dev_T) {
         cfg.sx = dev_T[3];
         cfg.sy = dev_T[7];
         cfg.sz = dev_T[11];
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 ng = scal[SCAL_NGROUPS];
-    unsigned long long sum = 0, cnt = 0;
-    for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const u32 s0 = gstart[g], s1 = gstart[g + 1];
-        int kx, ky, kz;
-        unpack_key(slots[sk[s0]].key, kx, ky, kz);
-        if (centre_dist2(kx, ky, kz, v, cfg.sx, cfg.sy, cfg.sz) <= cfg.rc2) {
-            sum += s1 - s0;
-            cnt += 1;
+    unsigned long long near_sum = 0, near_cnt = 0;
+    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += (gridDim.x * blockDim.x) >> 5) {
+        const u32 base = gstart[g], size = gsize[g], h = gslot[g];
+        if (!sort_group(members + base, size, tmp + base, sbuf[warp], lane)) {
+            if (lane == 0) atomicOr(&ctr->err, (u32)ERR_GROUP_SIZE);
+        }
+        if (lane == 0) {
+            flags[members[base]] = 1u;
+            slot_cnt[h] = 0u;
+            if (cfg.asmd) {
+                int kx, ky, kz;
+                unpack_key(slots[h].key, kx, ky, kz);
+                if (centre_dist2(kx, ky, kz, v, cfg.sx, cfg.sy, cfg.sz) <= cfg.rc2) {
+                    near_sum += size;
+                    near_cnt += 1;
+                }
+            }
         }
     }
-    if (cnt) {
-        atomicAdd(&ctr->near_sum, sum);
-        atomicAdd(&ctr->near_cnt, cnt);
+    if (lane == 0 && near_cnt) {
+        atomicAdd(&ctr->near_sum, near_sum);
+        atomicAdd(&ctr->near_cnt, near_cnt);
     }
 }
 
@@ -201,9 +356,10 @@ __device__ __forceinline__ u32 asmd_cap(int kx, int ky, int kz, double v, const 
 }
 
 struct AdmitArgs {
-    const u32* sk;
-    const u32* sv;
+    const u32* gslot;     // slot of each group
+    const u32* sv;        // group members (input indices), each group sorted ascending
     const u32* gstart;
+    const u32* gsize;
     const u32* scal;
     const float4* world;
     Slot* slots;
@@ -251,8 +407,8 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     const u32 ring_tail = a.ctr->ring_tail;
     const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
     for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps_total) {
-        const u32 start = a.gstart[g], end = a.gstart[g + 1];
-        const u32 slot = a.sk[start];
+        const u32 start = a.gstart[g], end = start + a.gsize[g];
+        const u32 slot = a.gslot[g];
         const u32 ord = a.head_ord[a.sv[start]];
         Slot* sp = a.slots + slot;
         u32 bucket = sp->bucket;
@@ -349,16 +505,6 @@ __global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __rest
     pts[pos[i]].w = __uint_as_float(base + r);
     if (r + 1 == scal[SCAL_NADMIT] && (unsigned long long)base + scal[SCAL_NADMIT] > 0xFFFFFFFFull)
         atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
-}
-
-// Group heads: the first (smallest) input index of every voxel of the batch.
-__global__ void k_mark_heads(const u32* __restrict__ gstart, const u32* __restrict__ sv,
-                             const u32* __restrict__ scal, u32* __restrict__ head_flag) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 ng = scal[SCAL_NGROUPS];
-    for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        head_flag[sv[gstart[g]]] = 1u;
 }
 
 // Position of each admitted point in the grouped order and the list of added positions.
@@ -851,32 +997,32 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
         FAR_TRY(cudaMemsetAsync(&m.ctr->n_added, 0, sizeof(u32), st));
         return cudaSuccess;
     }
-    const u32 sentinel = m.cap;
+    const u32 sentinel = m.mask + 1u;
     Pose12 T{};
     if (pose) T = *pose;
     FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
-               m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted);
-    FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr);
+               m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted, s.flags);
+    FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr,
+               s.slot_cnt);
     mark(0);
-    bool alt = false;
-    FAR_TRY(radix_sort_pairs(s.sk, s.sv, s.sk_alt, s.sv_alt, n, m.key_bits, s.hist, s.partials, st, &alt));
+    // groups by slot: contiguous ranges of s.sv_alt, each sorted by input index
+    FAR_LAUNCH(k_group_alloc, blocks_for(n), TPB, 0, st, s.sk, s.sv, n, sentinel, s.slot_cnt, s.slot_base, s.scal,
+               s.gstart, s.gsize, s.gslot);
+    FAR_LAUNCH(k_group_scatter, blocks_for(n), TPB, 0, st, s.sk, s.sv, n, sentinel, s.slot_base, s.sv_alt);
     mark(1);
-    const u32* sk = alt ? s.sk_alt : s.sk;
-    const u32* sv = alt ? s.sv_alt : s.sv;
-    FAR_LAUNCH(k_group_heads, blocks_for(n), TPB, 0, st, sk, n, sentinel, s.flags);
-    FAR_TRY(scan_exclusive(s.flags, s.gidx, n, nullptr, s.scal + SCAL_NGROUPS, s.partials, st));
-    FAR_LAUNCH(k_group_starts, blocks_for(n), TPB, 0, st, sk, s.flags, s.gidx, n, sentinel, s.gstart, s.scal);
-    if (cfg.asmd)
-        FAR_LAUNCH(k_asmd_near, blocks_for(n), TPB, 0, st, s.gstart, s.scal, sk, m.slots, (double)m.v, cfg, dpose.T,
-                                                   m.ctr);
-    // voxel ordinals in first-input-index order (flags were cleared by k_group_starts)
-    FAR_LAUNCH(k_mark_heads, blocks_for(n), TPB, 0, st, s.gstart, sv, s.scal, s.flags);
+    {
+        const u32 warps = min(n, 152u * 32u);
+        FAR_LAUNCH(k_group_sort, blocks_for(warps * 32u), TPB, 0, st, s.sv_alt, s.sk_alt, s.scal, s.gstart, s.gsize,
+                   s.gslot, s.slot_cnt, s.flags, m.slots, (double)m.v, cfg, dpose.T, m.ctr);
+    }
+    // voxel ordinals in first-input-index order (k_world_keys cleared the flags)
     FAR_TRY(scan_exclusive(s.flags, s.head_ord, n, nullptr, nullptr, s.partials, st));
     mark(2);
     AdmitArgs a;
-    a.sk = sk;
-    a.sv = sv;
+    a.gslot = s.gslot;
+    a.sv = s.sv_alt;
     a.gstart = s.gstart;
+    a.gsize = s.gsize;
     a.scal = s.scal;
     a.world = s.world;
     a.slots = m.slots;

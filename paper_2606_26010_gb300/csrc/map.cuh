@@ -50,7 +50,9 @@ struct Scratch {
     float4* world = nullptr;   // keyed points (map frame), by input index
     u64* keys = nullptr;
     u32 *sk = nullptr, *sv = nullptr, *sk_alt = nullptr, *sv_alt = nullptr;
-    u32 *flags = nullptr, *gidx = nullptr, *gstart = nullptr;
+    u32 *flags = nullptr, *gstart = nullptr;
+    u32 *gsize = nullptr, *gslot = nullptr;       // by group: size and hash slot
+    u32 *slot_cnt = nullptr, *slot_base = nullptr;  // by hash slot (both maps): batch counts, group bases
     u32 *admitted = nullptr, *rank = nullptr, *pos = nullptr, *added = nullptr;
     // voxel-grouped order of the admitted points: voxels ordered by their first input index,
     // points of a voxel in input order (deterministic, and follows the scan's spatial order)
@@ -59,7 +61,7 @@ struct Scratch {
     u32 *a_ord = nullptr;      // by input index: voxel ordinal of an admitted point
     u32 *a_j = nullptr;        // by input index: position among the voxel's points admitted by this batch
     u32 *dest = nullptr;       // by input index: position of an admitted point in the grouped order
-    u32 *hist = nullptr, *partials = nullptr;
+    u32* partials = nullptr;
     u32* scal = nullptr;       // device scalars, see SCAL_*
     // registration sources
     float4 *src = nullptr, *src_cov = nullptr;
@@ -87,7 +89,7 @@ struct Scratch {
     signed char* src_exp = nullptr;      // exponent of each source's scan-local voxel
 };
 
-enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_COUNT = 8 };
+enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_COUNT = 8 };
 
 struct InsertCfg {
     int asmd = 0;

@@ -26,14 +26,14 @@ namespace {
 constexpr u32 kStaticMaxPoints = 16384;
 constexpr u32 kStaticMaxPerVoxel = 20;
 constexpr u32 kLocalCap = 2 * kStaticMaxPoints;           // power of two >= 2 n, as the map plan uses
-constexpr u32 kHistWords = 256u * (kStaticMaxPoints / 2048u + 1u);
 constexpr u32 kPartialWords = 1024;
 
 constexpr size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Byte offsets of every sub-buffer inside the static array.
 struct Layout {
-    size_t slots, pts, ring, ctr, in4, world, keys, u32s[16], gstart, hist, partials, scal, src, src_cov, total;
+    size_t slots, pts, ring, ctr, in4, world, keys, u32s[17], gstart, slot_cnt, slot_base, partials, scal, src, src_cov,
+        total;
 };
 
 constexpr Layout make_layout() {
@@ -51,9 +51,10 @@ constexpr Layout make_layout() {
     L.in4 = take((size_t)kStaticMaxPoints * sizeof(float4));
     L.world = take((size_t)kStaticMaxPoints * sizeof(float4));
     L.keys = take((size_t)kStaticMaxPoints * sizeof(u64));
-    for (int i = 0; i < 16; ++i) L.u32s[i] = take((size_t)(kStaticMaxPoints + 1) * sizeof(u32));
+    for (int i = 0; i < 17; ++i) L.u32s[i] = take((size_t)(kStaticMaxPoints + 1) * sizeof(u32));
     L.gstart = take((size_t)(kStaticMaxPoints + 2) * sizeof(u32));
-    L.hist = take((size_t)kHistWords * sizeof(u32));
+    L.slot_cnt = take((size_t)(kLocalCap + 1) * sizeof(u32));   // zero at load; every insert leaves it zero
+    L.slot_base = take((size_t)(kLocalCap + 1) * sizeof(u32));
     L.partials = take((size_t)kPartialWords * sizeof(u32));
     L.scal = take((size_t)SCAL_COUNT * sizeof(u32));
     L.src = take((size_t)kStaticMaxPoints * sizeof(float4));
@@ -114,8 +115,7 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     if (!out_index || !out_cov || !out_valid || !on_device(out_index) || !on_device(out_cov) || !on_device(out_valid) ||
         (out_knn_ids && !on_device(out_knn_ids)))
         return reject(FAR_ERR_INVALID, "outputs must be device pointers (out_knn_ids may be NULL)");
-    if ((size_t)256 * radix_blocks((u32)n) > kHistWords ||
-        scan_blocks(256u * radix_blocks((u32)n)) + 2 > kPartialWords || scan_blocks((u32)n) + 2 > kPartialWords)
+    if (scan_blocks((u32)n) + 2 > kPartialWords)
         return reject(FAR_ERR_INVALID, "internal: static scratch layout too small");
 
     // Set-up, once per device with that device current: resolve the array's device address.
@@ -166,11 +166,12 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     s.in4 = reinterpret_cast<float4*>(base + kLayout.in4);
     s.world = reinterpret_cast<float4*>(base + kLayout.world);
     s.keys = reinterpret_cast<u64*>(base + kLayout.keys);
-    u32** u32s[16] = {&s.sk,   &s.sv,    &s.sk_alt,    &s.sv_alt,   &s.flags,   &s.gidx,  &s.admitted, &s.rank,
-                      &s.pos,  &s.added, &s.src_index, &s.head_ord, &s.grp_cnt, &s.a_ord, &s.a_j,      &s.dest};
-    for (int i = 0; i < 16; ++i) *u32s[i] = reinterpret_cast<u32*>(base + kLayout.u32s[i]);
+    u32** u32s[17] = {&s.sk,   &s.sv,    &s.sk_alt,    &s.sv_alt,   &s.flags,   &s.gsize, &s.admitted, &s.rank, &s.pos,
+                      &s.added, &s.src_index, &s.head_ord, &s.grp_cnt, &s.a_ord, &s.a_j,   &s.dest,     &s.gslot};
+    for (int i = 0; i < 17; ++i) *u32s[i] = reinterpret_cast<u32*>(base + kLayout.u32s[i]);
     s.gstart = reinterpret_cast<u32*>(base + kLayout.gstart);
-    s.hist = reinterpret_cast<u32*>(base + kLayout.hist);
+    s.slot_cnt = reinterpret_cast<u32*>(base + kLayout.slot_cnt);
+    s.slot_base = reinterpret_cast<u32*>(base + kLayout.slot_base);
     s.partials = reinterpret_cast<u32*>(base + kLayout.partials);
     s.scal = reinterpret_cast<u32*>(base + kLayout.scal);
     s.src = reinterpret_cast<float4*>(base + kLayout.src);
