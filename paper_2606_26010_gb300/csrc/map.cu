@@ -729,9 +729,12 @@ __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, do
     const float fv = (float)v, fcx = (float)cx, fcy = (float)cy, fcz = (float)cz, fr2 = (float)r2;
     // Each FP32 centre difference is off by at most a few ulps of the largest coordinate M,
     // so e2 is within about 8 * 2^-23 * M / r of d^2 in relative terms near the radius r;
-    // the band below is wider than that, and everything inside it takes the FP64 test.
-    const double M = fabs(cx) + fabs(cy) + fabs(cz) + sqrt(r2) + v;
-    const float band = (float)(1e-5 + 1e-6 * M / fmax(sqrt(r2), 1e-3));
+    // the band below is twice that (plus 2e-5), and everything inside it takes the FP64
+    // test. The band is FP32 arithmetic: FP64 square roots and divisions in every thread
+    // would cost more than the whole table scan on this GPU.
+    const float fr = sqrtf(fr2);
+    const float Mf = fabsf(fcx) + fabsf(fcy) + fabsf(fcz) + fr + fv;
+    const float band = 2e-5f + 2e-6f * Mf / fmaxf(fr, 1e-3f);
     const float lo2 = fr2 * (1.0f - band), hi2 = fr2 * (1.0f + band);
     for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
         const u64 key = slots[h].key;
