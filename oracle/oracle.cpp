@@ -87,17 +87,26 @@ float dist2_f32(const float a[3], const float b[3]) {
 
 // ------------------------------------------------------------------ precision variant: 50 m tiles
 // Tile reading (precision_mode = 1): the tile of a world coordinate x is
-// T = floor(x / 50) (FP64 division), the tile-relative coordinate is
+// T = floor(x / 50) (exact, see tile_floor), the tile-relative coordinate is
 // x_t = fp32(x - 50 T), and the voxel key is T tv + clamp(floor(fp32(x_t * inv_v)), 0, tv - 1)
 // with tv = 50 / v voxels per tile side (v must divide 50 m). The clamp keeps every key
 // inside the tile of its point when x_t rounds to 50 or to a tiny negative value.
 constexpr double kTile = 50.0;
 
+// floor(x / 50) in exact arithmetic: the rounded quotient's floor, moved by one when 50 T
+// (exact in FP64) shows it is off.
+double tile_floor(double x) {
+    double T = std::floor(x / kTile);
+    if (kTile * T > x) T -= 1.0;
+    else if (kTile * (T + 1.0) <= x) T += 1.0;
+    return T;
+}
+
 bool tile_key(const double x[3], float inv_v, int tv, Key* out, float local[3], int32_t tile[3]) {
     int32_t k[3];
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(x[a])) return false;
-        double T = std::floor(x[a] / kTile);
+        double T = tile_floor(x[a]);
         if (!(std::fabs(T) * tv < (double)kKeyLimit)) return false;
         float xt = (float)(x[a] - kTile * T);
         float s = xt * inv_v;
@@ -360,7 +369,7 @@ int knn27(const OracleMap& m, const float q[3], int k, std::vector<const MapPoin
     if (m.prec) {
         fr.tv = m.tv;
         for (int a = 0; a < 3; ++a) {
-            double T = std::floor((double)q[a] / kTile);
+            double T = tile_floor((double)q[a]);
             fr.f[a] = (int32_t)T;
             qf[a] = (float)((double)q[a] - kTile * T);
         }
@@ -639,7 +648,7 @@ const MapPoint* nearest27(const OracleMap& m, const float q[3], float* d2_out) {
     if (m.prec) {
         fr.tv = m.tv;
         for (int a = 0; a < 3; ++a) {
-            double T = std::floor((double)q[a] / kTile);
+            double T = tile_floor((double)q[a]);
             fr.f[a] = (int32_t)T;
             qf[a] = (float)((double)q[a] - kTile * T);
         }
@@ -658,7 +667,7 @@ Frame anchor_frame(const OracleMap& m, const double T[16], double A[3]) {
     if (m.prec) {
         fr.tv = m.tv;
         for (int a = 0; a < 3; ++a) {
-            double t = std::floor(T[4 * a + 3] / kTile);
+            double t = tile_floor(T[4 * a + 3]);
             fr.f[a] = (int32_t)t;
             A[a] = kTile * t;
         }

@@ -459,7 +459,10 @@ GnArgs gn_args(far_map* m, const double* pose, u32 n, float tau, float kappa, do
         a.anchor[j] = 0.0;
         a.ftile[j] = 0;
         if (m->map.tv > 0) {
-            const double T = std::floor(pose[4 * j + 3] / 50.0);
+            // floor(t / 50) exactly (the rounded quotient's floor, corrected by the exact 50 T)
+            double T = std::floor(pose[4 * j + 3] / 50.0);
+            if (50.0 * T > pose[4 * j + 3]) T -= 1.0;
+            else if (50.0 * (T + 1.0) <= pose[4 * j + 3]) T += 1.0;
             a.ftile[j] = (int)T;
             a.anchor[j] = 50.0 * T;
         }

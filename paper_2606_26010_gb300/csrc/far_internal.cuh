@@ -215,11 +215,20 @@ __device__ __forceinline__ bool better(float d2, u32 id, float bd2, u32 bid) {
 // ----------------------------------------------------------------------------- precision variant
 __device__ __forceinline__ int floor_div(int k, int tv) { return k >= 0 ? k / tv : -((-k + tv - 1) / tv); }
 
-// Tile reading: T = floor(x / 50) (FP64), x_t = fp32(x - 50 T), key = T tv + clamp(floor(fp32(x_t * inv_v)),
+// floor(x / 50) in exact arithmetic, without an FP64 division: the floor of x * 0.02 is
+// off by at most one, which the exact products 50 T and 50 (T + 1) settle.
+__device__ __forceinline__ double tile_floor(double x) {
+    double T = floor(__dmul_rn(x, 0.02));
+    if (__dmul_rn(TILE_D, T) > x) T -= 1.0;
+    else if (__dmul_rn(TILE_D, T + 1.0) <= x) T += 1.0;
+    return T;
+}
+
+// Tile reading: T = floor(x / 50) (exact), x_t = fp32(x - 50 T), key = T tv + clamp(floor(fp32(x_t * inv_v)),
 // 0, tv - 1). Returns false when x is not finite or the key leaves [-2^20, 2^20).
 __device__ __forceinline__ bool tile_key_axis(double x, float inv_v, int tv, int& key, float& local) {
     if (!isfinite(x)) return false;
-    const double T = floor(__ddiv_rn(x, TILE_D));
+    const double T = tile_floor(x);
     if (!(fabs(T) * (double)tv < (double)KEY_BIAS)) return false;
     const float xt = __double2float_rn(__dsub_rn(x, __dmul_rn(TILE_D, T)));
     int kin = (int)floorf(__fmul_rn(xt, inv_v));

@@ -401,9 +401,16 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     const int lane = threadIdx.x & 31;
     const u32 warps_total = (gridDim.x * blockDim.x) >> 5;
     const u32 ng = a.scal[SCAL_NGROUPS];
-    double n_near = (double)a.nmax;
-    if (a.cfg.asmd && a.ctr->near_cnt > 0)
-        n_near = __ddiv_rn((double)a.ctr->near_sum, (double)a.ctr->near_cnt);
+    // N_near once per block (FP64 divisions and square roots are slow on this GPU: each is
+    // evaluated by one thread and shared)
+    __shared__ double s_near;
+    if (threadIdx.x == 0) {
+        double nn = (double)a.nmax;
+        if (a.cfg.asmd && a.ctr->near_cnt > 0) nn = __ddiv_rn((double)a.ctr->near_sum, (double)a.ctr->near_cnt);
+        s_near = nn;
+    }
+    __syncthreads();
+    const double n_near = s_near;
     const u32 ring_tail = a.ctr->ring_tail;
     const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
     for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps_total) {
@@ -437,7 +444,11 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
         }
         int kx, ky, kz;
         unpack_key(sp->key, kx, ky, kz);
-        const u32 cap = a.cfg.asmd ? asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax) : a.nmax;
+        u32 cap = a.nmax;
+        if (a.cfg.asmd) {
+            if (lane == 0) cap = asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax);
+            cap = __shfl_sync(0xffffffffu, cap, 0);
+        }
         float4* bp = a.pts + (size_t)bucket * a.nmax;
         float4 e0 = (lane < (int)cnt) ? bp[lane] : far4;
         float4 e1 = (lane + 32 < (int)cnt) ? bp[lane + 32] : far4;
@@ -852,7 +863,7 @@ __device__ __forceinline__ bool world_query_frame(const MapView& m, float qx, fl
     for (int a = 0; a < 3; ++a) {
         const double x = (double)q[a];
         if (!isfinite(x)) return false;
-        const double T = floor(__ddiv_rn(x, TILE_D));
+        const double T = tile_floor(x);
         if (!(fabs(T) * (double)m.tv < (double)KEY_BIAS)) return false;
         ft[a] = (int)T;
         qf[a] = __double2float_rn(__dsub_rn(x, __dmul_rn(TILE_D, T)));

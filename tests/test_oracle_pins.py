@@ -676,3 +676,14 @@ def test_termination_measures_the_increment_at_the_sensor():
     assert s0["iters"] == s1["iters"] < 30
     D01 = np.linalg.inv(shift @ P0) @ P1
     assert np.linalg.norm(D01[:3, 3]) < 1e-7
+
+
+def test_prec_tile_of_a_point_just_below_a_tile_corner():
+    """A world coordinate one ulp below a multiple of 50 m lies in the lower tile (exact floor),
+    and its key is the exact voxel index, at the last voxel of that tile."""
+    x = np.nextafter(50.0 * 2003, 0.0)          # 100150 - 1.5e-11
+    pose = synth.make_pose(np.eye(3), [x - 1.0, 0.25, 0.25])
+    m = oracle.OracleMap(0.5, 20, 1, min_spacing=0.0, precision_mode=1)
+    m.insert(np.array([[1.0, 0.0, 0.0]], np.float32), pose)
+    ex = m.export()
+    assert list(ex["keys"][0]) == [2003 * 100 - 1, 0, 0]
