@@ -90,6 +90,20 @@ def parse_args():
     return ap.parse_args()
 
 
+def aggregate_ranks(dev_s: float, pts: float, world: int, device: str):
+    """Whole-job figures of a replicated run: the slowest rank's time and every rank's points."""
+    if world <= 1:
+        return dev_s, pts
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([dev_s, pts], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def rank_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -295,15 +309,7 @@ def run_ours(args):
     mp.close()
     pts = float(sum(scans[t].shape[0] for t in range(1 + args.warmup, n_total)))
     dev_s = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([dev_s, pts], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        dev_s_all, pts_all = float(mx[0]), float(sm[1])
-    else:
-        dev_s_all, pts_all = dev_s, pts
+    dev_s_all, pts_all = aggregate_ranks(dev_s, pts, world, "cuda")
     value = pts_all / dev_s_all / 1e6
     lat = np.array(step_ms)
 

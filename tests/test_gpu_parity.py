@@ -120,6 +120,18 @@ def test_no_spacing_and_single_voxel_cap(far):
         assert_maps_equal(g.export(), o.export())
 
 
+@pytest.mark.parametrize("size", [33, 513, 2500, 6000, 9000])
+def test_large_voxel_groups_admit_in_input_order(far, size):
+    """All points of a batch in a few voxels: groups above 32, 128 and 512 points (register sorts)
+    and above 1024 (chunks sorted in shared memory and merged) still admit in input order."""
+    rng = np.random.default_rng(size)
+    pts = rng.uniform(0.01, 0.99, size=(size, 3)).astype(np.float32)   # voxels (0|1, 0|1, 0|1) at v = 0.5
+    for spacing in (0.0, 0.03):
+        g, o = build_pair(far, [pts, pts[::-1].copy()], [np.eye(4), np.eye(4)], nmax=64, spacing=spacing,
+                          max_scan=20_000)
+        assert_maps_equal(g.export(), o.export())
+
+
 # ------------------------------------------------------------------ searches
 def test_scan_sources_bit_exact(far, problem1):
     g = far.VoxelMap(0.5, 20, 5, max_scan_points=300_000)
@@ -254,6 +266,21 @@ def test_strides_and_device_inputs_agree(far, problem1, maps1):
     dev = torch.from_numpy(problem1.query).cuda()
     assert np.array_equal(g.register(dev, problem1.init)[0], base)           # device pointer
     assert np.array_equal(g.register(problem1.query, problem1.init)[0], base)  # deterministic
+
+
+def test_graph_loop_equals_explicit_launches(far, problem1, maps1):
+    """With conv_eps > 0 the loop runs as a graph with a device-side while loop; with profiling it
+    runs as explicit launches. Both apply the same kernels in the same order: identical results."""
+    g, _ = maps1
+    kw = dict(max_iters=10, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+    T1, C1, s1 = g.register(problem1.query, problem1.init, **kw)
+    g.set_profiling(True)
+    try:
+        T2, C2, s2 = g.register(problem1.query, problem1.init, **kw)
+    finally:
+        g.set_profiling(False)
+    assert np.array_equal(T1, T2) and np.array_equal(C1, C2)
+    assert s1["iters"] == s2["iters"] and s1["converged"] == s2["converged"] == 1
 
 
 def test_convergence_flag_stops_iterations(far, problem1, maps1):
