@@ -127,76 +127,114 @@ __device__ __forceinline__ u32 warp_sum_u(u32 v) {
     return v;
 }
 
-// Nearest map point of q (smallest (d^2, id)) searched by a group of TPP consecutive
-// lanes. The 27 voxels are taken in the order own, faces, edges, corners, in rounds of
-// TPP (lane sl takes entry round * TPP + sl); after each round the group shares its best
-// packed key (d2 bits << 32 | id, ordered like (d2, id) since d2 >= 0), and a voxel whose
-// box distance exceeds min(best, tau^2) is skipped. Candidates are loaded four at a time.
-// best_v is the c_nb_order index of the winner's voxel (its frame offset in the precision
-// variant). Every lane of the warp must call this (full-warp shuffles).
-template <int TPP, bool PREC>
-__device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
-                                              float limit2, int sl, unsigned long long& best_key, u32& best_pos,
-                                              int& best_v) {
-    best_key = ~0ull;
-    best_pos = 0;
-    best_v = 0;
+// Scan voxel c_nb_order[v] around the query for its nearest candidate, unless its box
+// distance exceeds `bound`. Candidates are loaded four at a time.
+template <bool PREC>
+__device__ __forceinline__ void nn_try_voxel(const MapView& m, u32 max_probe, const QFrame<PREC>& f,
+                                             const FaceDist& fd, int v, float bound, unsigned long long& best_key,
+                                             u32& best_pos, int& best_v) {
+    const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
+    const int nx = f.k[0] + dx, ny = f.k[1] + dy, nz = f.k[2] + dz;
+    u32 bucket, count;
+    if (box_lb2(fd, dx, dy, dz) > bound || !key_in_range(nx) || !key_in_range(ny) || !key_in_range(nz) ||
+        !find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count))
+        return;
     const float qx = f.q[0], qy = f.q[1], qz = f.q[2];
-    const int kx = f.k[0], ky = f.k[1], kz = f.k[2];
-    const FaceDist fd = face_distances(qx, qy, qz, f.lk[0], f.lk[1], f.lk[2], m.v);
-    constexpr int kRounds = (27 + TPP - 1) / TPP;
-    for (int round = 0; round < kRounds; ++round) {
-        const int v = round * TPP + sl;
-        float bound = fminf(__uint_as_float((u32)(best_key >> 32)), limit2);
-        if (best_key == ~0ull) bound = limit2;
-        if (keyed && v < 27) {
-            const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
-            const int nx = kx + dx, ny = ky + dy, nz = kz + dz;
-            u32 bucket, count;
-            if (!(box_lb2(fd, dx, dy, dz) > bound) && key_in_range(nx) && key_in_range(ny) && key_in_range(nz) &&
-                find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) {
-                const u32 base = bucket * m.nmax;
-                const float ox = f.off(0, dx), oy = f.off(1, dy), oz = f.off(2, dz);
-                for (u32 j0 = 0; j0 < count; j0 += 4) {
-                    float4 c[4];
+    const u32 base = bucket * m.nmax;
+    const float ox = f.off(0, dx), oy = f.off(1, dy), oz = f.off(2, dz);
+    for (u32 j0 = 0; j0 < count; j0 += 4) {
+        float4 c[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        if constexpr (PREC) {
-                            c[u].x = __fadd_rn(c[u].x, ox);
-                            c[u].y = __fadd_rn(c[u].y, oy);
-                            c[u].z = __fadd_rn(c[u].z, oz);
-                        }
-                    }
+        for (int u = 0; u < 4; ++u) {
+            c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (PREC) {
+                c[u].x = __fadd_rn(c[u].x, ox);
+                c[u].y = __fadd_rn(c[u].y, oy);
+                c[u].z = __fadd_rn(c[u].z, oz);
+            }
+        }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (j0 + u < count) {
-                            const float d2 = dist2_rn(qx, qy, qz, c[u].x, c[u].y, c[u].z);
-                            const unsigned long long key =
-                                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c[u].w);
-                            if (key < best_key) {
-                                best_key = key;
-                                best_pos = base + j0 + u;
-                                if constexpr (PREC) best_v = v;
-                            }
-                        }
-                    }
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u < count) {
+                const float d2 = dist2_rn(qx, qy, qz, c[u].x, c[u].y, c[u].z);
+                const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c[u].w);
+                if (key < best_key) {
+                    best_key = key;
+                    best_pos = base + j0 + u;
+                    if constexpr (PREC) best_v = v;
                 }
             }
         }
+    }
+}
+
+// Share the group's best (packed key d2 bits << 32 | id, ordered like (d2, id) since d2 >= 0).
+template <int TPP, bool PREC>
+__device__ __forceinline__ void group_best(unsigned long long& best_key, u32& best_pos, int& best_v) {
 #pragma unroll
-        for (int o = TPP / 2; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best_key, o);
-            const u32 op = __shfl_xor_sync(0xffffffffu, best_pos, o);
-            int ov = 0;
-            if constexpr (PREC) ov = __shfl_xor_sync(0xffffffffu, best_v, o);
-            if (ok < best_key) {
-                best_key = ok;
-                best_pos = op;
-                if constexpr (PREC) best_v = ov;
-            }
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best_key, o);
+        const u32 op = __shfl_xor_sync(0xffffffffu, best_pos, o);
+        int ov = 0;
+        if constexpr (PREC) ov = __shfl_xor_sync(0xffffffffu, best_v, o);
+        if (ok < best_key) {
+            best_key = ok;
+            best_pos = op;
+            if constexpr (PREC) best_v = ov;
         }
     }
+}
+
+__device__ __forceinline__ float nn_group_bound(unsigned long long best_key, float limit2) {
+    return best_key == ~0ull ? limit2 : fminf(__uint_as_float((u32)(best_key >> 32)), limit2);
+}
+
+// Nearest map point of q (smallest (d^2, id)) searched by a group of TPP consecutive
+// lanes. The first TPP voxels of the order own, faces, edges, corners are scanned at once
+// (lane sl takes entry sl); the group then keeps only the other voxels whose box distance
+// does not exceed min(best, tau^2), lists them in shared memory (`list`, 27 entries per
+// group) and scans them TPP at a time, sharing the best after each round. A voxel whose box
+// distance exceeds the bound cannot hold a point with a smaller (d^2, id), so the result is
+// the exact minimum over the 27 voxels. best_v is the c_nb_order index of the winner's voxel
+// (its frame offset in the precision variant). Every lane of the warp must call this.
+template <int TPP, bool PREC>
+__device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
+                                              float limit2, int sl, unsigned long long& best_key, u32& best_pos,
+                                              int& best_v, unsigned char* list) {
+    best_key = ~0ull;
+    best_pos = 0;
+    best_v = 0;
+    const FaceDist fd = face_distances(f.q[0], f.q[1], f.q[2], f.lk[0], f.lk[1], f.lk[2], m.v);
+    if (keyed && sl < 27) nn_try_voxel<PREC>(m, max_probe, f, fd, sl, limit2, best_key, best_pos, best_v);
+    group_best<TPP, PREC>(best_key, best_pos, best_v);
+    // survivors of the remaining voxels under the group's bound, compacted in input order
+    const float bound0 = nn_group_bound(best_key, limit2);
+    u32 mine = 0;
+    int k = 0;
+    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+        if (keyed && !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound0)) mine |= 1u << k;
+    const int cnt = __popc(mine);
+    int pre = cnt;   // inclusive prefix over the group's lanes
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o, TPP);
+        if (sl >= o) pre += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, TPP - 1, TPP);
+    pre -= cnt;
+    k = 0;
+    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+        if (mine & (1u << k)) list[pre++] = (unsigned char)v;
+    __syncwarp();
+    const int rounds = (__reduce_max_sync(0xffffffffu, (u32)total) + TPP - 1) / TPP;   // warp-uniform
+    for (int r = 0; r < rounds; ++r) {
+        const int s2 = r * TPP + sl;
+        if (s2 < total)
+            nn_try_voxel<PREC>(m, max_probe, f, fd, list[s2], nn_group_bound(best_key, limit2), best_key, best_pos,
+                               best_v);
+        group_best<TPP, PREC>(best_key, best_pos, best_v);
+    }
+    __syncwarp();
 }
 
 // Linearisation half of a Gauss-Newton iteration: TPP lanes cooperate on each source
@@ -211,6 +249,7 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
     constexpr int ACC_STRIDE = NACC + 3;
     constexpr int kParts = GN_THREADS / 32;
     __shared__ float gacc[kGroups * ACC_STRIDE];
+    __shared__ unsigned char vlist[kGroups][28];   // surviving neighbour voxels of each group's query
     __shared__ float red[kParts][NACC + 2];
     __shared__ float pose_f[12];
     __shared__ u32 s_flag;
@@ -260,7 +299,7 @@ __device__ __forceinline__ void gn_lin_block(const GnArgs& a, u32 vblock, u32 vg
             if (keyed && nearest27q<PREC>(m, max_probe, f, a.tau2, d2b, idb, bpos, bv))
                 bkey = ((unsigned long long)__float_as_uint(d2b) << 32) | idb;
         } else {
-            group_nearest<TPP, PREC>(m, max_probe, f, keyed, a.tau2, sl, bkey, bpos, bv);
+            group_nearest<TPP, PREC>(m, max_probe, f, keyed, a.tau2, sl, bkey, bpos, bv, vlist[threadIdx.x / TPP]);
         }
         if (!active || sl != 0) continue;
         const float bd2 = __uint_as_float((u32)(bkey >> 32));
