@@ -297,10 +297,35 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
     return true;
 }
 
-// One warp per group: sort its members by input index, flag the group's first input index
-// (its voxel ordinal follows from a scan of the flags), clear the slot's counter for the
-// next insert and, with ASMD (a10), add the group to the near-voxel sums when its voxel
-// centre lies within r_c of the sensor.
+// Warp w of W takes the groups w, w + W, w + 2W, ... (32 per pass, one per lane), so that the
+// large groups, which lie close together in group order, spread over the warps.
+// Groups of at most GS_LANE_MAX members are sorted by one lane each (insertion network in
+// registers); larger ones by the whole warp (sort_group).
+constexpr u32 GS_LANE_MAX = 8;
+
+__device__ __forceinline__ void sort_lane(u32* a, u32 size, u32& head) {
+    u32 v[GS_LANE_MAX];
+#pragma unroll
+    for (u32 r = 0; r < GS_LANE_MAX; ++r) v[r] = r < size ? a[r] : 0xFFFFFFFFu;
+#pragma unroll
+    for (u32 i = 1; i < GS_LANE_MAX; ++i)
+#pragma unroll
+        for (u32 j = i; j > 0; --j) {
+            const u32 lo = min(v[j - 1], v[j]), hi = max(v[j - 1], v[j]);
+            v[j - 1] = lo;
+            v[j] = hi;
+        }
+#pragma unroll
+    for (u32 r = 0; r < GS_LANE_MAX; ++r)
+        if (r < size) a[r] = v[r];
+    head = v[0];
+}
+
+// Each lane of a warp takes one group of a batch of 32 (strided over the group range): sort its members by input index,
+// flag the group's first input index (its voxel ordinal follows from a scan of the flags),
+// clear the slot's counter for the next insert and, with ASMD (a10), add the group to the
+// near-voxel sums when its voxel centre lies within r_c of the sensor. Groups larger than
+// GS_LANE_MAX are sorted afterwards by the whole warp, one at a time.
 __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u32* __restrict__ tmp,
                                                     const u32* __restrict__ scal, const u32* __restrict__ gstart,
                                                     const u32* __restrict__ gsize, const u32* __restrict__ gslot,
@@ -317,14 +342,32 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 ng = scal[SCAL_NGROUPS];
+    const u32 warps_total = (gridDim.x * blockDim.x) >> 5;
+    const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long near_sum = 0, near_cnt = 0;
-    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += (gridDim.x * blockDim.x) >> 5) {
-        const u32 base = gstart[g], size = gsize[g], h = gslot[g];
-        if (!sort_group(members + base, size, tmp + base, sbuf[warp], lane)) {
-            if (lane == 0) atomicOr(&ctr->err, (u32)ERR_GROUP_SIZE);
+    for (u32 j0 = 0; w + j0 * warps_total < ng; j0 += 32) {
+        const u32 g = w + (j0 + lane) * warps_total;
+        const bool gv = g < ng;
+        u32 base = 0, size = 0, h = 0, head = 0;
+        if (gv) {
+            base = gstart[g];
+            size = gsize[g];
+            h = gslot[g];
+            if (size <= GS_LANE_MAX) sort_lane(members + base, size, head);
         }
-        if (lane == 0) {
-            flags[members[base]] = 1u;
+        u32 big = __ballot_sync(0xffffffffu, gv && size > GS_LANE_MAX);
+        while (big) {
+            const int f = __ffs(big) - 1;
+            big &= big - 1u;
+            const u32 fb = __shfl_sync(0xffffffffu, base, f), fs = __shfl_sync(0xffffffffu, size, f);
+            if (!sort_group(members + fb, fs, tmp + fb, sbuf[warp], lane)) {
+                if (lane == 0) atomicOr(&ctr->err, (u32)ERR_GROUP_SIZE);
+            }
+            __syncwarp();
+            if (lane == f) head = members[fb];
+        }
+        if (gv) {
+            flags[head] = 1u;
             slot_cnt[h] = 0u;
             if (cfg.asmd) {
                 int kx, ky, kz;
@@ -335,6 +378,11 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
                 }
             }
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        near_sum += __shfl_xor_sync(0xffffffffu, near_sum, o);
+        near_cnt += __shfl_xor_sync(0xffffffffu, near_cnt, o);
     }
     if (lane == 0 && near_cnt) {
         atomicAdd(&ctr->near_sum, near_sum);
@@ -385,11 +433,13 @@ struct AdmitArgs {
     int* grp_exp0;
 };
 
-// a11 admission: one warp per voxel group. Candidates are walked in input order;
-// a candidate enters while the voxel holds fewer than its cap and no point of the
-// voxel is closer than d_min (FP32 d^2 >= d_min^2). Lanes hold the voxel's points
-// (lane j: points j and j + 32) and test a candidate against all of them at once;
-// windows of 32 candidates are prefetched one per lane.
+// a11 admission. A warp takes 32 voxel groups at a time (strided over the group range): each
+// lane reads the header of one group (members, slot, bucket, fill, ASMD cap) and opens a bucket for a new voxel. The warp
+// then walks the groups that can still take points. Candidates are walked in input order; a
+// candidate enters while the voxel holds fewer than its cap and no point of the voxel is
+// closer than d_min (FP32 d^2 >= d_min^2). Lanes hold the voxel's points (lane j: points j
+// and j + 32) and test a candidate against all of them at once; windows of 32 candidates
+// are prefetched one per lane.
 __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     pdl_wait();
     pdl_trigger();
@@ -413,92 +463,120 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     const double n_near = s_near;
     const u32 ring_tail = a.ctr->ring_tail;
     const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
-    for (u32 g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps_total) {
-        const u32 start = a.gstart[g], end = start + a.gsize[g];
-        const u32 slot = a.gslot[g];
-        const u32 ord = a.head_ord[a.sv[start]];
-        Slot* sp = a.slots + slot;
-        u32 bucket = sp->bucket;
-        u32 cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
-        if (bucket == NO_BUCKET) {
-            u32 b = NO_BUCKET;
-            if (lane == 0) {
-                const u32 h = atomicAdd(&a.ctr->ring_head, 1u);
+    const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (u32 j0 = 0; w + j0 * warps_total < ng; j0 += 32) {
+        // --- lane-parallel headers
+        const u32 g = w + (j0 + lane) * warps_total;
+        const bool gv = g < ng;
+        u32 start = 0, end = 0, slot = 0, ord = 0, bucket = NO_BUCKET, cnt = 0, cap = 0;
+        Slot* sp = nullptr;
+        if (gv) {
+            start = a.gstart[g];
+            end = start + a.gsize[g];
+            slot = a.gslot[g];
+            ord = a.head_ord[a.sv[start]];
+            sp = a.slots + slot;
+            bucket = sp->bucket;
+            cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
+        }
+        // new voxels take buckets from the ring: one atomic per warp
+        const bool need = gv && bucket == NO_BUCKET;
+        const u32 need_mask = __ballot_sync(0xffffffffu, need);
+        if (need_mask) {
+            u32 h0 = 0;
+            if (lane == __ffs(need_mask) - 1) h0 = atomicAdd(&a.ctr->ring_head, (u32)__popc(need_mask));
+            h0 = __shfl_sync(0xffffffffu, h0, __ffs(need_mask) - 1);
+            const u32 h = h0 + __popc(need_mask & ((1u << lane) - 1u));
+            bool got = false;
+            if (need) {
                 if (h < ring_tail) {
-                    b = a.ring[h % a.max_buckets];
-                    sp->bucket = b;
+                    bucket = a.ring[h % a.max_buckets];
+                    sp->bucket = bucket;
                     sp->count = 0;
-                    if (a.cexp) a.cexp[b] = EXP_NONE;  // a recycled bucket starts without an exponent
-                    atomicAdd(&a.ctr->n_voxels, 1u);
+                    if (a.cexp) a.cexp[bucket] = EXP_NONE;  // a recycled bucket starts without an exponent
+                    got = true;
                 } else {
                     atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
                     atomicAdd(&a.ctr->n_dropped, end - start);
                 }
             }
-            b = __shfl_sync(0xffffffffu, b, 0);
-            if (b == NO_BUCKET) {
-                if (lane == 0) a.grp_cnt[ord] = 0;
-                continue;
-            }
-            bucket = b;
+            const u32 got_mask = __ballot_sync(0xffffffffu, got);
+            if (lane == 0 && got_mask) atomicAdd(&a.ctr->n_voxels, (u32)__popc(got_mask));
         }
-        int kx, ky, kz;
-        unpack_key(sp->key, kx, ky, kz);
-        u32 cap = a.nmax;
-        if (a.cfg.asmd) {
-            if (lane == 0) cap = asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax);
-            cap = __shfl_sync(0xffffffffu, cap, 0);
-        }
-        float4* bp = a.pts + (size_t)bucket * a.nmax;
-        float4 e0 = (lane < (int)cnt) ? bp[lane] : far4;
-        float4 e1 = (lane + 32 < (int)cnt) ? bp[lane + 32] : far4;
-        const u32 cnt0 = cnt;
-        for (u32 w0 = start; w0 < end && cnt < cap; w0 += 32) {
-            // lane l holds candidate w0 + l and tests it against the points held at window start
-            const u32 i = w0 + lane;
-            const bool in_window = i < end;
-            const u32 my_idx = in_window ? a.sv[i] : 0u;
-            const float4 my_c = in_window ? a.world[my_idx] : far4;
-            bool pass = in_window;
-            for (u32 j = 0; j < cnt; ++j) {
-                const float ex = __shfl_sync(0xffffffffu, j < 32 ? e0.x : e1.x, j & 31u);
-                const float ey = __shfl_sync(0xffffffffu, j < 32 ? e0.y : e1.y, j & 31u);
-                const float ez = __shfl_sync(0xffffffffu, j < 32 ? e0.z : e1.z, j & 31u);
-                pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, ex, ey, ez) >= a.dmin2);
-            }
-            // resolve in input order: the first passing lane is admitted, later lanes are
-            // re-tested against it only (earlier lanes already failed against a subset)
-            while (cnt < cap) {
-                const u32 ballot = __ballot_sync(0xffffffffu, pass);
-                if (ballot == 0u) break;
-                const int f = __ffs(ballot) - 1;
-                const float cx = __shfl_sync(0xffffffffu, my_c.x, f);
-                const float cy = __shfl_sync(0xffffffffu, my_c.y, f);
-                const float cz = __shfl_sync(0xffffffffu, my_c.z, f);
-                const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
-                if (lane == (int)(cnt & 31u)) {
-                    if (cnt < 32) e0 = c;
-                    else e1 = c;
+        if (gv) {
+            if (bucket != NO_BUCKET) {
+                cap = a.nmax;
+                if (a.cfg.asmd) {
+                    int kx, ky, kz;
+                    unpack_key(sp->key, kx, ky, kz);
+                    cap = asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax);
                 }
-                if (lane == f) {
-                    bp[cnt] = c;
-                    a.pos[my_idx] = bucket * a.nmax + cnt;
-                    a.admitted[my_idx] = 1u;
-                    a.a_ord[my_idx] = ord;
-                    a.a_j[my_idx] = cnt - cnt0;
+                if (a.cexp) {
+                    a.grp_bucket[ord] = bucket;
+                    a.grp_cnt0[ord] = cnt;
+                    a.grp_exp0[ord] = a.cexp[bucket];
                 }
-                ++cnt;
-                if (lane <= f) pass = false;
-                else if (pass) pass = dist2_rn(my_c.x, my_c.y, my_c.z, cx, cy, cz) >= a.dmin2;
             }
+            if (cnt >= cap) a.grp_cnt[ord] = 0;
         }
-        if (lane == 0) {
-            if (cnt != cnt0) sp->count = cnt;
-            a.grp_cnt[ord] = cnt - cnt0;
-            if (a.cexp) {
-                a.grp_bucket[ord] = bucket;
-                a.grp_cnt0[ord] = cnt0;
-                a.grp_exp0[ord] = a.cexp[bucket];
+        // --- groups that can take points, one at a time by the whole warp
+        u32 work = __ballot_sync(0xffffffffu, cnt < cap);
+        while (work) {
+            const int f = __ffs(work) - 1;
+            work &= work - 1u;
+            const u32 w_start = __shfl_sync(0xffffffffu, start, f);
+            const u32 w_end = __shfl_sync(0xffffffffu, end, f);
+            const u32 w_ord = __shfl_sync(0xffffffffu, ord, f);
+            const u32 w_bucket = __shfl_sync(0xffffffffu, bucket, f);
+            const u32 w_cap = __shfl_sync(0xffffffffu, cap, f);
+            const u32 w_slot = __shfl_sync(0xffffffffu, slot, f);
+            const u32 cnt0 = __shfl_sync(0xffffffffu, cnt, f);
+            u32 c_n = cnt0;
+            float4* bp = a.pts + (size_t)w_bucket * a.nmax;
+            float4 e0 = (lane < (int)c_n) ? bp[lane] : far4;
+            float4 e1 = (lane + 32 < (int)c_n) ? bp[lane + 32] : far4;
+            for (u32 w0 = w_start; w0 < w_end && c_n < w_cap; w0 += 32) {
+                // lane l holds candidate w0 + l and tests it against the points held at window start
+                const u32 i = w0 + lane;
+                const bool in_window = i < w_end;
+                const u32 my_idx = in_window ? a.sv[i] : 0u;
+                const float4 my_c = in_window ? a.world[my_idx] : far4;
+                bool pass = in_window;
+                for (u32 j = 0; j < c_n; ++j) {
+                    const float ex = __shfl_sync(0xffffffffu, j < 32 ? e0.x : e1.x, j & 31u);
+                    const float ey = __shfl_sync(0xffffffffu, j < 32 ? e0.y : e1.y, j & 31u);
+                    const float ez = __shfl_sync(0xffffffffu, j < 32 ? e0.z : e1.z, j & 31u);
+                    pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, ex, ey, ez) >= a.dmin2);
+                }
+                // resolve in input order: the first passing lane is admitted, later lanes are
+                // re-tested against it only (earlier lanes already failed against a subset)
+                while (c_n < w_cap) {
+                    const u32 ballot = __ballot_sync(0xffffffffu, pass);
+                    if (ballot == 0u) break;
+                    const int fl = __ffs(ballot) - 1;
+                    const float cx = __shfl_sync(0xffffffffu, my_c.x, fl);
+                    const float cy = __shfl_sync(0xffffffffu, my_c.y, fl);
+                    const float cz = __shfl_sync(0xffffffffu, my_c.z, fl);
+                    const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
+                    if (lane == (int)(c_n & 31u)) {
+                        if (c_n < 32) e0 = c;
+                        else e1 = c;
+                    }
+                    if (lane == fl) {
+                        bp[c_n] = c;
+                        a.pos[my_idx] = w_bucket * a.nmax + c_n;
+                        a.admitted[my_idx] = 1u;
+                        a.a_ord[my_idx] = w_ord;
+                        a.a_j[my_idx] = c_n - cnt0;
+                    }
+                    ++c_n;
+                    if (lane <= fl) pass = false;
+                    else if (pass) pass = dist2_rn(my_c.x, my_c.y, my_c.z, cx, cy, cz) >= a.dmin2;
+                }
+            }
+            if (lane == 0) {
+                if (c_n != cnt0) a.slots[w_slot].count = c_n;
+                a.grp_cnt[w_ord] = c_n - cnt0;
             }
         }
     }
@@ -559,6 +637,7 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
     const u32 max_probe = m.ctr->max_probe;
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = threadIdx.x % KNN_TPP;
+    __shared__ unsigned char vlist[TPB / KNN_TPP][28];   // surviving neighbour voxels per query
     const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
     const int zero[3] = {0, 0, 0};
     for (u32 base = (t & ~31u) / KNN_TPP; base < nn; base += stride) {   // warp-uniform trip count
@@ -569,7 +648,8 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
         const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, bd, bid, bpos);
+        const int found =
+            group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid, bpos);
         if (!active || sl != 0) continue;
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (found >= K) covariance_from_neighbours<K>(m.pts, bpos, p.x, p.y, p.z, c0, c1);
@@ -598,6 +678,7 @@ __global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __re
     const u32 max_probe = m.ctr->max_probe;
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = threadIdx.x % KNN_TPP;
+    __shared__ unsigned char vlist[TPB / KNN_TPP][28];   // surviving neighbour voxels per query
     const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
     for (u32 base = (t & ~31u) / KNN_TPP; base < nn; base += stride) {   // warp-uniform trip count
         const u32 r = base + (threadIdx.x & 31u) / KNN_TPP;
@@ -610,7 +691,8 @@ __global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __re
         own_qframe(m, p.x, p.y, p.z, kx, ky, kz, f);
         float bd[K];
         u32 bid[K], bpos[K];
-        const int found = group_knn<K, KNN_TPP, true>(m, max_probe, f, active, sl, bd, bid, bpos);
+        const int found =
+            group_knn<K, KNN_TPP, true>(m, max_probe, f, active, sl, vlist[threadIdx.x / KNN_TPP], bd, bid, bpos);
         if (!active || sl != 0) continue;
         float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool valid = false;
@@ -879,6 +961,7 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
     const u32 max_probe = m.ctr->max_probe;
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = threadIdx.x % KNN_TPP;
+    __shared__ unsigned char vlist[TPB / KNN_TPP][28];   // surviving neighbour voxels per query
     const u32 stride = gridDim.x * blockDim.x / KNN_TPP;
     const int zero[3] = {0, 0, 0};
     for (u32 base = (t & ~31u) / KNN_TPP; base < n; base += stride) {   // warp-uniform trip count
@@ -891,11 +974,13 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
         if (m.tv > 0) {
             QFrame<true> f;
             const bool keyed = active && world_query_frame(m, p.x, p.y, p.z, f);
-            found = group_knn<K, KNN_TPP, true>(m, max_probe, f, keyed, sl, bd, bid, bpos);
+            found = group_knn<K, KNN_TPP, true>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid,
+                                                bpos);
         } else {
             QFrame<false> f;
             const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
-            found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, bd, bid, bpos);
+            found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid,
+                                                 bpos);
         }
         if (!active || sl != 0) continue;
         found_out[r] = found;
@@ -1025,7 +1110,8 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     FAR_LAUNCH(k_group_scatter, blocks_for(n), TPB, 0, st, s.sk, s.sv, n, sentinel, s.slot_base, s.sv_alt);
     mark(1);
     {
-        const u32 warps = min(n, 152u * 32u);
+        // one resident wave (3 blocks of 8 warps per SM at 77 registers)
+        const u32 warps = min(n, 152u * 24u);
         FAR_LAUNCH(k_group_sort, blocks_for(warps * 32u), TPB, 0, st, s.sv_alt, s.sk_alt, s.scal, s.gstart, s.gsize,
                    s.gslot, s.slot_cnt, s.flags, m.slots, (double)m.v, cfg, dpose.T, m.ctr);
     }
@@ -1060,8 +1146,9 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     a.grp_bucket = s.grp_bucket;
     a.grp_cnt0 = s.grp_cnt0;
     a.grp_exp0 = s.grp_exp0;
-    // one warp per group; groups <= n
-    const u32 warps = min(n, 152u * 64u);
+    // groups <= n, up to 32 per warp and pass; one resident wave (4 blocks of 8 warps per SM at
+    // 64 registers)
+    const u32 warps = min(n, 152u * 32u);
     FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
     mark(3);
     FAR_TRY(scan_exclusive(s.admitted, s.rank, n, nullptr, s.scal + SCAL_NADMIT, s.partials, st));

@@ -264,35 +264,65 @@ __device__ __forceinline__ void knn_insert(float d2, u32 id, u32 pos, float (&bd
     }
 }
 
-// K nearest of the query searched by a group of TPP consecutive lanes: lane sl scans the
-// voxels round * TPP + sl of the order own, faces, edges, corners into its own sorted K
-// best; after each round the group shares the smallest K-th distance of any lane (the K best
-// of the union are at least that close) and a voxel whose box distance exceeds it is
-// skipped. The lanes' lists are then merged pairwise, so every lane of the group ends with
-// the K best of the union in (d2, id) order (the lanes saw disjoint voxels). Returns the
-// number of candidates the group saw, capped at K. Every lane of the warp must call this.
+// K nearest of the query searched by a group of TPP consecutive lanes. Lane sl first scans
+// voxel sl of the order own, faces, edges, corners into its own sorted K best; the group then
+// takes the smallest K-th distance of any lane as its bound (the K best of the union are at
+// least that close), lists the remaining voxels whose box distance does not exceed it
+// (compacted into `list`, at least 27 - TPP bytes of the group's own memory) and scans them
+// TPP at a time, re-testing each against the bound of the round before. The lanes' lists are
+// then merged pairwise, so every lane of the group ends with the K best of the union in
+// (d2, id) order (the lanes saw disjoint voxels). Returns the number of candidates the group
+// saw, capped at K. Every lane of the warp must call this.
 template <int K, int TPP, bool PREC>
 __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
-                                         int sl, float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+                                         int sl, unsigned char* list, float (&bd)[K], u32 (&bid)[K],
+                                         u32 (&bpos)[K]) {
     knn_init<K>(bd, bid, bpos);
     int found = 0;
     const FaceDist fd = face_distances(f.q[0], f.q[1], f.q[2], f.lk[0], f.lk[1], f.lk[2], m.v);
-    float bound = F_INF;
-    constexpr int kRounds = (27 + TPP - 1) / TPP;
-    for (int round = 0; round < kRounds; ++round) {
-        const int v = round * TPP + sl;
-        if (keyed && v < 27) {
-            const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
-            const int nx = f.k[0] + dx, ny = f.k[1] + dy, nz = f.k[2] + dz;
-            if (key_in_range(nx) && key_in_range(ny) && key_in_range(nz) && !(box_lb2(fd, dx, dy, dz) > bound))
-                knn_scan_voxel<K, PREC>(m, max_probe, nx, ny, nz, f.q[0], f.q[1], f.q[2], found, bd, bid, bpos,
-                                        f.off(0, dx), f.off(1, dy), f.off(2, dz));
-        }
+    auto scan = [&](int v) {
+        const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
+        const int nx = f.k[0] + dx, ny = f.k[1] + dy, nz = f.k[2] + dz;
+        if (key_in_range(nx) && key_in_range(ny) && key_in_range(nz))
+            knn_scan_voxel<K, PREC>(m, max_probe, nx, ny, nz, f.q[0], f.q[1], f.q[2], found, bd, bid, bpos,
+                                    f.off(0, dx), f.off(1, dy), f.off(2, dz));
+    };
+    auto group_bound = [&]() {
         float kth = bd[K - 1];
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) kth = fminf(kth, __shfl_xor_sync(0xffffffffu, kth, o));
-        bound = kth;
+        return kth;
+    };
+    if (keyed && sl < 27) scan(sl);
+    float bound = group_bound();
+    // survivors of the remaining voxels under the group's bound, compacted in voxel order
+    u32 mine = 0;
+    int k = 0;
+    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+        if (keyed && !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound)) mine |= 1u << k;
+    const int cnt = __popc(mine);
+    int pre = cnt;   // inclusive prefix over the group's lanes
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o, TPP);
+        if (sl >= o) pre += t;
     }
+    const int total = __shfl_sync(0xffffffffu, pre, TPP - 1, TPP);
+    pre -= cnt;
+    k = 0;
+    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+        if (mine & (1u << k)) list[pre++] = (unsigned char)v;
+    __syncwarp();
+    const int rounds = (__reduce_max_sync(0xffffffffu, (u32)total) + TPP - 1) / TPP;   // warp-uniform
+    for (int r = 0; r < rounds; ++r) {
+        const int s2 = r * TPP + sl;
+        if (s2 < total) {
+            const int v = list[s2];
+            if (!(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound)) scan(v);
+        }
+        bound = group_bound();
+    }
+    __syncwarp();
 #pragma unroll
     for (int o = TPP / 2; o > 0; o >>= 1) {
         found += __shfl_xor_sync(0xffffffffu, found, o);
