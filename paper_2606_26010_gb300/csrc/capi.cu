@@ -145,7 +145,7 @@ Plan make_plan(const far_map_params& p, far_map* m) {
     pl.local_buckets = pl.max_n;
     pl.local_cap = next_pow2((uint64_t)pl.max_n * 2);
     const size_t n = pl.max_n;
-    const size_t partials = scan_blocks(pl.max_n) + 2;
+    const size_t partials = 2 * scan_blocks(pl.max_n) + 2;   // scan_exclusive2: two jobs
     const size_t slots_max = std::max<size_t>(pl.cap, pl.local_cap) + 1;
     static far_map dummy;
     far_map* t = m ? m : &dummy;

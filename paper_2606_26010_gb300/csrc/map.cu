@@ -43,7 +43,8 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     // the insert's first kernel clears its per-insert state (scalars, ASMD sums, admitted flags)
-    if (i < SCAL_COUNT) scal[i] = 0u;
+    // and records the first id it will assign
+    if (i < SCAL_COUNT) scal[i] = (i == SCAL_IDBASE) ? ctr->next_id : 0u;
     if (i == 0) {
         ctr->near_sum = 0ull;
         ctr->near_cnt = 0ull;
@@ -582,42 +583,33 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     }
 }
 
-__global__ void k_assign_ids(const u32* __restrict__ admitted, const u32* __restrict__ rank,
-                             const u32* __restrict__ pos, u32 n, float4* pts, const u32* __restrict__ scal,
-                             MapCounters* ctr) {
+// Admitted points after the two scans: the id (first id + rank in input order), the position
+// in the grouped order (the voxel's ordinal base + its index among the voxel's admitted
+// points) and the list of added positions (and keys); thread 0 advances the map's counters
+// (no thread of this launch reads them).
+__global__ void k_place_admitted(const u32* __restrict__ admitted, const u32* __restrict__ rank,
+                                 const u32* __restrict__ a_ord, const u32* __restrict__ a_j,
+                                 const u32* __restrict__ grp_base, const u32* __restrict__ pos, u32 n,
+                                 float4* pts, u32* __restrict__ dest, u32* __restrict__ added,
+                                 const u64* __restrict__ keys, u64* __restrict__ added_key,
+                                 const u32* __restrict__ scal, MapCounters* ctr) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 id0 = scal[SCAL_IDBASE], n_add = scal[SCAL_NADMIT];
+    if (i == 0) {
+        ctr->next_id = id0 + n_add;
+        ctr->n_points += n_add;
+        ctr->n_added = n_add;
+        if ((unsigned long long)id0 + n_add > 0xFFFFFFFFull) atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
+    }
     if (i >= n || !admitted[i]) return;
-    const u32 base = ctr->next_id;
-    const u32 r = rank[i];
-    pts[pos[i]].w = __uint_as_float(base + r);
-    if (r + 1 == scal[SCAL_NADMIT] && (unsigned long long)base + scal[SCAL_NADMIT] > 0xFFFFFFFFull)
-        atomicOr(&ctr->err, (u32)ERR_ID_OVERFLOW);
-}
-
-// Position of each admitted point in the grouped order and the list of added positions.
-__global__ void k_grouped_dest(const u32* __restrict__ admitted, const u32* __restrict__ a_ord,
-                               const u32* __restrict__ a_j, const u32* __restrict__ grp_base,
-                               const u32* __restrict__ pos, u32 n, u32* __restrict__ dest,
-                               u32* __restrict__ added, const u64* __restrict__ keys, u64* __restrict__ added_key) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !admitted[i]) return;
+    const u32 p = pos[i];
+    pts[p].w = __uint_as_float(id0 + rank[i]);
     const u32 d = grp_base[a_ord[i]] + a_j[i];
     dest[i] = d;
-    if (added) added[d] = pos[i];
+    if (added) added[d] = p;
     if (added_key) added_key[d] = keys[i];
-}
-
-__global__ void k_finalize_insert(MapCounters* ctr, const u32* __restrict__ scal) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 t = scal[SCAL_NADMIT];
-    ctr->next_id += t;
-    ctr->n_points += t;
-    ctr->n_added = t;
 }
 
 // Lanes cooperating on one k-NN query (group_knn); every grid-stride step is warp-uniform.
@@ -1151,14 +1143,14 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     const u32 warps = min(n, 152u * 32u);
     FAR_LAUNCH(k_admit, blocks_for(warps * 32u), TPB, 0, st, a);
     mark(3);
-    FAR_TRY(scan_exclusive(s.admitted, s.rank, n, nullptr, s.scal + SCAL_NADMIT, s.partials, st));
-    FAR_TRY(scan_exclusive(s.grp_cnt, s.grp_cnt, n, s.scal + SCAL_NGROUPS, nullptr, s.partials, st));
-    FAR_LAUNCH(k_assign_ids, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.pos, n, m.pts, s.scal, m.ctr);
-    FAR_LAUNCH(k_finalize_insert, 1, 1, 0, st, m.ctr, s.scal);
+    // ranks of the admitted points (input order) and the voxels' bases in the grouped order
+    FAR_TRY(scan_exclusive2(s.admitted, s.rank, nullptr, s.scal + SCAL_NADMIT, s.grp_cnt, s.grp_cnt,
+                            s.scal + SCAL_NGROUPS, nullptr, n, s.partials, st));
     const bool prec = m.tv > 0;
     const bool covs = covariances && (m.cov || prec);
-    FAR_LAUNCH(k_grouped_dest, blocks_for(n), TPB, 0, st, s.admitted, s.a_ord, s.a_j, s.grp_cnt, s.pos, n, s.dest,
-               covs ? s.added : nullptr, s.keys, (covs && prec) ? s.added_key : nullptr);
+    FAR_LAUNCH(k_place_admitted, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.a_ord, s.a_j, s.grp_cnt, s.pos, n,
+               m.pts, s.dest, covs ? s.added : nullptr, s.keys, (covs && prec) ? s.added_key : nullptr, s.scal,
+               m.ctr);
     mark(4);
     if (covs && !prec)
         FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));

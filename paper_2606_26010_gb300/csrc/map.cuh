@@ -89,7 +89,8 @@ struct Scratch {
     signed char* src_exp = nullptr;      // exponent of each source's scan-local voxel
 };
 
-enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_COUNT = 8 };
+// SCAL_IDBASE: the map's next point id when the insert began (the first id it assigns)
+enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_IDBASE = 3, SCAL_COUNT = 8 };
 
 struct InsertCfg {
     int asmd = 0;

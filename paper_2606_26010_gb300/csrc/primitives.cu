@@ -39,35 +39,52 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* smem_warp, u32& total
     return res;
 }
 
-__global__ void k_scan_reduce(const u32* __restrict__ in, u32 n, const u32* __restrict__ n_dev, u32* partials) {
+// One array of a launch: blockIdx.y selects the job; each job has nb partial sums.
+struct ScanJob {
+    const u32* in;
+    u32* out;
+    u32 n;
+    const u32* n_dev;   // may be null
+    u32* total;         // may be null
+};
+struct ScanJobs {
+    ScanJob j[2];
+    u32 nb;             // blocks per job
+};
+
+__global__ void k_scan_reduce(ScanJobs J, u32* partials) {
     pdl_wait();
     pdl_trigger();
     __shared__ u32 sw[33];
-    if (n_dev) n = min(n, *n_dev);
+    const ScanJob jb = J.j[blockIdx.y];
+    u32 n = jb.n;
+    if (jb.n_dev) n = min(n, *jb.n_dev);
     const u32 base = blockIdx.x * SCAN_TILE;
     u32 s = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
         u32 idx = base + i * SCAN_THREADS + threadIdx.x;
-        if (idx < n) s += in[idx];
+        if (idx < n) s += jb.in[idx];
     }
     u32 total;
     block_excl_scan(s, sw, total);
-    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+    if (threadIdx.x == 0) partials[blockIdx.y * J.nb + blockIdx.x] = total;
 }
 
 // Downsweep: every block adds up the sums of the blocks before it (a short strided
 // sum over at most a few hundred partials) and scans its own tile; the last block also
 // writes the total. Two launches per scan, no waiting between blocks.
-__global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u32 n, const u32* __restrict__ n_dev,
-                            const u32* __restrict__ partials, u32 nb, u32* __restrict__ total_out) {
+__global__ void k_scan_down(ScanJobs J, const u32* __restrict__ partials) {
     pdl_wait();
     pdl_trigger();
     __shared__ u32 sw[33];
     __shared__ u32 s_off;
-    if (n_dev) n = min(n, *n_dev);
+    const ScanJob jb = J.j[blockIdx.y];
+    const u32* part = partials + blockIdx.y * J.nb;
+    u32 n = jb.n;
+    if (jb.n_dev) n = min(n, *jb.n_dev);
     u32 pre = 0;
-    for (u32 b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += partials[b];
+    for (u32 b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += part[b];
     u32 ptot;
     block_excl_scan(pre, sw, ptot);
     if (threadIdx.x == 0) s_off = ptot;
@@ -78,7 +95,7 @@ __global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u
     u32 s = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-        v[i] = (base + i < n) ? in[base + i] : 0u;
+        v[i] = (base + i < n) ? jb.in[base + i] : 0u;
         s += v[i];
     }
     u32 total;
@@ -86,10 +103,18 @@ __global__ void k_scan_down(const u32* __restrict__ in, u32* __restrict__ out, u
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i)
         if (base + i < n) {
-            out[base + i] = run;
+            jb.out[base + i] = run;
             run += v[i];
         }
-    if (total_out && blockIdx.x == nb - 1 && threadIdx.x == 0) *total_out = off + total;
+    if (jb.total && blockIdx.x == J.nb - 1 && threadIdx.x == 0) *jb.total = off + total;
+}
+
+cudaError_t scan_jobs(const ScanJobs& J, u32 njobs, u32* partials, cudaStream_t s) {
+    if (J.nb > 1024u * 64u) return cudaErrorInvalidValue;
+    const dim3 grid(J.nb, njobs);
+    FAR_LAUNCH(k_scan_reduce, grid, SCAN_THREADS, 0, s, J, partials);
+    FAR_LAUNCH(k_scan_down, grid, SCAN_THREADS, 0, s, J, partials);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -98,12 +123,19 @@ u32 scan_blocks(u32 n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
 
 cudaError_t scan_exclusive(const u32* in, u32* out, u32 n, const u32* n_dev, u32* total_dev, u32* partials,
                            cudaStream_t s) {
-    u32 nb = scan_blocks(n);
-    if (nb == 0) nb = 1;
-    if (nb > 1024u * 64u) return cudaErrorInvalidValue;
-    FAR_LAUNCH(k_scan_reduce, nb, SCAN_THREADS, 0, s, in, n, n_dev, partials);
-    FAR_LAUNCH(k_scan_down, nb, SCAN_THREADS, 0, s, in, out, n, n_dev, partials, nb, total_dev);
-    return cudaGetLastError();
+    ScanJobs J{};
+    J.j[0] = ScanJob{in, out, n, n_dev, total_dev};
+    J.nb = max(1u, scan_blocks(n));
+    return scan_jobs(J, 1, partials, s);
+}
+
+cudaError_t scan_exclusive2(const u32* in0, u32* out0, const u32* n_dev0, u32* total0, const u32* in1, u32* out1,
+                            const u32* n_dev1, u32* total1, u32 n, u32* partials, cudaStream_t s) {
+    ScanJobs J{};
+    J.j[0] = ScanJob{in0, out0, n, n_dev0, total0};
+    J.j[1] = ScanJob{in1, out1, n, n_dev1, total1};
+    J.nb = max(1u, scan_blocks(n));
+    return scan_jobs(J, 2, partials, s);
 }
 
 }  // namespace far

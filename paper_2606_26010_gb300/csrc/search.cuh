@@ -127,31 +127,40 @@ __device__ __forceinline__ void knn_scan_voxel(const MapView& m, u32 max_probe, 
     u32 bucket, count;
     if (!find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) return;
     const u32 base = bucket * m.nmax;
-    for (u32 j = 0; j < count; ++j) {
-        float4 p = __ldg(m.pts + base + j);
-        if constexpr (PREC) {
-            p.x = __fadd_rn(p.x, ox);
-            p.y = __fadd_rn(p.y, oy);
-            p.z = __fadd_rn(p.z, oz);
-        }
-        const float d2 = dist2_rn(qx, qy, qz, p.x, p.y, p.z);
-        const u32 id = __float_as_uint(p.w);
-        ++found;
-        if (!better(d2, id, bd[K - 1], bid[K - 1])) continue;
-        // sorted insert: the candidate bubbles up past every worse entry
-        float cd = d2;
-        u32 ci = id, cp = base + j;
+    found += (int)count;
+    // points are loaded four at a time so that several loads are in flight
+    for (u32 j0 = 0; j0 < count; j0 += 4) {
+        float4 c[4];
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            const bool sw = better(cd, ci, bd[s], bid[s]);
-            const float td = bd[s];
-            const u32 ti = bid[s], tp = bpos[s];
-            bd[s] = sw ? cd : td;
-            bid[s] = sw ? ci : ti;
-            bpos[s] = sw ? cp : tp;
-            cd = sw ? td : cd;
-            ci = sw ? ti : ci;
-            cp = sw ? tp : cp;
+        for (int u = 0; u < 4; ++u) {
+            c[u] = (j0 + u < count) ? __ldg(m.pts + base + j0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (PREC) {
+                c[u].x = __fadd_rn(c[u].x, ox);
+                c[u].y = __fadd_rn(c[u].y, oy);
+                c[u].z = __fadd_rn(c[u].z, oz);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u >= count) continue;
+            const float d2 = dist2_rn(qx, qy, qz, c[u].x, c[u].y, c[u].z);
+            const u32 id = __float_as_uint(c[u].w);
+            if (!better(d2, id, bd[K - 1], bid[K - 1])) continue;
+            // sorted insert: the candidate bubbles up past every worse entry
+            float cd = d2;
+            u32 ci = id, cp = base + j0 + u;
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const bool sw = better(cd, ci, bd[s], bid[s]);
+                const float td = bd[s];
+                const u32 ti = bid[s], tp = bpos[s];
+                bd[s] = sw ? cd : td;
+                bid[s] = sw ? ci : ti;
+                bpos[s] = sw ? cp : tp;
+                cd = sw ? td : cd;
+                ci = sw ? ti : ci;
+                cp = sw ? tp : cp;
+            }
         }
     }
 }

@@ -115,7 +115,7 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     if (!out_index || !out_cov || !out_valid || !on_device(out_index) || !on_device(out_cov) || !on_device(out_valid) ||
         (out_knn_ids && !on_device(out_knn_ids)))
         return reject(FAR_ERR_INVALID, "outputs must be device pointers (out_knn_ids may be NULL)");
-    if (scan_blocks((u32)n) + 2 > kPartialWords)
+    if (2 * scan_blocks((u32)n) + 2 > kPartialWords)
         return reject(FAR_ERR_INVALID, "internal: static scratch layout too small");
 
     // Set-up, once per device with that device current: resolve the array's device address.
