@@ -116,11 +116,6 @@ __device__ __forceinline__ void se3_exp_dev(const double (&xi)[6], double (&E)[1
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 __device__ __forceinline__ u32 warp_sum_u(u32 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -910,12 +905,18 @@ cudaError_t gn_graph_build(const GnArgs* d_args, u32 n_upper, int tpp, bool prec
         lp.kernelParams = largs;
         e = cudaGraphAddKernelNode(&lin, body, nullptr, 0, &lp);
         void* sargs[] = {(void*)&ap, (void*)&grid, (void*)&loop};
-        cudaKernelNodeParams sp = {};
-        sp.func = (void*)k_gn_solve_dev;
-        sp.gridDim = dim3(1);
-        sp.blockDim = dim3(SOLVE_THREADS);
-        sp.kernelParams = sargs;
-        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&solve, body, &lin, 1, &sp);
+        // programmatic edge: the solve launches while the linearisation runs and waits for it
+        // in pdl_wait(), as the explicit chain does
+        cudaGraphNodeParams sp = {};
+        sp.type = cudaGraphNodeTypeKernel;
+        sp.kernel.func = (void*)k_gn_solve_dev;
+        sp.kernel.gridDim = dim3(1);
+        sp.kernel.blockDim = dim3(SOLVE_THREADS);
+        sp.kernel.kernelParams = sargs;
+        cudaGraphEdgeData ed = {};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&solve, body, &lin, &ed, 1, &sp);
     }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
