@@ -97,61 +97,93 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
 }
 
 // Slot of each point's voxel (inserting new keys), and the point's arrival rank among the
-// points of this batch in that slot (out_rank, from the per-slot counter slot_cnt).
+// points of this batch in that slot (out_rank, from the per-slot counter slot_cnt). The lanes
+// of a warp that found the same slot take their ranks with one atomic (points of a voxel
+// arrive together in scan order).
 __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slots, u32 mask,
                                  u32* __restrict__ out_slot, u32* __restrict__ out_rank, MapCounters* ctr,
                                  u32* __restrict__ slot_cnt) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const u64 key = keys[i];
+    const int lane = threadIdx.x & 31;
     const u32 sentinel = mask + 1u;
-    if (key == KEY_INVALID) {
-        out_slot[i] = sentinel;
-        return;
-    }
-    int kx, ky, kz;
-    unpack_key(key, kx, ky, kz);
-    u32 h = hash_key(kx, ky, kz) & mask;
-    for (u32 p = 0; p <= mask; ++p) {
-        const u64 k = *reinterpret_cast<volatile u64*>(&slots[h].key);
-        if (k == key) {
-            out_slot[i] = h;
-            out_rank[i] = atomicAdd(&slot_cnt[h], 1u);
-            atomicMax(&ctr->max_probe, p);
-            return;
-        }
-        if (k == KEY_EMPTY) {
-            const u64 old = atomicCAS(&slots[h].key, KEY_EMPTY, key);
-            if (old == KEY_EMPTY || old == key) {
-                out_slot[i] = h;
-                out_rank[i] = atomicAdd(&slot_cnt[h], 1u);
-                atomicMax(&ctr->max_probe, p);
-                return;
+    u32 found = sentinel, probes = 0;
+    const u64 key = i < n ? keys[i] : KEY_INVALID;
+    if (key != KEY_INVALID) {
+        int kx, ky, kz;
+        unpack_key(key, kx, ky, kz);
+        u32 h = hash_key(kx, ky, kz) & mask;
+        for (u32 p = 0; p <= mask; ++p) {
+            const u64 k = *reinterpret_cast<volatile u64*>(&slots[h].key);
+            if (k == key) {
+                found = h;
+                probes = p;
+                break;
             }
+            if (k == KEY_EMPTY) {
+                const u64 old = atomicCAS(&slots[h].key, KEY_EMPTY, key);
+                if (old == KEY_EMPTY || old == key) {
+                    found = h;
+                    probes = p;
+                    break;
+                }
+            }
+            h = (h + 1u) & mask;
         }
-        h = (h + 1u) & mask;
+        if (found == sentinel) {
+            atomicOr(&ctr->err, (u32)ERR_TABLE_FULL);
+            atomicAdd(&ctr->n_dropped, 1u);
+        }
     }
-    out_slot[i] = sentinel;
-    atomicOr(&ctr->err, (u32)ERR_TABLE_FULL);
-    atomicAdd(&ctr->n_dropped, 1u);
+    const u32 peers = __match_any_sync(0xffffffffu, found);
+    const int leader = __ffs(peers) - 1;
+    u32 base = 0;
+    if (lane == leader && found != sentinel) base = atomicAdd(&slot_cnt[found], (u32)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const u32 pmax = __reduce_max_sync(0xffffffffu, probes);
+    if (lane == 0 && pmax > 0) atomicMax(&ctr->max_probe, pmax);
+    if (i >= n) return;
+    out_slot[i] = found;
+    if (found != sentinel) out_rank[i] = base + (u32)__popc(peers & ((1u << lane) - 1u));
 }
 
 // Groups: the first point of each slot (rank 0) opens the slot's group, a contiguous range
-// of its size taken from the running total, and records it under a group index.
+// of its size taken from the running total, and records it under a group index. The heads of
+// a warp take their group indices and ranges with one atomic each.
 __global__ void k_group_alloc(const u32* __restrict__ slot_of, const u32* __restrict__ rank, u32 n, u32 sentinel,
                               const u32* __restrict__ slot_cnt, u32* __restrict__ slot_base, u32* __restrict__ scal,
                               u32* __restrict__ gstart, u32* __restrict__ gsize, u32* __restrict__ gslot) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const u32 h = slot_of[i];
-    if (h == sentinel || rank[i] != 0u) return;
-    const u32 size = slot_cnt[h];
-    const u32 g = atomicAdd(&scal[SCAL_NGROUPS], 1u);
-    const u32 base = atomicAdd(&scal[SCAL_NVALID], size);
+    const int lane = threadIdx.x & 31;
+    u32 h = sentinel;
+    bool head = false;
+    if (i < n) {
+        h = slot_of[i];
+        head = h != sentinel && rank[i] == 0u;
+    }
+    const u32 size = head ? slot_cnt[h] : 0u;
+    const u32 heads = __ballot_sync(0xffffffffu, head);
+    if (heads == 0u) return;
+    u32 incl = size;   // inclusive prefix of the sizes over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+    u32 g0 = 0, b0 = 0;
+    if (lane == 0) {
+        g0 = atomicAdd(&scal[SCAL_NGROUPS], (u32)__popc(heads));
+        b0 = atomicAdd(&scal[SCAL_NVALID], total);
+    }
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (!head) return;
+    const u32 g = g0 + (u32)__popc(heads & ((1u << lane) - 1u));
+    const u32 base = b0 + incl - size;
     slot_base[h] = base;
     gstart[g] = base;
     gsize[g] = size;
