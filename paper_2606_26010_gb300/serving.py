@@ -12,6 +12,7 @@ queueing and processing. All arithmetic runs in libfar.so.
 from __future__ import annotations
 
 import collections
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -177,7 +178,21 @@ class Server:
 
     def run(self, vehicles: list, duration_s: float):
         """Discrete-event loop: admissions, departures and arrivals up to the current time, then a
-        batched step if any vehicle has a pending scan, else a jump to the next event."""
+        batched step if any vehicle has a pending scan, else a jump to the next event. Python's
+        cyclic garbage collector is paused while serving (objects made so far are frozen out of
+        it), so no collection pause lands inside a step; it is restored at the end."""
+        was_enabled = gc.isenabled()
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        try:
+            return self._run(vehicles, duration_s)
+        finally:
+            gc.unfreeze()
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, vehicles: list, duration_s: float):
         joins = sorted(vehicles, key=lambda v: v.spec.join_s)
         ji = 0
         t = 0.0
