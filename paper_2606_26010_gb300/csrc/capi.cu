@@ -898,6 +898,7 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
     far_status result = FAR_OK;
     if (r.status == 5) result = fail(FAR_ERR_DEGENERATE, "registration degenerate (%u correspondences)", r.n_corr);
     if (r.status == 6) result = fail(FAR_ERR_TIMEOUT, "registration exceeded its time budget after %u iterations", r.iters);
+    if (r.status == 7) result = fail(FAR_ERR_CUDA, "internal: the Gauss-Newton loop ran past its iteration limit");
     if (stats) {
         stats->iters = r.iters;
         stats->n_src = r.n_src;
@@ -973,6 +974,7 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     if (r.status == 5) res = fail(FAR_ERR_DEGENERATE, "registration degenerate (%u correspondences); scan not inserted",
                                   r.n_corr);
     if (r.status == 6) res = fail(FAR_ERR_TIMEOUT, "registration exceeded its time budget; scan not inserted");
+    if (r.status == 7) res = fail(FAR_ERR_CUDA, "internal: the Gauss-Newton loop ran past its iteration limit");
     if (result) {
         result->reg.iters = r.iters;
         result->reg.n_src = r.n_src;

@@ -129,9 +129,11 @@ struct RegState {
     u32 n_corr, n_p2p;
     u32 iters;           // updates applied
     u32 converged;
-    u32 status;          // 0 ok, 5 degenerate
+    u32 status;          // 0 ok, 5 degenerate, 6 time budget, 7 graph loop overran (internal)
     u32 done;            // stop flag read at kernel entry
     u32 block_counter;   // last-block detection
+    u32 trips;           // executions of the graph loop's body (bounds the loop)
+    double red[32];      // the reduced values of the last linearisation (one per solve block)
     u32 n_src;           // source points of this registration
     unsigned long long t_start_ns;  // %globaltimer at the start of the registration
 };

@@ -446,56 +446,10 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(
     gn_lin_block<TPP, PREC>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
 
-// Solve half: one block reduces the block partials in a fixed order (FP64), then one
-// thread solves H xi = -g by Cholesky and applies T <- exp(xi) T (Eq. 6) in FP64.
-constexpr int SOLVE_THREADS = 256;   // 8 warps; the single solving thread keeps up to 255 registers
-__device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
-    __shared__ double tot[NPART];
-    __shared__ u32 s_flag;
+// The single solving thread: H and g from the reduced values, Cholesky, SE(3) update (Eq. 6),
+// convergence and time checks, bookkeeping. T: the pose at the start of the launch.
+__device__ __forceinline__ void gn_solve_serial(const GnArgs& a, const double* tot, const double (&T)[12]) {
     RegState* st = a.st;
-    // the stop flag, the pose and the partials are loaded together: when the flag is set the
-    // loaded values are simply not used (the partial buffer is always allocated)
-    double T[12];
-    if (threadIdx.x == 0) {
-        s_flag = *reinterpret_cast<volatile u32*>(&st->done);
-#pragma unroll
-        for (int j = 0; j < 12; ++j) T[j] = st->T[j];
-    }
-    {
-        // warp w reduces values w, w + 8, w + 16, w + 24 at once: lane l sums blocks l, l + 32, ...
-        // into two chains per value (eight loads per step, unrolled so that 32 are in flight),
-        // then a fixed shuffle tree; the order never depends on timing
-        constexpr int W = SOLVE_THREADS / 32, VPW = NPART / W;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const double* col = a.partials + (size_t)w * nblocks;
-        const size_t vs = (size_t)W * nblocks;
-        double c0[VPW], c1[VPW];
-#pragma unroll
-        for (int j = 0; j < VPW; ++j) c0[j] = c1[j] = 0.0;
-        u32 b = lane;
-#pragma unroll 4
-        for (; b + 32 < nblocks; b += 64) {
-#pragma unroll
-            for (int j = 0; j < VPW; ++j) {
-                c0[j] += col[j * vs + b];
-                c1[j] += col[j * vs + b + 32];
-            }
-        }
-        if (b < nblocks) {
-#pragma unroll
-            for (int j = 0; j < VPW; ++j) c0[j] += col[j * vs + b];
-        }
-#pragma unroll
-        for (int j = 0; j < VPW; ++j) {
-            double s = c0[j] + c1[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) tot[w + j * W] = s;
-        }
-    }
-    __syncthreads();
-    if (s_flag || threadIdx.x != 0) return;
-
     double H[6][6], g[6];
 #pragma unroll
     for (int r = 0, idx = 0; r < 6; ++r)
@@ -565,18 +519,71 @@ __device__ __forceinline__ void gn_solve_block(const GnArgs& a, u32 nblocks) {
     st->n_p2p = (u32)tot[29];
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve(GnArgs a, u32 nblocks) {
-    pdl_wait();
-    pdl_trigger();
-    gn_solve_block(a, nblocks);
+// Solve half of a Gauss-Newton iteration. Value v of the block partials (col = partials +
+// v * nblocks) is summed in FP64 by one warp in a fixed order: lane l adds blocks l, l + 64, ...
+// and l + 32, l + 96, ... in two chains, then the two chains, then a fixed shuffle tree (every
+// lane ends with the same sum). The order depends neither on timing nor on the kernel that runs
+// it, so a problem's result is the same alone and in a batch.
+__device__ __forceinline__ double warp_reduce_value(const double* __restrict__ col, u32 nblocks, int lane) {
+    double c0 = 0.0, c1 = 0.0;
+    u32 b = lane;
+#pragma unroll 4
+    for (; b + 32 < nblocks; b += 64) {
+        c0 += __ldcg(col + b);
+        c1 += __ldcg(col + b + 32);
+    }
+    if (b < nblocks) c0 += __ldcg(col + b);
+    double s = c0 + c1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
-// Batched solve: block p reduces and solves problem p.
-__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_batch(const BatchProblem* __restrict__ probs) {
+// Solve half of one registration over NPART one-warp blocks (the FP64 rate of a single SM
+// would otherwise bound the reduction): block v reduces value v into st->red[v]; every block
+// then takes a ticket, and the block that takes the last one (all values written and fenced
+// before their tickets) solves. Returns true in that block.
+__device__ __forceinline__ bool gn_solve_wide(const GnArgs& a, u32 nblocks) {
+    static_assert(NPART == 32, "one lane per reduced value in the solving block");
+    RegState* st = a.st;
+    const int lane = threadIdx.x & 31;
+    const double v = warp_reduce_value(a.partials + (size_t)blockIdx.x * nblocks, nblocks, lane);
+    __shared__ u32 s_last;
+    __shared__ double tot[NPART];
+    if (lane == 0) {
+        st->red[blockIdx.x] = v;
+        __threadfence();
+        const u32 t = atomicAdd(&st->block_counter, 1u);
+        s_last = t + 1u == gridDim.x;
+        if (s_last) st->block_counter = 0u;   // ready for the next launch
+    }
+    __syncwarp();
+    if (!s_last) return false;
+    __threadfence();
+    tot[lane] = __ldcg(&st->red[lane]);
+    __syncwarp();
+    if (lane == 0 && *reinterpret_cast<volatile u32*>(&st->done) == 0u) {
+        double T[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) T[j] = st->T[j];
+        gn_solve_serial(a, tot, T);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32) k_gn_solve(GnArgs a, u32 nblocks) {
     pdl_wait();
     pdl_trigger();
-    const BatchProblem& p = probs[blockIdx.x];
-    gn_solve_block(p.args, p.nblocks);
+    gn_solve_wide(a, nblocks);
+}
+
+// Batched solve: blocks (v, p) reduce value v of problem p; the last of problem p's blocks
+// solves it (the same arithmetic as the single-problem solve).
+__global__ void __launch_bounds__(32) k_gn_solve_batch(const BatchProblem* __restrict__ probs) {
+    pdl_wait();
+    pdl_trigger();
+    const BatchProblem& p = probs[blockIdx.y];
+    gn_solve_wide(p.args, p.nblocks);
 }
 
 // Kernels of the graph loop: the arguments come from device memory.
@@ -587,15 +594,25 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_dev(co
     gn_lin_block<TPP, PREC>(*ap, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) k_gn_solve_dev(const GnArgs* __restrict__ ap, u32 nblocks,
-                                                                cudaGraphConditionalHandle loop) {
+__global__ void __launch_bounds__(32) k_gn_solve_dev(const GnArgs* __restrict__ ap, u32 nblocks,
+                                                    cudaGraphConditionalHandle loop) {
     pdl_wait();
     pdl_trigger();
-    gn_solve_block(*ap, nblocks);
-    if (threadIdx.x == 0) {
-        const RegState* st = ap->st;
+    const GnArgs& a = *ap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the body runs at most max_iters times (every run but a final one applies an update);
+        // past that bound the loop ends with an internal error instead of running on
+        RegState* st = a.st;
+        if (st->trips++ > a.max_iters) {
+            st->status = 7;
+            st->done = 1;
+            cudaGraphSetConditional(loop, 0u);
+        }
+    }
+    if (gn_solve_wide(a, nblocks) && threadIdx.x == 0) {
+        const RegState* st = a.st;
         const bool stop = *reinterpret_cast<const volatile u32*>(&st->done) != 0u ||
-                          *reinterpret_cast<const volatile u32*>(&st->iters) >= ap->max_iters;
+                          *reinterpret_cast<const volatile u32*>(&st->iters) >= a.max_iters;
         cudaGraphSetConditional(loop, stop ? 0u : 1u);
     }
 }
@@ -617,6 +634,7 @@ __global__ void k_gn_begin_batch(const BatchProblem* __restrict__ probs, u32 npr
     st->xi_norm2 = 0.0;
     st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
     st->block_counter = 0;
+    st->trips = 0;
     st->n_src = *probs[p].args.n_src;
     st->t_start_ns = globaltimer_ns();
 }
@@ -646,6 +664,7 @@ __global__ void k_gn_begin(RegState* st, Pose16 init, const u32* n_src) {
     st->xi_norm2 = 0.0;
     st->n_corr = st->n_p2p = st->iters = st->converged = st->status = st->done = 0;
     st->block_counter = 0;
+    st->trips = 0;
     st->t_start_ns = globaltimer_ns();
 }
 
@@ -822,7 +841,7 @@ cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblo
 }
 
 cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s) {
-    FAR_LAUNCH_PDL(k_gn_solve, 1, SOLVE_THREADS, 0, s, a, nblocks);
+    FAR_LAUNCH_PDL(k_gn_solve, NPART, 32, 0, s, a, nblocks);
     return cudaGetLastError();
 }
 
@@ -848,7 +867,7 @@ cudaError_t gn_batch_iteration(const BatchProblem* probs, const u32* block_prob,
                  else FAR_LAUNCH_PDL((k_gn_lin_batch<1, false>), total_blocks, GN_THREADS, 0, s, probs, block_prob);
                  break;
     }
-    FAR_LAUNCH_PDL(k_gn_solve_batch, nprob, SOLVE_THREADS, 0, s, probs);
+    FAR_LAUNCH_PDL(k_gn_solve_batch, dim3(NPART, nprob), 32, 0, s, probs);
     return cudaGetLastError();
 }
 
@@ -910,8 +929,8 @@ cudaError_t gn_graph_build(const GnArgs* d_args, u32 n_upper, int tpp, bool prec
         cudaGraphNodeParams sp = {};
         sp.type = cudaGraphNodeTypeKernel;
         sp.kernel.func = (void*)k_gn_solve_dev;
-        sp.kernel.gridDim = dim3(1);
-        sp.kernel.blockDim = dim3(SOLVE_THREADS);
+        sp.kernel.gridDim = dim3(NPART);
+        sp.kernel.blockDim = dim3(32);
         sp.kernel.kernelParams = sargs;
         cudaGraphEdgeData ed = {};
         ed.from_port = cudaGraphKernelNodePortProgrammatic;
