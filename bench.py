@@ -278,6 +278,7 @@ def run_ours(args):
     # ---- profiled pass over the same scans (stage times, per-launch k_gn_lin durations for the
     # roofline): the library records CUDA events between its kernels on the map's stream
     gn_ms, gn_bytes, gn_launches, stage_acc, ins_acc = [], [], [], {}, {}
+    knn_ms, knn_bytes = [], []
     mp = make_map()
     mp.set_profiling(True)
     thr_p = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
@@ -286,15 +287,21 @@ def run_ours(args):
         for t in range(1, n_total):
             if t > args.warmup:
                 flush.zero_()
-            est_p, _ = step(mp, thr_p, t, est_p, dev[t])
+            est_p, res_p = step(mp, thr_p, t, est_p, dev[t])
             if t <= args.warmup:
                 continue
             st = mp.stage_times()
             for k_, v_ in st.items():
                 stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
-            for w_, parts in mp.insert_times().items():
+            ins_t = mp.insert_times()
+            for w_, parts in ins_t.items():
                 for k_, v_ in parts.items():
                     ins_acc.setdefault(w_, {})[k_] = ins_acc.get(w_, {}).get(k_, 0.0) + v_
+            # source covariances (k_knn_cov on the scan-local map, with k_make_sources before it):
+            # each source is read as a query and once as a candidate (the local map holds exactly
+            # the sources), and its covariance is written: 16 + 16 + 32 B
+            knn_ms.append(ins_t["sources"]["cov_ms"])
+            knn_bytes.append(64.0 * res_p["n_src"])
             n_src, u_v, p_touched = mp.gn_footprint()
             nblk = min((scans[t].shape[0] * 4 + 127) // 128, 152 * 5)
             # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B; 12 + 12 + 1
@@ -327,6 +334,16 @@ def run_ours(args):
                 "mean_launch_us": round(1e3 * tot_t / max(1, sum(gn_launches)) * 1e3, 2),
                 "launches": int(sum(gn_launches)),
                 "measured_in": "profiled pass over the same scans (per-launch CUDA events on the map's stream)"}
+
+    knn_t = sum(knn_ms) / 1e3
+    knn_achieved = sum(knn_bytes) / knn_t / 1e9 if knn_t > 0 else 0.0
+    roofline_knn = {"bound": "hbm", "achieved": round(knn_achieved, 2), "peak": peak, "unit": "GB/s",
+                    "frac": round(knn_achieved / peak, 5), "traffic": None,
+                    "kernel": "k_knn_cov<5> (source covariances, the largest share of the launch list)",
+                    "algorithmic_bytes_per_launch": round(sum(knn_bytes) / max(1, len(knn_bytes))),
+                    "mean_launch_us": round(1e3 * knn_t / max(1, len(knn_ms)) * 1e3, 2), "launches": len(knn_ms),
+                    "measured_in": "profiled pass: events around k_make_sources + k_knn_cov of each scan; bytes "
+                                   "exclude the hash slots (a lower bound)"}
 
     # ---- end-to-end pass through the public API from pinned host memory
     e2e = None
@@ -390,6 +407,7 @@ def run_ours(args):
                                           "median_rot_rad": round(float(np.median([e[1] for e in rpe])), 7)},
         "map_points_end": int(results[-1]["n_points"]),
         "roofline": roofline,
+        "roofline_knn_cov": roofline_knn,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches_in_steps),
