@@ -103,6 +103,7 @@ struct far_map {
     cudaEvent_t src_end = nullptr;
     bool ins_used[2] = {false, false};
     far_insert_times ins_last[2] = {};
+    bool local_dirty = false;        // the scan-local map may hold a scan (see build_sources)
 };
 
 namespace {
@@ -439,12 +440,18 @@ Pose12 pose12(const double* T) {
 }
 
 // Scan-local map + Eq. 1 source covariances (a2, a3) from s.in4[0..n).
+// The scan-local map starts empty (cleared at creation) and is emptied again after each use
+// by resetting only the slots the insert used; a build that stopped half-way leaves it dirty,
+// and the next one clears it in full.
 far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
-    CK(map_clear(m->local, m->stream));
+    if (m->local_dirty) CK(map_clear(m->local, m->stream));
+    m->local_dirty = true;
     InsertCfg cfg;
     CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream, DevicePose(), insert_marks(m, 0)));
     CK(make_sources(m->local, m->s, n, knn_ids, m->stream));
     if (m->profiling) cudaEventRecord(m->src_end, m->stream);
+    CK(map_local_reset(m->local, m->s, n, m->stream));
+    m->local_dirty = false;
     return FAR_OK;
 }
 

@@ -1225,6 +1225,34 @@ cudaError_t map_clear(DeviceMap& m, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Empty again the slots a scan-local insert used (its group slots: every slot that received a
+// key) and reset the counters. The scan-local map never evicts, so its bucket ring is still the
+// identity and only the head and tail need resetting.
+__global__ void k_local_reset(Slot* slots, const u32* __restrict__ gslot, const u32* __restrict__ scal,
+                              MapCounters* ctr, u32 max_buckets) {
+    pdl_wait();
+    pdl_trigger();
+    const u32 ng = scal[SCAL_NGROUPS];
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        MapCounters c{};
+        c.ring_tail = max_buckets;
+        *ctr = c;
+    }
+    for (u32 g = t; g < ng; g += gridDim.x * blockDim.x) {
+        Slot* sp = slots + gslot[g];
+        sp->key = KEY_EMPTY;
+        sp->bucket = NO_BUCKET;
+        sp->count = 0xFFFFFFFFu;   // as the cleared table holds
+    }
+}
+
+cudaError_t map_local_reset(DeviceMap& m, const Scratch& s, u32 n, cudaStream_t st) {
+    FAR_LAUNCH(k_local_reset, max(1u, min(blocks_for(n), 152u * 8u)), TPB, 0, st, m.slots, s.gslot, s.scal, m.ctr,
+               m.max_buckets);
+    return cudaGetLastError();
+}
+
 cudaError_t map_evict(DeviceMap& m, const double center[3], double radius, cudaStream_t st, const double* dev_pose) {
     FAR_TRY(cudaMemsetAsync(&m.ctr->removed, 0, sizeof(unsigned long long), st));
     const u32 blocks = min(blocks_for(m.cap), 152u * 16u);

@@ -128,6 +128,10 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
                              bool covariances, cudaStream_t st, DevicePose dpose = DevicePose(),
                              const InsertMarks* marks = nullptr);
 
+// Empty the scan-local map m after an insert of n points through scratch s (only the slots that
+// insert used), so that it can serve the next scan without a full clear.
+cudaError_t map_local_reset(DeviceMap& m, const Scratch& s, u32 n, cudaStream_t st);
+
 // Scan-local sources after map_insert_batch on the local map: s.src / s.src_index in
 // voxel-grouped order (s.src[j].w = admission rank), then their covariances from the
 // local map; knn_ids_out rows are indexed by rank.
