@@ -547,7 +547,9 @@ __device__ __forceinline__ bool gn_solve_wide(const GnArgs& a, u32 nblocks) {
     static_assert(NPART == 32, "one lane per reduced value in the solving block");
     RegState* st = a.st;
     const int lane = threadIdx.x & 31;
-    const double v = warp_reduce_value(a.partials + (size_t)blockIdx.x * nblocks, nblocks, lane);
+    // once the stop flag is set a launch only keeps the ticket count (no reduction, no solve)
+    const bool stopped = *reinterpret_cast<volatile u32*>(&st->done) != 0u;
+    const double v = stopped ? 0.0 : warp_reduce_value(a.partials + (size_t)blockIdx.x * nblocks, nblocks, lane);
     __shared__ u32 s_last;
     __shared__ double tot[NPART];
     if (lane == 0) {

@@ -59,8 +59,8 @@ u32 gn_max_blocks(u32 n_upper);   // largest grid gn_grid returns for n_upper po
 // Reset the registration state to `init`; n_src (device, may be null) is recorded in st->n_src.
 cudaError_t gn_begin(RegState* st, const double init[16], const u32* n_src, cudaStream_t s);
 // One Gauss-Newton iteration = k_gn_lin (search, linearisation, block partials) then
-// k_gn_solve (fixed-order FP64 reduction, Cholesky, SE(3) update); both return at entry
-// once the state's stop flag is set.
+// k_gn_solve (fixed-order FP64 reduction over 32 one-warp blocks, then Cholesky and SE(3)
+// update by the last of them); once the state's stop flag is set both skip their work.
 cudaError_t gn_iteration(const GnArgs& a, u32 n_upper, cudaStream_t s);
 cudaError_t gn_linearise(const GnArgs& a, u32 n_upper, cudaStream_t s, u32* nblocks);
 cudaError_t gn_solve(const GnArgs& a, u32 nblocks, cudaStream_t s);

@@ -651,7 +651,7 @@ constexpr int KNN_TPP = 4;
 // (q != null) or m.pts[qpos[r]]; output index is out_pos[r] (map points) or r.
 // With knn_ids, the output row of a query is its rank, taken from q[r].w.
 template <int K>
-__global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __restrict__ q,
+__global__ void __launch_bounds__(TPB, K <= 6 ? 3 : 2) k_knn_cov(MapView m, const float4* __restrict__ q,
                                                  const u32* __restrict__ qpos, u32 n, const u32* __restrict__ n_dev,
                                                  float4* __restrict__ cov_out, const u32* __restrict__ out_pos,
                                                  u32* __restrict__ knn_ids) {
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(TPB) k_knn_cov(MapView m, const float4* __rest
 // map position qpos[r], voxel key qkey[r]) in the frame of each point's tile, kept in FP32
 // in cov_tmp; each valid covariance raises its voxel's exponent.
 template <int K>
-__global__ void __launch_bounds__(TPB) k_knn_cov_tile(MapView m, const u32* __restrict__ qpos,
+__global__ void __launch_bounds__(TPB, K <= 6 ? 3 : 2) k_knn_cov_tile(MapView m, const u32* __restrict__ qpos,
                                                       const u64* __restrict__ qkey, u32 n,
                                                       const u32* __restrict__ n_dev, float4* __restrict__ cov_tmp,
                                                       int* __restrict__ cexp) {

@@ -273,13 +273,44 @@ __device__ __forceinline__ void knn_insert(float d2, u32 id, u32 pos, float (&bd
     }
 }
 
+// The K best of two sorted lists (ascending (d2, id), disjoint candidates) into the first: the
+// K smallest of the union are min(a_i, b_{K-1-i}) (a bitonic sequence), which an odd-even
+// transposition sort puts back in order. Registers only.
+template <int K>
+__device__ __forceinline__ void knn_merge(const float (&od)[K], const u32 (&oi)[K], const u32 (&op)[K], float (&bd)[K],
+                                          u32 (&bid)[K], u32 (&bpos)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int j = K - 1 - i;
+        if (better(od[j], oi[j], bd[i], bid[i])) {
+            bd[i] = od[j];
+            bid[i] = oi[j];
+            bpos[i] = op[j];
+        }
+    }
+#pragma unroll
+    for (int pass = 0; pass < K; ++pass)
+#pragma unroll
+        for (int i = pass & 1; i + 1 < K; i += 2) {
+            const bool sw = better(bd[i + 1], bid[i + 1], bd[i], bid[i]);
+            const float d0 = bd[i], d1 = bd[i + 1];
+            const u32 i0 = bid[i], i1 = bid[i + 1], p0 = bpos[i], p1 = bpos[i + 1];
+            bd[i] = sw ? d1 : d0;
+            bd[i + 1] = sw ? d0 : d1;
+            bid[i] = sw ? i1 : i0;
+            bid[i + 1] = sw ? i0 : i1;
+            bpos[i] = sw ? p1 : p0;
+            bpos[i + 1] = sw ? p0 : p1;
+        }
+}
+
 // K nearest of the query searched by a group of TPP consecutive lanes. Lane sl first scans
 // voxel sl of the order own, faces, edges, corners into its own sorted K best; the group then
 // takes the smallest K-th distance of any lane as its bound (the K best of the union are at
 // least that close), lists the remaining voxels whose box distance does not exceed it
 // (compacted into `list`, at least 27 - TPP bytes of the group's own memory) and scans them
 // TPP at a time, re-testing each against the bound of the round before. The lanes' lists are
-// then merged pairwise, so every lane of the group ends with the K best of the union in
+// then merged pairwise (knn_merge), so every lane of the group ends with the K best of the union in
 // (d2, id) order (the lanes saw disjoint voxels). Returns the number of candidates the group
 // saw, capped at K. Every lane of the warp must call this.
 template <int K, int TPP, bool PREC>
@@ -343,8 +374,7 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
             oi[j] = __shfl_xor_sync(0xffffffffu, bid[j], o);
             op[j] = __shfl_xor_sync(0xffffffffu, bpos[j], o);
         }
-#pragma unroll
-        for (int j = 0; j < K; ++j) knn_insert<K>(od[j], oi[j], op[j], bd, bid, bpos);
+        knn_merge<K>(od, oi, op, bd, bid, bpos);
     }
     return found < K ? found : K;
 }
