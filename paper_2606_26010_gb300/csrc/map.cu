@@ -470,9 +470,9 @@ struct AdmitArgs {
 // lane reads the header of one group (members, slot, bucket, fill, ASMD cap) and opens a bucket for a new voxel. The warp
 // then walks the groups that can still take points. Candidates are walked in input order; a
 // candidate enters while the voxel holds fewer than its cap and no point of the voxel is
-// closer than d_min (FP32 d^2 >= d_min^2). Lanes hold the voxel's points (lane j: points j
-// and j + 32) and test a candidate against all of them at once; windows of 32 candidates
-// are prefetched one per lane.
+// closer than d_min (FP32 d^2 >= d_min^2). The voxel's points sit in the warp's shared buffer;
+// each lane holds one candidate of a window of 32 (in input order) and tests it against them
+// (broadcast reads), then the passing candidates are admitted in input order.
 __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     pdl_wait();
     pdl_trigger();
@@ -487,6 +487,7 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     // N_near once per block (FP64 divisions and square roots are slow on this GPU: each is
     // evaluated by one thread and shared)
     __shared__ double s_near;
+    __shared__ float4 s_vox[TPB / 32][NMAX_LIMIT];   // per warp: the points of the voxel it admits into
     if (threadIdx.x == 0) {
         double nn = (double)a.nmax;
         if (a.cfg.asmd && a.ctr->near_cnt > 0) nn = __ddiv_rn((double)a.ctr->near_sum, (double)a.ctr->near_cnt);
@@ -566,8 +567,12 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
             const u32 cnt0 = __shfl_sync(0xffffffffu, cnt, f);
             u32 c_n = cnt0;
             float4* bp = a.pts + (size_t)w_bucket * a.nmax;
-            float4 e0 = (lane < (int)c_n) ? bp[lane] : far4;
-            float4 e1 = (lane + 32 < (int)c_n) ? bp[lane + 32] : far4;
+            // the voxel's points in the warp's shared buffer (the previous group's readers are done)
+            float4* vp = s_vox[threadIdx.x >> 5];
+            __syncwarp();
+            if (lane < (int)c_n) vp[lane] = bp[lane];
+            if (lane + 32 < (int)c_n) vp[lane + 32] = bp[lane + 32];
+            __syncwarp();
             for (u32 w0 = w_start; w0 < w_end && c_n < w_cap; w0 += 32) {
                 // lane l holds candidate w0 + l and tests it against the points held at window start
                 const u32 i = w0 + lane;
@@ -576,10 +581,8 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
                 const float4 my_c = in_window ? a.world[my_idx] : far4;
                 bool pass = in_window;
                 for (u32 j = 0; j < c_n; ++j) {
-                    const float ex = __shfl_sync(0xffffffffu, j < 32 ? e0.x : e1.x, j & 31u);
-                    const float ey = __shfl_sync(0xffffffffu, j < 32 ? e0.y : e1.y, j & 31u);
-                    const float ez = __shfl_sync(0xffffffffu, j < 32 ? e0.z : e1.z, j & 31u);
-                    pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, ex, ey, ez) >= a.dmin2);
+                    const float4 e = vp[j];   // the same address for every lane: one broadcast read
+                    pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, e.x, e.y, e.z) >= a.dmin2);
                 }
                 // resolve in input order: the first passing lane is admitted, later lanes are
                 // re-tested against it only (earlier lanes already failed against a subset)
@@ -591,12 +594,9 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
                     const float cy = __shfl_sync(0xffffffffu, my_c.y, fl);
                     const float cz = __shfl_sync(0xffffffffu, my_c.z, fl);
                     const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
-                    if (lane == (int)(c_n & 31u)) {
-                        if (c_n < 32) e0 = c;
-                        else e1 = c;
-                    }
                     if (lane == fl) {
                         bp[c_n] = c;
+                        vp[c_n] = c;
                         a.pos[my_idx] = w_bucket * a.nmax + c_n;
                         a.admitted[my_idx] = 1u;
                         a.a_ord[my_idx] = w_ord;
@@ -606,6 +606,7 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
                     if (lane <= fl) pass = false;
                     else if (pass) pass = dist2_rn(my_c.x, my_c.y, my_c.z, cx, cy, cz) >= a.dmin2;
                 }
+                __syncwarp();   // this window's admitted points are visible to the next window
             }
             if (lane == 0) {
                 if (c_n != cnt0) a.slots[w_slot].count = c_n;
