@@ -252,27 +252,6 @@ __device__ __forceinline__ void knn_init(float (&bd)[K], u32 (&bid)[K], u32 (&bp
     }
 }
 
-// Insert (d2, id, pos) into the sorted K best (the candidate bubbles past every worse entry;
-// registers only).
-template <int K>
-__device__ __forceinline__ void knn_insert(float d2, u32 id, u32 pos, float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
-    if (!better(d2, id, bd[K - 1], bid[K - 1])) return;
-    float cd = d2;
-    u32 ci = id, cp = pos;
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const bool sw = better(cd, ci, bd[s], bid[s]);
-        const float td = bd[s];
-        const u32 ti = bid[s], tp = bpos[s];
-        bd[s] = sw ? cd : td;
-        bid[s] = sw ? ci : ti;
-        bpos[s] = sw ? cp : tp;
-        cd = sw ? td : cd;
-        ci = sw ? ti : ci;
-        cp = sw ? tp : cp;
-    }
-}
-
 // The K best of two sorted lists (ascending (d2, id), disjoint candidates) into the first: the
 // K smallest of the union are min(a_i, b_{K-1-i}) (a bitonic sequence), which an odd-even
 // transposition sort puts back in order. Registers only.
@@ -377,17 +356,6 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
         knn_merge<K>(od, oi, op, bd, bid, bpos);
     }
     return found < K ? found : K;
-}
-
-// K nearest of a world-coordinate query of a plain map.
-template <int K>
-__device__ __forceinline__ int knn27(const MapView& m, u32 max_probe, float qx, float qy, float qz,
-                                     float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
-    knn_init<K>(bd, bid, bpos);
-    QFrame<false> f;
-    const int zero[3] = {0, 0, 0};
-    if (!make_qframe<false>(m, qx, qy, qz, zero, f)) return 0;
-    return knn27q<K, false>(m, max_probe, f, bd, bid, bpos);
 }
 
 // Nearest map point of the query over the 27 voxels (smallest (d^2, id)). Voxels whose box
