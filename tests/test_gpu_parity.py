@@ -144,6 +144,23 @@ def test_scan_sources_bit_exact(far, problem1):
         assert_cov_close(a["cov"], b["cov"], b["valid"].astype(bool))
 
 
+def test_scan_local_map_reuse_equals_a_fresh_map(far, problem1):
+    """The scan-local map is emptied after each use by resetting only the slots that scan used;
+    source stages of scans of different sizes (and an empty one) on one map must equal those of
+    a fresh map, bit for bit."""
+    big = synth.TrackSequence(42).scan(0)
+    small = problem1.query
+    g = far.VoxelMap(0.5, 20, 5, max_scan_points=300_000)
+    for scan in (big, small, np.zeros((0, 3), np.float32), small[::3], big):
+        a = g.scan_sources(scan)
+        fresh = far.VoxelMap(0.5, 20, 5, max_scan_points=300_000)
+        b = fresh.scan_sources(scan)
+        fresh.close()
+        for key in ("index", "valid", "knn", "cov"):
+            np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+    g.close()
+
+
 def test_nearest_and_knn_bit_exact(far, problem1, maps1):
     g, o = maps1
     rng = np.random.default_rng(2)
