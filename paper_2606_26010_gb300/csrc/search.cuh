@@ -283,10 +283,38 @@ __device__ __forceinline__ void knn_merge(const float (&od)[K], const u32 (&oi)[
         }
 }
 
+// K-th smallest distance of the union of the group's TPP sorted lists (distances only, every
+// lane of the group ends with it): a butterfly over the lanes keeps the K smallest of each pair,
+// min(a_i, b_{K-1-i}), sorted again by an odd-even transposition sort.
+template <int K, int TPP>
+__device__ __forceinline__ float group_union_kth(const float (&bd)[K]) {
+    float c[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) c[i] = bd[i];
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1) {
+        float p[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) p[i] = __shfl_xor_sync(0xffffffffu, c[i], o);
+#pragma unroll
+        for (int i = 0; i < K; ++i) c[i] = fminf(c[i], p[K - 1 - i]);
+#pragma unroll
+        for (int pass = 0; pass < K; ++pass)
+#pragma unroll
+            for (int i = pass & 1; i + 1 < K; i += 2) {
+                const float lo = fminf(c[i], c[i + 1]), hi = fmaxf(c[i], c[i + 1]);
+                c[i] = lo;
+                c[i + 1] = hi;
+            }
+    }
+    return c[K - 1];
+}
+
 // K nearest of the query searched by a group of TPP consecutive lanes. Lane sl first scans
 // voxel sl of the order own, faces, edges, corners into its own sorted K best; the group then
-// takes the smallest K-th distance of any lane as its bound (the K best of the union are at
-// least that close), lists the remaining voxels whose box distance does not exceed it
+// takes the K-th distance of the union of the lanes' lists as its bound (group_union_kth; the K
+// best of all 27 voxels are at least that close), lists the remaining voxels whose box distance
+// does not exceed it
 // (compacted into `list`, at least 27 - TPP bytes of the group's own memory) and scans them
 // TPP at a time, re-testing each against the bound of the round before. The lanes' lists are
 // then merged pairwise (knn_merge), so every lane of the group ends with the K best of the union in
@@ -313,7 +341,9 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
         return kth;
     };
     if (keyed && sl < 27) scan(sl);
-    float bound = group_bound();
+    // the K best of the union are at least as close as the union's K-th distance, which is finite
+    // once the first round's voxels hold K points together (sparse regions)
+    float bound = group_union_kth<K, TPP>(bd);
     // survivors of the remaining voxels under the group's bound, compacted in voxel order
     u32 mine = 0;
     int k = 0;
@@ -339,7 +369,7 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
             const int v = list[s2];
             if (!(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound)) scan(v);
         }
-        bound = group_bound();
+        bound = fminf(bound, group_bound());
     }
     __syncwarp();
 #pragma unroll
