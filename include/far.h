@@ -80,7 +80,9 @@ typedef struct far_insert_params {
 /* Registration parameters (Sec. III-A.2, Eq. 4-6 and the termination rule). */
 typedef struct far_reg_params {
     uint32_t max_iters;         /* Gauss-Newton iterations at most */
-    double conv_eps;            /* stop when ||xi||_2 <= conv_eps (paper: 5e-3); 0 => run max_iters */
+    double conv_eps;            /* stop when the increment measured at the initial sensor position c,
+                                 * ||[phi; rho + phi x c]||_2 with xi = [phi; rho] about the world
+                                 * origin, is <= conv_eps (paper: 5e-3); 0 => run max_iters */
     float tau;                  /* correspondence distance threshold (m) */
     float kappa;                /* Cauchy kernel scale (Eq. 5) */
     double time_budget_s;       /* wall-clock cap of one registration; <= 0 => none */
@@ -188,17 +190,22 @@ far_status far_scan_sources(far_map* map, const float* xyz, uint64_t n, uint32_t
  * (the origin; precision_mode 1: 50 floor(t / 50) of the pose's translation), IRLS Cauchy weights
  * w = 1 / (1 + e^2 / kappa^2), e^2 = d^T M d, M = (Sigma_r + R Sigma_s R^T)^-1
  * or I when either covariance is invalid. out_corr[n_src] (may be NULL) receives
- * the map id matched by each source point or -1. Host outputs.
+ * the map id matched by each source point or -1. The search query of a source
+ * point s is the FP32 chain fma(R_i0, s_0, fma(R_i1, s_1, fma(R_i2, s_2, t_i)))
+ * of the pose rounded once to FP32 (translation taken relative to A), so the
+ * matches of a pose are one exact answer. threads_per_point as in far_reg_params
+ * (the lanes that search one point; the matches do not depend on it). Host outputs.
  */
 far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, const double pose[16],
-                         float tau, float kappa, double out_H[36], double out_g[6], int32_t* out_corr,
-                         far_reg_stats* stats);
+                         float tau, float kappa, uint32_t threads_per_point, double out_H[36], double out_g[6],
+                         int32_t* out_corr, far_reg_stats* stats);
 
 /*
  * Register a scan against the map (Sec. III-A.2): scan-local downsampling and
  * covariances, then Gauss-Newton iterations from `init_pose`, each solving
  * H xi = -g by FP64 Cholesky and applying T <- exp(xi) T (Eq. 6), until
- * ||xi|| <= conv_eps or max_iters. out_cov (may be NULL) receives H^-1 of the
+ * the increment at the initial sensor position is <= conv_eps (see
+ * far_reg_params) or max_iters. out_cov (may be NULL) receives H^-1 of the
  * last linearisation. Returns FAR_ERR_DEGENERATE (pose = last good estimate)
  * when fewer than 6 correspondences remain or H is not positive definite.
  */
@@ -268,18 +275,23 @@ far_status far_batch_process(far_batch* batch, const float* const* xyz, const ui
  * embedded or safety partition, a memory-capped client of a shared GPU server),
  * or a thread that must not allocate while other threads capture CUDA graphs -
  * and therefore cannot create a far_map. It runs the same kernels (scan-local
- * downsampling with the spacing rule, then Eq. 1 covariances from k neighbours)
- * on one ~8 MB file-scope device array that every GPU loading the library keeps
+ * downsampling with the spacing rule, then the covariance of every kept point
+ * from its k nearest kept neighbours, regularised as far_scan_sources does) on
+ * one ~8 MB file-scope device array that every GPU loading the library keeps
  * until the process exits. Limits: n <= 16384 points, max_pts_per_voxel <= 20,
  * k_cov <= 16; larger sizes return FAR_ERR_INVALID with a message.
- * Inputs and outputs are DEVICE pointers owned by the caller (outputs have room
- * for n entries: index[n], cov[6 n], valid[n], knn_ids[k n] or NULL); n_src is
- * host memory. Work runs on `cuda_stream`; the call synchronises it.
+ * Inputs and outputs are DEVICE pointers of the current device (or managed
+ * memory) owned by the caller; memory of another GPU returns FAR_ERR_INVALID.
+ * Outputs have room for n entries: index[n], cov[6 n], valid[n], knn_ids[k n]
+ * or NULL; n_src is host memory. Work runs on `cuda_stream`; the call
+ * synchronises it.
  * The first call on a device resolves the array's address (cudaGetSymbolAddress)
- * for that device; make that first call before any stream capture. Every call
- * reuses the same array and resets what must start at zero, so calls whose GPU
- * work overlaps (other streams, other host threads, one device) race and must be
- * serialised by the caller.
+ * for that device with it current, and the address is kept for the life of the
+ * process: make that first call before any stream capture, and do not reset the
+ * device (cudaDeviceReset) after it. Every call reuses the same array and first
+ * clears what must start at zero (also after a call that failed half-way), so
+ * calls whose GPU work overlaps (other streams, other host threads, one device)
+ * race and must be serialised by the caller.
  */
 far_status far_scan_sources_static(const float* xyz, uint64_t n, uint32_t stride_bytes, float voxel_size,
                                    uint32_t max_pts_per_voxel, uint32_t k_cov, float min_spacing, void* cuda_stream,

@@ -29,15 +29,40 @@
 // (spacing, candidate order) are evaluated on coordinates relative to a tile
 // origin instead of the world origin; Gauss-Newton is linearised about an
 // anchor (the tile corner of the initial position) instead of the world origin.
+//
+// Threads (CPU-baseline timing only): om_set_threads(n) splits the per-point loops
+// (scan-local covariances, added-point covariances, linearisation) into n fixed
+// contiguous chunks run on std::threads; the linearisation sums each chunk in order and
+// adds the chunk sums in chunk order, so a run is deterministic for a given n, and n = 1
+// is exactly the sequential code. Map inserts stay sequential (admission is ordered).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
 namespace {
+
+int g_threads = 1;
+
+// Run fn(chunk, begin, end) over [0, n) in g_threads fixed contiguous chunks (chunk c covers
+// [c n / T, (c + 1) n / T)); one thread runs everything on the caller's thread.
+template <class F>
+void parallel_chunks(size_t n, int chunks, F fn) {
+    if (chunks <= 1 || n < 2) {
+        fn(0, (size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int c = 0; c < chunks; ++c) {
+        const size_t b = n * (size_t)c / (size_t)chunks, e = n * (size_t)(c + 1) / (size_t)chunks;
+        pool.emplace_back([&fn, c, b, e]() { fn(c, b, e); });
+    }
+    for (std::thread& t : pool) t.join();
+}
 
 // ------------------------------------------------------------------ voxel keys
 // Key reading: k = floor(x * (1/v)) per axis, the product rounded to FP32, with
@@ -549,22 +574,24 @@ InsertResult map_insert(OracleMap& m, const float* xyz, int64_t n, const double*
 // Sec. III-A.3: covariances are computed for the added points only, against the
 // whole updated map; existing points keep theirs.
 void added_covariances(OracleMap& m, InsertResult& res) {
-    std::vector<const MapPoint*> nb;
     std::vector<double> covs(6 * res.added.size());
     std::vector<int> valid(res.added.size());
-    for (size_t i = 0; i < res.added.size(); ++i) {
-        const MapPoint* p = res.added[i].second;
-        Frame fr;
-        if (m.prec) {
-            fr.tv = m.tv;
-            std::memcpy(fr.f, p->tile, sizeof(fr.f));
+    parallel_chunks(res.added.size(), g_threads, [&](int, size_t b, size_t e) {
+        std::vector<const MapPoint*> nb;
+        for (size_t i = b; i < e; ++i) {
+            const MapPoint* p = res.added[i].second;
+            Frame fr;
+            if (m.prec) {
+                fr.tv = m.tv;
+                std::memcpy(fr.f, p->tile, sizeof(fr.f));
+            }
+            // the query is the point itself, centred on its own voxel, in the frame of its tile
+            int found = knn27_at(m, res.added[i].first, p->p, fr, m.k, &nb);
+            valid[i] = (found >= m.k) ? 1 : 0;
+            if (valid[i]) covariance_eq1(nb, &covs[6 * i]);
+            else std::fill(&covs[6 * i], &covs[6 * i] + 6, 0.0);
         }
-        // the query is the point itself, centred on its own voxel, in the frame of its tile
-        int found = knn27_at(m, res.added[i].first, p->p, fr, m.k, &nb);
-        valid[i] = (found >= m.k) ? 1 : 0;
-        if (valid[i]) covariance_eq1(nb, &covs[6 * i]);
-        else std::fill(&covs[6 * i], &covs[6 * i] + 6, 0.0);
-    }
+    });
     for (size_t i = 0; i < res.added.size(); ++i) {
         std::memcpy(res.added[i].second->cov, &covs[6 * i], 6 * sizeof(double));
         res.added[i].second->valid = valid[i];
@@ -592,25 +619,26 @@ std::vector<SourcePoint> scan_local_sources(const float* xyz, int64_t n, float v
     local.dmin2 = dmin2;
     InsertResult ins = map_insert(local, xyz, n, nullptr, 0, 0.0, 1.0);
     // ids are the admission rank, which increases with the input index
-    std::vector<SourcePoint> src;
+    std::vector<SourcePoint> src(local.next_id);
     std::vector<const MapPoint*> by_id(local.next_id, nullptr);
     for (const auto& kv : local.vox)
         for (const MapPoint& p : kv.second.pts) by_id[p.id] = &p;
-    std::vector<const MapPoint*> nb;
     if (knn_ids) knn_ids->assign((size_t)local.next_id * (size_t)k, 0xFFFFFFFFu);
-    for (uint32_t id = 0; id < local.next_id; ++id) {
-        SourcePoint sp;
-        const MapPoint* p = by_id[id];
-        for (int a = 0; a < 3; ++a) { sp.sf[a] = p->p[a]; sp.s[a] = (double)p->p[a]; }
-        sp.index = ins.admitted_index[id];
-        int found = knn27(local, p->p, k, &nb);
-        if (knn_ids)
-            for (int j = 0; j < found; ++j) (*knn_ids)[(size_t)id * k + j] = nb[j]->id;
-        sp.valid = (found >= k) ? 1 : 0;
-        if (sp.valid) covariance_eq1(nb, sp.cov);
-        else std::fill(sp.cov, sp.cov + 6, 0.0);
-        src.push_back(sp);
-    }
+    parallel_chunks(local.next_id, g_threads, [&](int, size_t b, size_t e) {
+        std::vector<const MapPoint*> nb;
+        for (size_t id = b; id < e; ++id) {
+            SourcePoint& sp = src[id];
+            const MapPoint* p = by_id[id];
+            for (int a = 0; a < 3; ++a) { sp.sf[a] = p->p[a]; sp.s[a] = (double)p->p[a]; }
+            sp.index = ins.admitted_index[id];
+            int found = knn27(local, p->p, k, &nb);
+            if (knn_ids)
+                for (int j = 0; j < found; ++j) (*knn_ids)[id * k + j] = nb[j]->id;
+            sp.valid = (found >= k) ? 1 : 0;
+            if (sp.valid) covariance_eq1(nb, sp.cov);
+            else std::fill(sp.cov, sp.cov + 6, 0.0);
+        }
+    });
     return src;
 }
 
@@ -701,8 +729,9 @@ struct LinResult {
 //   Left perturbation T <- exp(xi) T, xi = [phi; rho]: J = [[q]x, -I], with q taken
 //   relative to the anchor A (the origin for the plain map, see anchor_frame).
 //   H = sum w J^T M J, g = sum w J^T M d.
-LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, const double T[16], const Frame& fr,
-                    const double A[3], float tau2, double kappa, int32_t* corr_out) {
+LinResult linearize_range(const OracleMap& m, const std::vector<SourcePoint>& src, size_t n_begin, size_t n_end,
+                          const double T[16], const Frame& fr, const double A[3], float tau2, double kappa,
+                          int32_t* corr_out) {
     LinResult L;
     std::memset(L.H, 0, sizeof(L.H));
     std::memset(L.g, 0, sizeof(L.g));
@@ -712,12 +741,24 @@ LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, con
         t[i] = T[4 * i + 3];
     }
     double k2 = kappa * kappa;
-    for (size_t n = 0; n < src.size(); ++n) {
+    // The search query is an FP32 quantity (the paper registers in float32, Sec. III-A.2): the
+    // pose rounded once to FP32 (rotation entries, and the translation relative to the anchor
+    // A), applied to the FP32 source point as the chain fma(R_i0, s0, fma(R_i1, s1,
+    // fma(R_i2, s2, t_i))) with one rounding per fused multiply-add. The residual and the
+    // Jacobian below use the FP64 transform.
+    float Rf[3][3], tf[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rf[i][j] = (float)R[i][j];
+        tf[i] = (float)(t[i] - A[i]);
+    }
+    for (size_t n = n_begin; n < n_end; ++n) {
         const SourcePoint& sp = src[n];
         double q[3];
         for (int i = 0; i < 3; ++i) q[i] = R[i][0] * sp.s[0] + R[i][1] * sp.s[1] + R[i][2] * sp.s[2] + t[i];  // Eq. 2 / Eq. 6
         // FP32 query in the frame of the anchor (the world frame for the plain map)
-        float qf[3] = {(float)(q[0] - A[0]), (float)(q[1] - A[1]), (float)(q[2] - A[2])};
+        float qf[3];
+        for (int i = 0; i < 3; ++i)
+            qf[i] = std::fmaf(Rf[i][0], sp.sf[0], std::fmaf(Rf[i][1], sp.sf[1], std::fmaf(Rf[i][2], sp.sf[2], tf[i])));
         float d2;
         const MapPoint* nn = nearest27_frame(m, qf, fr, &d2);
         if (corr_out) corr_out[n] = -1;
@@ -773,6 +814,26 @@ LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, con
         L.chi2 += 0.5 * k2 * std::log(1.0 + e2 / k2);  // Eq. 5 with e^2 = d^T M d
         L.n_corr += 1;
         if (p2p) L.n_p2p += 1;
+    }
+    return L;
+}
+
+// The linearisation over all sources: per-chunk sums (one chunk with one thread), added in
+// chunk order.
+LinResult linearize(const OracleMap& m, const std::vector<SourcePoint>& src, const double T[16], const Frame& fr,
+                    const double A[3], float tau2, double kappa, int32_t* corr_out) {
+    if (g_threads <= 1) return linearize_range(m, src, 0, src.size(), T, fr, A, tau2, kappa, corr_out);
+    std::vector<LinResult> part(g_threads);
+    parallel_chunks(src.size(), g_threads, [&](int c, size_t b, size_t e) {
+        part[c] = linearize_range(m, src, b, e, T, fr, A, tau2, kappa, corr_out);
+    });
+    LinResult L = part[0];
+    for (int c = 1; c < g_threads; ++c) {
+        for (int i = 0; i < 36; ++i) L.H[i] += part[c].H[i];
+        for (int i = 0; i < 6; ++i) L.g[i] += part[c].g[i];
+        L.n_corr += part[c].n_corr;
+        L.n_p2p += part[c].n_p2p;
+        L.chi2 += part[c].chi2;
     }
     return L;
 }
@@ -946,6 +1007,12 @@ void om_linearize(const OracleMap* m, const float* src_xyz, const double* src_co
     *n_corr = L.n_corr;
     *n_p2p = L.n_p2p;
     *chi2 = L.chi2;
+}
+
+// Threads of the per-point loops (1 = sequential); returns the value in effect.
+int om_set_threads(int n) {
+    g_threads = n < 1 ? 1 : (n > 256 ? 256 : n);
+    return g_threads;
 }
 
 void om_se3_exp(const double* xi, double* T) { se3_exp(xi, T); }

@@ -828,8 +828,8 @@ far_status far_scan_sources(far_map* map, const float* xyz, uint64_t n, uint32_t
 }
 
 far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes, const double pose[16],
-                         float tau, float kappa, double out_H[36], double out_g[6], int32_t* out_corr,
-                         far_reg_stats* stats) {
+                         float tau, float kappa, uint32_t threads_per_point, double out_H[36], double out_g[6],
+                         int32_t* out_corr, far_reg_stats* stats) {
     far_status st = check_points(map, xyz, n, stride_bytes);
     if (st != FAR_OK) return st;
     if (!pose || !finite_pose(pose) || !out_H || !out_g) return fail(FAR_ERR_INVALID, "pose/H/g invalid");
@@ -842,7 +842,7 @@ far_status far_linearize(far_map* map, const float* xyz, uint64_t n, uint32_t st
         CK(cudaMemsetAsync(map->s.scal, 0, SCAL_COUNT * sizeof(u32), map->stream));
     }
     CK(gn_begin(map->s.st, pose, map->s.scal + SCAL_NADMIT, map->stream));
-    GnArgs a = gn_args(map, pose, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0);
+    GnArgs a = gn_args(map, pose, std::max(nn, 1u), tau, kappa, 0.0, 0, map->s.i32_out, 0.0, (int)threads_per_point);
     reset_marks(map);
     if ((st = run_gn(map, a, std::max(nn, 1u), 1)) != FAR_OK) return st;
     mark(map, EV_END);

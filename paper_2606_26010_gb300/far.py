@@ -108,8 +108,8 @@ _SIGS = {
     "far_map_nearest": (ctypes.c_int, [_vp, _vp, _u64, _u32, ctypes.c_float, _vp, _vp]),
     "far_map_knn": (ctypes.c_int, [_vp, _vp, _u64, _u32, _u32, _vp, _vp]),
     "far_scan_sources": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp]),
-    "far_linearize": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp,
-                                     _vp]),
+    "far_linearize": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, ctypes.c_float, ctypes.c_float, _u32, _vp, _vp,
+                                     _vp, _vp]),
     "far_register_scan": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp]),
     "far_scan_sources_static": (ctypes.c_int, [_vp, _u64, _u32, ctypes.c_float, _u32, _u32, ctypes.c_float, _vp,
                                                _vp, _vp, _vp, _vp, _vp]),
@@ -305,14 +305,15 @@ class VoxelMap:
         m = m.value
         return dict(index=idx[:m], cov=cov[:m], valid=valid[:m], knn=knn[:m])
 
-    def linearize(self, xyz, pose, tau, kappa) -> dict:
+    def linearize(self, xyz, pose, tau, kappa, threads_per_point=0) -> dict:
         ptr, n, stride, keep = _points(xyz)
         H = np.zeros(36)
         g = np.zeros(6)
         corr = np.zeros(max(n, 1), np.int32)
         st = RegStats()
         _check(self._L.far_linearize(self._h, ptr, n, stride, _p(_pose(pose)), ctypes.c_float(tau),
-                                     ctypes.c_float(kappa), _p(H), _p(g), _p(corr), ctypes.byref(st)))
+                                     ctypes.c_float(kappa), threads_per_point, _p(H), _p(g), _p(corr),
+                                     ctypes.byref(st)))
         return dict(H=H.reshape(6, 6), g=g, corr=corr[:st.n_src], **st.as_dict())
 
     # ---- registration (Sec. III-A.2)
