@@ -1,5 +1,6 @@
-// far_scan_sources_static: the scan-local downsampling and Eq. 1 covariances
-// (the same kernels as far_scan_sources) for callers that cannot allocate
+// far_scan_sources_static: the scan-local downsampling and the per-point
+// covariances of each kept point from its k nearest kept neighbours (the same
+// kernels as far_scan_sources) for callers that cannot allocate
 // device memory, e.g. a process whose memory is fixed before it starts (an
 // embedded or safety partition, a memory-capped multi-process server client),
 // or code that must not call cudaMalloc while other work may be capturing CUDA
@@ -53,7 +54,7 @@ constexpr Layout make_layout() {
     L.keys = take((size_t)kStaticMaxPoints * sizeof(u64));
     for (int i = 0; i < 17; ++i) L.u32s[i] = take((size_t)(kStaticMaxPoints + 1) * sizeof(u32));
     L.gstart = take((size_t)(kStaticMaxPoints + 2) * sizeof(u32));
-    L.slot_cnt = take((size_t)(kLocalCap + 1) * sizeof(u32));   // zero at load; every insert leaves it zero
+    L.slot_cnt = take((size_t)(kLocalCap + 1) * sizeof(u32));   // zeroed at the start of every call
     L.slot_base = take((size_t)(kLocalCap + 1) * sizeof(u32));
     L.partials = take((size_t)kPartialWords * sizeof(u32));
     L.scal = take((size_t)SCAL_COUNT * sizeof(u32));
@@ -78,13 +79,16 @@ far_status reject(far_status s, const char* msg) {
     return s;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device `dev` (or managed memory): the kernels read and
+// write these pointers directly, so memory of another GPU is rejected.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -111,19 +115,23 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     }
     if (stride_bytes < 12 || stride_bytes % 4 != 0)
         return reject(FAR_ERR_INVALID, "stride_bytes must be >= 12 and a multiple of 4");
-    if (!xyz || !on_device(xyz)) return reject(FAR_ERR_INVALID, "xyz must be a device pointer");
-    if (!out_index || !out_cov || !out_valid || !on_device(out_index) || !on_device(out_cov) || !on_device(out_valid) ||
-        (out_knn_ids && !on_device(out_knn_ids)))
-        return reject(FAR_ERR_INVALID, "outputs must be device pointers (out_knn_ids may be NULL)");
-    if (2 * scan_blocks((u32)n) + 2 > kPartialWords)
-        return reject(FAR_ERR_INVALID, "internal: static scratch layout too small");
-
-    // Set-up, once per device with that device current: resolve the array's device address.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return reject(FAR_ERR_CUDA, "no current CUDA device");
     }
+    if (!xyz || !on_device(xyz, dev)) return reject(FAR_ERR_INVALID, "xyz must be memory of the current device");
+    if (!out_index || !out_cov || !out_valid || !on_device(out_index, dev) || !on_device(out_cov, dev) ||
+        !on_device(out_valid, dev) || (out_knn_ids && !on_device(out_knn_ids, dev)))
+        return reject(FAR_ERR_INVALID,
+                      "outputs must be memory of the current device (out_knn_ids may be NULL)");
+    if (2 * scan_blocks((u32)n) + 2 > kPartialWords)
+        return reject(FAR_ERR_INVALID, "internal: static scratch layout too small");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    // Set-up, once per device with that device current: resolve the array's device address.
+    // The address is cached for the life of the process; a device reset after the first call
+    // reloads the module elsewhere and is not supported.
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -140,7 +148,6 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
         }
         base = g_dev_base[dev];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     DeviceMap local;
     local.slots = reinterpret_cast<Slot*>(base + kLayout.slots);
@@ -177,9 +184,11 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     s.src = reinterpret_cast<float4*>(base + kLayout.src);
     s.src_cov = reinterpret_cast<float4*>(base + kLayout.src_cov);
 
-    // The array keeps the previous call's contents: map_clear and the insert reset
-    // every counter, key and flag that must start at zero.
-    cudaError_t e = pack_points(xyz, (u32)n, stride_bytes, s.in4, st);
+    // The array keeps the previous call's contents, possibly of a call that stopped half-way:
+    // the per-slot counters are zeroed here, map_clear resets the table, the bucket ring and the
+    // map counters, and the insert resets every other counter and flag it reads.
+    cudaError_t e = cudaMemsetAsync(s.slot_cnt, 0, (size_t)(kLocalCap + 1) * sizeof(u32), st);
+    if (e == cudaSuccess) e = pack_points(xyz, (u32)n, stride_bytes, s.in4, st);
     if (e == cudaSuccess) e = map_clear(local, st);
     InsertCfg cfg;
     if (e == cudaSuccess) e = map_insert_batch(local, s, (u32)n, nullptr, cfg, false, st);
