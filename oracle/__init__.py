@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.cpp")
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                                src, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -72,6 +72,7 @@ def _load():
                                              ctypes.c_float, _vp, _vp, _vp, _vp]),
         "om_linearize": (None, [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_float, ctypes.c_double,
                                 _vp, _vp, _vp, _vp, _vp, _vp]),
+        "om_set_threads": (ctypes.c_int, [ctypes.c_int]),
         "om_se3_exp": (None, [_vp, _vp]),
         "om_se3_log": (None, [_vp, _vp]),
         "om_gn_step": (ctypes.c_int, [_vp] * 5),
@@ -225,6 +226,12 @@ def scan_sources(xyz, voxel_size: float, max_pts_per_voxel: int, k_cov: int, min
     m = L.om_scan_sources(_p(pts), n, ctypes.c_float(voxel_size), max_pts_per_voxel, k_cov,
                           ctypes.c_float(min_spacing), _p(index), _p(cov), _p(valid), _p(knn)) if n else 0
     return dict(index=index[:m], cov=cov[:m], valid=valid[:m], knn=knn[:m])
+
+
+def set_threads(n: int) -> int:
+    """Threads of the per-point loops (CPU-baseline timing): fixed contiguous chunks, chunk sums
+    added in chunk order; 1 (the default) is the sequential oracle. Returns the value in effect."""
+    return int(_load().om_set_threads(int(n)))
 
 
 def se3_exp(xi) -> np.ndarray:

@@ -467,6 +467,52 @@ def test_asmd_caps_invariants_and_far_limit():
             assert c <= max(k, 1) or c == min(lut[tuple(key)], k)
 
 
+def _asmd_voxel_points(key, v, n, rng):
+    """n distinct dyadic points strictly inside voxel `key` (world frame)."""
+    cells = rng.choice(15 ** 3, size=n, replace=False)
+    ijk = np.stack([cells // 225, (cells // 15) % 15, cells % 15], axis=1)
+    return (np.asarray(key, float) + (ijk + 0.5) / 16.0 + 1.0 / 32.0) * v
+
+
+@pytest.mark.parametrize("side", [1, -1])
+@pytest.mark.parametrize("r", [0.0, 8.0, 16.0, 24.0, 32.0, 40.0, 64.0, 128.0])
+def test_asmd_cap_equals_the_linear_decay_at_known_ranges(r, side):
+    """Sec. III-A.3 ASMD pinned on exact inputs: three voxels within r_near of the sensor hold 16
+    points each (N_near = 16 exactly), and a test voxel whose centre lies exactly r from the
+    sensor holds 24 points, more than any cap. With the spacing rule off, the test voxel keeps
+    exactly its cap, which must be clamp(round_half_up(N_near + (k - N_near) min(r / r_max, 1)),
+    k, N_max) with k = 4, N_max = 20, r_max = 64: at r = 8, 24 and 40 the value is 14.5, 11.5
+    and 8.5, so rounding down, a decay in r^2, or a range measured from either corner of the
+    voxel (the test voxel lies on either side of the sensor) all give a different count."""
+    v, nmax, k, r_near, r_max = 0.5, 20, 4, 2.0, 64.0
+    rng = np.random.default_rng(int(r) + 3)
+    sensor = np.array([0.25, 0.25, 0.25])                     # centre of voxel (0, 0, 0)
+    near_keys = [(0, 0, 0), (1, 0, 0), (0, 1, 0)]
+    test_key = (side * int(round(r / v)), 0, 0)                 # centre (0.25 +- r, 0.25, 0.25)
+    parts = [_asmd_voxel_points(kk, v, 16, rng) for kk in near_keys if r == 0.0 or kk != test_key]
+    if r > 0.0:
+        parts.append(_asmd_voxel_points(test_key, v, 24, rng))
+    else:
+        parts[0] = _asmd_voxel_points(test_key, v, 16, rng)     # the sensor's own voxel is a near voxel
+    world = np.concatenate(parts)
+    pose = synth.make_pose(np.eye(3), sensor)
+    local = (world - sensor).astype(np.float32)
+    assert np.array_equal(local.astype(np.float64) + sensor, world)   # the transform is exact
+    m = oracle.OracleMap(v, nmax, k, min_spacing=0.0)
+    _, n_near = m.insert(local, pose, asmd=True, r_c=r_near, r_max=r_max)
+    assert n_near == 16.0
+    ex = m.export()
+    counts = {tuple(kk): int(c) for kk, c in zip(ex["keys"], ex["counts"])}
+    centre = (np.asarray(test_key) + 0.5) * v
+    assert np.linalg.norm(centre - sensor) == r
+    val = 16.0 + (k - 16.0) * min(r / r_max, 1.0)
+    expect = int(min(max(math.floor(val + 0.5), k), nmax))
+    assert counts[test_key] == expect, (r, val, counts[test_key])
+    for kk in near_keys:
+        if kk != test_key:
+            assert counts[kk] == 16      # near voxels (r <= 0.5) have caps of 16 (or 15.9 -> 16)
+
+
 def test_evict_removes_exactly_the_far_voxels():
     rng = np.random.default_rng(15)
     v = 0.5
@@ -498,6 +544,34 @@ def test_threshold_closed_forms():
     delta = 2 * 100.0 * math.sin(th / 2) + 0.2
     sigma = math.sqrt((0.25 + delta ** 2) / 2)
     assert thr.get() == pytest.approx((3 * sigma, sigma / 3))
+
+
+def test_threshold_model_deviation_is_the_chord_at_r_max():
+    """The model deviation pinned by geometry built independently of the oracle: for the
+    increment dT = init^-1 result, a rotation by theta about a random axis moves a point at
+    distance r_max from the axis along a chord of length 2 r_max sin(theta / 2); delta is that
+    chord plus the translation's length. The rotation comes from scipy's rotation-vector map,
+    the point from a vector orthogonal to the axis, and init is a general pose, so the order of
+    the composition (init^-1 result, not result init^-1) matters."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(33)
+    r_max = 80.0
+    thr = oracle.Threshold(sigma0=2.0, min_motion=0.1, r_max=r_max)
+    deltas = []
+    for theta, tlen in ((0.02, 0.3), (0.005, 1.2), (0.11, 0.15)):
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        dR = Rotation.from_rotvec(theta * axis).as_matrix()
+        u = np.cross(axis, rng.normal(size=3))
+        p = r_max * u / np.linalg.norm(u)                   # distance r_max from the axis
+        dt = rng.normal(size=3)
+        dt *= tlen / np.linalg.norm(dt)
+        init = synth.make_pose(Rotation.from_rotvec(rng.normal(size=3)).as_matrix(), rng.normal(size=3) * 50)
+        result = init @ synth.make_pose(dR, dt)
+        deltas.append(np.linalg.norm(dR @ p - p) + tlen)
+        thr.update(init, result)
+        sigma = math.sqrt(np.mean(np.square(deltas)))
+        assert thr.get() == pytest.approx((3 * sigma, sigma / 3), rel=1e-9)
 
 
 # ----------------------------------------------------------------------------- precision variant (50 m tiles)
@@ -687,3 +761,30 @@ def test_prec_tile_of_a_point_just_below_a_tile_corner():
     m.insert(np.array([[1.0, 0.0, 0.0]], np.float32), pose)
     ex = m.export()
     assert list(ex["keys"][0]) == [2003 * 100 - 1, 0, 0]
+
+
+# ----------------------------------------------------------------------------- threaded oracle (CPU baseline)
+def test_threaded_oracle_equals_the_sequential_one():
+    """The CPU baseline's threaded mode computes the same maps bit for bit (per-point work is
+    identical) and the same registration up to the order of the chunk sums."""
+    p = synth.single_scan_problem(2)
+    out = {}
+    try:
+        for th in (1, 4):
+            oracle.set_threads(th)
+            m = oracle.OracleMap(0.5, 20, 5)
+            for s, T in zip(p.map_scans, p.map_poses):
+                m.insert(s, T, asmd=True, r_c=10.0, r_max=100.0)
+            pose, cov, st = m.register(p.query, p.init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
+            src = oracle.scan_sources(p.query, 0.5, 20, 5)
+            out[th] = (m.export(), pose, cov, st, src)
+    finally:
+        oracle.set_threads(1)
+    (e1, T1, C1, s1, src1), (e4, T4, C4, s4, src4) = out[1], out[4]
+    for key in e1:
+        np.testing.assert_array_equal(e1[key], e4[key], err_msg=key)
+    for key in src1:
+        np.testing.assert_array_equal(src1[key], src4[key], err_msg=key)
+    assert s1["n_corr"] == s4["n_corr"] and s1["iters"] == s4["iters"]
+    assert np.abs(T1 - T4).max() < 1e-12
+    assert np.abs(C1 - C4).max() <= 1e-9 * np.abs(C1).max()
