@@ -355,6 +355,53 @@ far_status far_threshold_init(far_threshold* t, double sigma0, double min_motion
 far_status far_threshold_get(const far_threshold* t, double* tau, double* kappa);
 far_status far_threshold_update(far_threshold* t, const double init_pose[16], const double result_pose[16]);
 
+/* ---------------------------------------------------------------- sensor fusion (host, FP64)
+ *
+ * The thin consumer of the registration (Sec. III-B): it turns registered poses into the
+ * odometry the scan pipeline feeds back as its next initial guess. Pure host code: no GPU
+ * is needed, nothing here touches a far_map.
+ */
+
+/*
+ * Eq. 7: the LiDAR's 3D velocity in its own frame from the registered poses of two scans
+ * dt seconds apart, v = R_cur^-1 (t_cur - t_prev) / dt (row-major 4x4 poses; dt > 0).
+ */
+far_status far_lidar_velocity(const double T_prev[16], const double T_cur[16], double dt, double v[3]);
+
+/*
+ * Kinematic EKF (Sec. III-B). State (Eq. 8) x = [t (map position), theta (roll, pitch, yaw
+ * with R(theta) = Rz(yaw) Ry(pitch) Rx(roll)), v (velocity in the body frame)], input
+ * u = [a_m (specific force), omega_m (rate)] of the IMU, body frame = LiDAR frame.
+ * far_ekf_predict applies Eq. 9 as one explicit Euler step from the filter's time to t:
+ *   t += dt R v,  theta += dt E(theta) (omega_m - omega_b),
+ *   v += dt (-[omega_m]x v + (a_m - a_b) + R^T (0, 0, -g)),
+ * with the analytic Jacobian and Q = diag(q) dt; the state is kept in a history of
+ * `history` entries. far_ekf_update takes a registration that refers to time t_meas (the
+ * scan's time stamp, possibly in the past): z_s = [t_L, theta_L, v_L] (Eq. 10 without the
+ * reference angles), projected to the current time by Eq. 11, z_k = z_s + h(x) - h(x_s)
+ * with h the identity and x_s the stored state at or just before t_meas (the oldest one if
+ * t_meas precedes the history); then a Kalman update with R = diag(r) (Joseph form), angle
+ * innovations wrapped to (-pi, pi]. Biases are fixed parameters (calibrated at standstill,
+ * as the paper does). FAR_ERR_INVALID on bad arguments or time going backwards;
+ * FAR_ERR_DEGENERATE when P + R is not positive definite.
+ */
+typedef struct far_ekf far_ekf;
+typedef struct far_ekf_params {
+    double gravity;       /* g in m/s^2 */
+    double acc_bias[3];   /* a_b */
+    double gyro_bias[3];  /* omega_b */
+    double q[9];          /* process noise density per state: Q = diag(q) dt */
+    double r[9];          /* measurement noise variances of [t_L, theta_L, v_L] */
+    uint32_t history;     /* stored states for the delay compensation, 2..2^20 */
+} far_ekf_params;
+far_status far_ekf_create(const far_ekf_params* params, double t0, const double x0[9], const double P0[81],
+                          far_ekf** out);
+far_status far_ekf_destroy(far_ekf* ekf);
+far_status far_ekf_predict(far_ekf* ekf, double t, const double acc[3], const double gyro[3]);
+far_status far_ekf_update(far_ekf* ekf, double t_meas, const double pose[16], const double v_L[3]);
+/* Current time, state, covariance (row-major 9x9) and pose (row-major 4x4); any may be NULL. */
+far_status far_ekf_get(const far_ekf* ekf, double* t, double x[9], double P[81], double pose[16]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfar.so")
-SOURCES = ["primitives.cu", "map.cu", "gicp.cu", "capi.cu", "static_scratch.cu"]
+SOURCES = ["primitives.cu", "map.cu", "gicp.cu", "capi.cu", "static_scratch.cu", "ekf.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False, defines: tuple = (), out: 
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(bdir, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers]):
             jobs.append([nvcc(), *flags, "-c", s, "-o", o])

@@ -90,6 +90,11 @@ class ThresholdState(ctypes.Structure):
                 ("sse", ctypes.c_double), ("n", ctypes.c_int64)]
 
 
+class EkfParams(ctypes.Structure):
+    _fields_ = [("gravity", ctypes.c_double), ("acc_bias", ctypes.c_double * 3), ("gyro_bias", ctypes.c_double * 3),
+                ("q", ctypes.c_double * 9), ("r", ctypes.c_double * 9), ("history", ctypes.c_uint32)]
+
+
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -126,6 +131,12 @@ _SIGS = {
     "far_threshold_init": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "far_threshold_get": (ctypes.c_int, [_vp, _vp, _vp]),
     "far_threshold_update": (ctypes.c_int, [_vp, _vp, _vp]),
+    "far_lidar_velocity": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
+    "far_ekf_create": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp]),
+    "far_ekf_destroy": (ctypes.c_int, [_vp]),
+    "far_ekf_predict": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
+    "far_ekf_update": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
+    "far_ekf_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -462,6 +473,62 @@ class Threshold:
 
     def update(self, init, result):
         _check(self._L.far_threshold_update(ctypes.byref(self._s), _p(_pose(init)), _p(_pose(result))))
+
+
+def lidar_velocity(T_prev, T_cur, dt) -> np.ndarray:
+    """Eq. 7 through the library: the LiDAR velocity in its own frame."""
+    v = np.zeros(3)
+    _check(lib().far_lidar_velocity(_p(_pose(T_prev)), _p(_pose(T_cur)), float(dt), _p(v)))
+    return v
+
+
+class Ekf:
+    """The library's kinematic EKF (Sec. III-B); arguments are marshalled only."""
+
+    def __init__(self, x0, P0, q, r, gravity=9.81, acc_bias=(0.0, 0.0, 0.0), gyro_bias=(0.0, 0.0, 0.0), t0=0.0,
+                 history=256):
+        self._L = lib()
+        prm = EkfParams()
+        prm.gravity = float(gravity)
+        prm.acc_bias[:] = [float(a) for a in acc_bias]
+        prm.gyro_bias[:] = [float(a) for a in gyro_bias]
+        prm.q[:] = [float(a) for a in q]
+        prm.r[:] = [float(a) for a in r]
+        prm.history = int(history)
+        h = ctypes.c_void_p()
+        x0 = np.ascontiguousarray(x0, np.float64).reshape(9)
+        P0 = np.ascontiguousarray(P0, np.float64).reshape(81)
+        _check(self._L.far_ekf_create(ctypes.byref(prm), float(t0), _p(x0), _p(P0), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            self._L.far_ekf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, t, acc, gyro):
+        a = np.ascontiguousarray(acc, np.float64).reshape(3)
+        g = np.ascontiguousarray(gyro, np.float64).reshape(3)
+        _check(self._L.far_ekf_predict(self._h, float(t), _p(a), _p(g)))
+
+    def update(self, t_meas, pose, v_l):
+        v = np.ascontiguousarray(v_l, np.float64).reshape(3)
+        _check(self._L.far_ekf_update(self._h, float(t_meas), _p(_pose(pose)), _p(v)))
+
+    def get(self):
+        t = ctypes.c_double(0)
+        x, P, T = np.zeros(9), np.zeros(81), np.zeros(16)
+        _check(self._L.far_ekf_get(self._h, ctypes.byref(t), _p(x), _p(P), _p(T)))
+        return t.value, x, P.reshape(9, 9), T.reshape(4, 4)
+
+    def pose(self) -> np.ndarray:
+        return self.get()[3]
 
 
 def version() -> str:

@@ -317,6 +317,52 @@ def constant_velocity_guess(prev2: np.ndarray, prev1: np.ndarray) -> np.ndarray:
     return prev1 @ (np.linalg.inv(prev2) @ prev1)
 
 
+# ---- synthetic IMU along the track -----------------------------------------------------
+GRAVITY = 9.81
+FRAME_RATE_HZ = 10.0
+
+
+def sequence_pose_at(seq: "TrackSequence", time_s: float) -> np.ndarray:
+    """Sensor pose of a TrackSequence at a continuous time (frame t is at t / 10 s)."""
+    return track_pose(seq.s0 + seq.step * FRAME_RATE_HZ * time_s)
+
+
+def track_imu(seq: "TrackSequence", t0: float, t1: float, rate_hz: float = 100.0, acc_sigma: float = 0.0,
+              gyro_sigma: float = 0.0, seed: int = 0):
+    """IMU samples (times, specific force, angular rate; body frame = sensor frame) along the
+    sequence's trajectory at rate_hz for times in (t0, t1], from central differences of the
+    analytic pose (step 1 ms) plus seeded white noise. The sample at time t describes the
+    motion over the interval that ends at t (its midpoint), as an IMU integrating between
+    readings would."""
+    rng = np.random.default_rng(seed)
+    n0 = int(math.floor(t0 * rate_hz + 1e-9)) + 1
+    n1 = int(math.floor(t1 * rate_hz + 1e-9))
+    times, acc, gyro = [], [], []
+    h = 1e-3
+    g_w = np.array([0.0, 0.0, -GRAVITY])
+    for k in range(n0, n1 + 1):
+        t = k / rate_hz
+        tm = t - 0.5 / rate_hz
+        Tm, T0, Tp = (sequence_pose_at(seq, tm - h), sequence_pose_at(seq, tm), sequence_pose_at(seq, tm + h))
+        R = T0[:3, :3]
+        p_dd = (Tp[:3, 3] - 2 * T0[:3, 3] + Tm[:3, 3]) / (h * h)
+        R_d = (Tp[:3, :3] - Tm[:3, :3]) / (2 * h)
+        W = R.T @ R_d
+        w = np.array([W[2, 1] - W[1, 2], W[0, 2] - W[2, 0], W[1, 0] - W[0, 1]]) * 0.5
+        f = R.T @ (p_dd - g_w)
+        times.append(t)
+        acc.append(f + rng.normal(scale=acc_sigma, size=3) if acc_sigma > 0 else f)
+        gyro.append(w + rng.normal(scale=gyro_sigma, size=3) if gyro_sigma > 0 else w)
+    return np.array(times), np.array(acc).reshape(-1, 3), np.array(gyro).reshape(-1, 3)
+
+
+def track_body_velocity(seq: "TrackSequence", time_s: float) -> np.ndarray:
+    """Velocity of the sensor in its own frame at a continuous time (central difference)."""
+    h = 1e-4
+    Tm, T0, Tp = sequence_pose_at(seq, time_s - h), sequence_pose_at(seq, time_s), sequence_pose_at(seq, time_s + h)
+    return T0[:3, :3].T @ ((Tp[:3, 3] - Tm[:3, 3]) / (2 * h))
+
+
 # ---- many independent problems of uneven size ------------------------------------------
 @dataclass
 class BatchProblemSpec:
