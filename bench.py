@@ -50,15 +50,21 @@ MAX_VOXELS = 1 << 19        # 0.5 M voxels (10 M points at N = 20); the map hold
 PRIOR_NOISE = (0.05, 0.1)   # IMU-like prior: metres, degrees per frame
 
 
-def workload_config(steps, warmup, n_gpus):
+SEQ_SCANS = 200             # the high-speed sequence: 200 scans (1.4 km)
+
+
+def workload_config(steps, warmup, n_gpus, prior="ekf", n_seq=SEQ_SCANS):
     return {
         "workload": "high-speed sequence: 128x2048 LiDAR (~260k pts/scan, sigma 0.03 m), 70 m/s at 10 Hz "
                     "on a walled oval (700 m straights, R 120 m), per-scan register + ASMD insert + evict",
-        "voxel_m": V, "n_max": NMAX, "k_cov": K_COV, "gn_max_iters": MAX_ITERS, "conv_eps": CONV_EPS,
-        "asmd": {"r_near_m": R_NEAR, "r_max_m": R_MAX}, "evict_radius_m": EVICT_R,
+        "sequence_scans": n_seq, "voxel_m": V, "n_max": NMAX, "k_cov": K_COV, "gn_max_iters": MAX_ITERS,
+        "conv_eps": CONV_EPS, "asmd": {"r_near_m": R_NEAR, "r_max_m": R_MAX}, "evict_radius_m": EVICT_R,
         "threshold": {"sigma0_m": SIGMA0, "min_motion_m": MIN_MOTION},
-        "init_prior": "true inter-frame motion + seeded noise (%.2f m, %.1f deg)" % PRIOR_NOISE,
-        "scans_timed": steps, "scans_warmup": warmup, "first_scan": "inserted at its true pose (setup)",
+        "init_prior": PRIOR_LABELS[prior],
+        "scans_timed": steps, "scans_warmup": warmup,
+        "timed_window": f"scans {n_seq - steps}-{n_seq - 1} (the end of the sequence; scans 1-{n_seq - steps - 1} "
+                        f"run first, untimed, the last {warmup} of them as warm-up)",
+        "first_scan": "inserted at its true pose (setup)",
         "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident before timing",
         "parallelism": "replicas" if n_gpus > 1 else "single GPU",
     }
@@ -84,7 +90,10 @@ def parse_args():
     ap.add_argument("--autotune", action="store_true", help="batched: tune v, lanes per point and load factor first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample-steps", type=int, default=20,
+                    help="scans of the oracle comparison and CPU baseline (lockstep with the GPU's poses)")
+    ap.add_argument("--prior", choices=["ekf", "cv", "noisy-truth"], default="ekf")
+    ap.add_argument("--scans", type=int, default=SEQ_SCANS, help="sequence length (scans)")
     ap.add_argument("--max-voxels", type=int, default=MAX_VOXELS,
                     help="bucket pool of the map (smaller values shrink the device footprint for profiling)")
     return ap.parse_args()
@@ -111,7 +120,7 @@ def rank_env():
 # --------------------------------------------------------------------------------------- inputs
 class Vehicle:
     """One simulated vehicle on the oval: scans, true poses (optionally moved by a world
-    offset) and the motion prior."""
+    offset) and the motion priors."""
 
     def __init__(self, rank: int, offset=(0.0, 0.0, 0.0)):
         self.seq = synth.TrackSequence(seed=42 + rank, s0=300.0 * rank)
@@ -121,14 +130,108 @@ class Vehicle:
     def pose(self, t: int) -> np.ndarray:
         return self.shift @ self.seq.pose(t)
 
-    def prior(self, t: int, prev_est: np.ndarray, rng=None) -> np.ndarray:
-        """IMU-like prediction: previous estimate times the true motion, with seeded noise."""
-        d = np.linalg.inv(self.seq.pose(t - 1)) @ self.seq.pose(t)
-        return prev_est @ d @ synth.random_offset(rng or self.rng, PRIOR_NOISE[1], PRIOR_NOISE[0])
+    def prior(self, t: int, ests, kind: str = "cv", rng=None) -> np.ndarray:
+        """Initial pose of scan t from the estimates of scans 0..t-1.
+        cv: constant velocity from the last two estimates (the first frame starts from the
+        known initial motion); noisy-truth: the last estimate times the true inter-frame motion
+        with seeded noise (an idealised IMU)."""
+        if kind == "cv":
+            if len(ests) < 2:
+                return ests[-1] @ (np.linalg.inv(self.pose(0)) @ self.pose(1))
+            return synth.constant_velocity_guess(ests[-2], ests[-1])
+        d = np.linalg.inv(self.pose(t - 1)) @ self.pose(t)
+        return ests[-1] @ d @ synth.random_offset(rng or self.rng, PRIOR_NOISE[1], PRIOR_NOISE[0])
+
+
+PRIOR_LABELS = {
+    "ekf": "kinematic EKF (Sec. III-B): 100 Hz synthetic IMU (0.05 m/s^2, 0.002 rad/s white noise) predicts to "
+           "the scan time; each registered pose and its Eq. 7 velocity are fused one IMU step later (Eq. 11 delay "
+           "compensation)",
+    "cv": "constant velocity from the last two estimates (first frame: the known initial motion)",
+    "noisy-truth": "previous estimate x true inter-frame motion x seeded noise (%.2f m, %.1f deg)" % PRIOR_NOISE,
+}
+IMU_RATE, IMU_ACC_SIGMA, IMU_GYRO_SIGMA = 100.0, 0.05, 0.002
+EKF_P0 = [0.01] * 3 + [1e-4] * 3 + [0.1] * 3
+EKF_Q = [1e-3] * 3 + [1e-5] * 3 + [0.5] * 3
+EKF_R = [1e-4] * 3 + [1e-6] * 3 + [0.05] * 3
+
+
+class Prior:
+    """Initial poses of the scans of one run: `init(t, ests)` before scan t, `observe(t, ests)`
+    after it (ests: the estimates of scans 0..t). For the EKF prior the filter is the library's
+    (product arm) or the oracle's (reference arm); both run on the host."""
+
+    def __init__(self, veh: Vehicle, kind: str, impl: str = "library", rng=None):
+        self.veh, self.kind, self.rng = veh, kind, rng
+        if kind != "ekf":
+            return
+        seq = veh.seq
+        self.frame_dt = 1.0 / synth.FRAME_RATE_HZ
+        x0 = np.concatenate([veh.pose(0)[:3, 3], euler_zyx(veh.pose(0)[:3, :3]), synth.track_body_velocity(seq, 0.0)])
+        if impl == "library":
+            from paper_2606_26010_gb300 import far
+            self.ekf = far.Ekf(x0, np.diag(EKF_P0), EKF_Q, EKF_R, t0=0.0, history=64)
+            self.vel = far.lidar_velocity
+        else:
+            from oracle import ekf as oe
+            self.ekf = oe.KinematicEKF(x0, np.diag(EKF_P0), EKF_Q, EKF_R, t0=0.0, history=64)
+            self.vel = oe.lidar_velocity
+        self.imu = imu_stream(veh)
+        self.k = 0   # next IMU sample
+
+    def _predict_to(self, t_s: float):
+        times, acc, gyro = self.imu
+        while self.k < len(times) and times[self.k] <= t_s + 1e-9:
+            self.ekf.predict(times[self.k], acc[self.k], gyro[self.k])
+            self.k += 1
+
+    def init(self, t: int, ests) -> np.ndarray:
+        if self.kind == "ekf":
+            self._predict_to(t * self.frame_dt)
+            return self.ekf.pose()
+        return self.veh.prior(t, ests, self.kind, self.rng)
+
+    def observe(self, t: int, ests, ok: bool = True):
+        if self.kind != "ekf" or not ok:
+            return
+        self._predict_to(t * self.frame_dt + 1.0 / IMU_RATE)      # the result arrives one IMU step later
+        self.ekf.update(t * self.frame_dt, ests[-1], self.vel(ests[-2], ests[-1], self.frame_dt))
+
+
+_IMU_CACHE = {}
+
+
+def imu_stream(veh: Vehicle):
+    key = (veh.seq.seed, veh.seq.s0)
+    if key not in _IMU_CACHE:
+        _IMU_CACHE[key] = synth.track_imu(veh.seq, 0.0, 30.0, IMU_RATE, IMU_ACC_SIGMA, IMU_GYRO_SIGMA,
+                                          seed=veh.seq.seed + 17)
+    return _IMU_CACHE[key]
+
+
+def euler_zyx(R) -> np.ndarray:
+    """(roll, pitch, yaw) of R = Rz(yaw) Ry(pitch) Rx(roll) (the EKF's angle convention)."""
+    return np.array([math.atan2(R[2, 1], R[2, 2]), -math.asin(max(-1.0, min(1.0, R[2, 0]))),
+                     math.atan2(R[1, 0], R[0, 0])])
+
+
+def sequence_scans(veh: Vehicle, n: int):
+    return [veh.seq.scan(t) for t in range(n)]
 
 
 def rot_angle(R):
     return math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2)))
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
 
 
 # --------------------------------------------------------------------------------------- clocks
@@ -183,27 +286,79 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# Sources whose change invalidates a kernel's committed ncu traffic figure.
+KERNEL_SOURCES = {
+    "k_gn_lin": ("gicp.cu", "search.cuh", "far_internal.cuh", "gicp.cuh"),
+    "k_knn_cov": ("map.cu", "search.cuh", "far_internal.cuh", "map.cuh"),
+    "k_admit": ("map.cu", "far_internal.cuh", "map.cuh"),
+}
+
+
+def kernel_source_hash(kernel="k_gn_lin"):
     h = hashlib.sha256()
-    for f in ("gicp.cu", "search.cuh", "far_internal.cuh", "gicp.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2606_26010_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per k_gn_lin launch from the committed ncu summary, if it matches the source."""
-    p = os.path.join(ROOT, "profiles", "k_gn_lin_hbm_128x2048.md")
+def ncu_traffic(kernel="k_gn_lin"):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if it matches the source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_hbm_128x2048.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     s = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    if not m or not s or s.group(1) != kernel_source_hash():
+    if not m or not s or s.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 
 
 # --------------------------------------------------------------------------------------- GPU arm
+def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from, clk=None, rng=None,
+                 on_step=None, e2e=False):
+    """Scans 1..n_seq-1 through far_process_scan, each from `prior` of the estimates so far.
+    Every step is bracketed by CUDA events on the map's stream after an L2 flush (device
+    time) or, with e2e, timed on the host around the call (pinned host input). The clock
+    sampler runs from scan `timed_from` on. Returns per-step records."""
+    import torch
+    ests = [veh.pose(0)]
+    recs = []
+    prior = Prior(veh, prior_kind, "library", rng)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for t in range(1, n_seq):
+            if clk is not None and t == timed_from:
+                torch.cuda.synchronize()
+                clk.__enter__()
+            init = prior.init(t, ests)
+            tau, kappa = thr.get()
+            flush.zero_()
+            if e2e:
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+            else:
+                ev0.record(stream)
+            pose, _, res = m.process_scan(dev[t], init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau,
+                                          kappa=kappa, asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R)
+            thr.update(init, pose)
+            if e2e:
+                ms = 1e3 * (time.perf_counter() - w0)
+            else:
+                ev1.record(stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+            recs.append(dict(t=t, ms=ms, init=init, pose=pose, res=res, n=int(dev[t].shape[0])))
+            ests.append(pose)
+            prior.observe(t, ests, res["status"] == 0)
+            if on_step is not None:
+                on_step(t, m, res)
+    if clk is not None:
+        torch.cuda.synchronize()
+        clk.__exit__(None, None, None)
+    return recs
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -219,8 +374,9 @@ def run_ours(args):
     offset = [float(x) for x in args.world_offset.split(",")]
     args.precision = args.precision or 0
     veh = Vehicle(rank, offset)
-    n_total = 1 + args.warmup + args.steps
-    scans = [veh.seq.scan(t) for t in range(n_total)]
+    n_seq = max(args.scans, 2 + args.warmup + args.steps)
+    timed_from = n_seq - args.steps
+    scans = sequence_scans(veh, n_seq)
     dev = [torch.from_numpy(s).cuda() for s in scans]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -232,139 +388,124 @@ def run_ours(args):
             m.insert(dev[0], veh.pose(0), asmd=True, r_near=R_NEAR, r_max=R_MAX)
         return m
 
-    def step(m, thr, t, est, inp):
-        init = veh.prior(t, est)
-        tau, kappa = thr.get()
-        pose, _, res = m.process_scan(inp, init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau, kappa=kappa,
-                                      asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R)
-        thr.update(init, pose)
-        return pose, res
+    def timed(recs):
+        return [r for r in recs if r["t"] >= timed_from]
 
-    # ---- device-resident pass (value): no profiling events inside the library, so the
-    # programmatically dependent launches overlap as they do in use
+    # ---- device-resident pass (value): the whole sequence, the last `steps` scans timed; no
+    # profiling events inside the library, so the dependent launches overlap as they do in use
     m = make_map()
-    thr = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-    est = veh.pose(0)
-    with torch.cuda.stream(stream):
-        for t in range(1, 1 + args.warmup):
-            est, _ = step(m, thr, t, est, dev[t])
-    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    step_ms, results, ests = [], [], {args.warmup: est}
-    launches_in_steps = 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            for t in range(1 + args.warmup, n_total):
-                flush.zero_()
-                l0 = far.launch_count()
-                ev0.record(stream)
-                est, res = step(m, thr, t, est, dev[t])
-                ev1.record(stream)
-                ev1.synchronize()
-                launches_in_steps += far.launch_count() - l0
-                step_ms.append(ev0.elapsed_time(ev1))
-                results.append(res)
-                ests[t] = est
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall0
-    rpe = []     # per-frame relative pose error of the estimates against the true motion
-    for t in range(1 + args.warmup, n_total):
-        D = np.linalg.inv(np.linalg.inv(veh.pose(t - 1)) @ veh.pose(t)) @ (np.linalg.inv(ests[t - 1]) @ ests[t])
-        rpe.append((float(np.linalg.norm(D[:3, 3])), rot_angle(D[:3, :3])))
+    launches = {}
 
-    # ---- profiled pass over the same scans (stage times, per-launch k_gn_lin durations for the
-    # roofline): the library records CUDA events between its kernels on the map's stream
-    gn_ms, gn_bytes, gn_launches, stage_acc, ins_acc = [], [], [], {}, {}
-    knn_ms, knn_bytes = [], []
-    mp = make_map()
-    mp.set_profiling(True)
-    thr_p = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-    est_p = veh.pose(0)
-    with torch.cuda.stream(stream):
-        for t in range(1, n_total):
-            if t > args.warmup:
-                flush.zero_()
-            est_p, res_p = step(mp, thr_p, t, est_p, dev[t])
-            if t <= args.warmup:
-                continue
-            st = mp.stage_times()
-            for k_, v_ in st.items():
-                stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
-            ins_t = mp.insert_times()
-            for w_, parts in ins_t.items():
-                for k_, v_ in parts.items():
-                    ins_acc.setdefault(w_, {})[k_] = ins_acc.get(w_, {}).get(k_, 0.0) + v_
-            # source covariances (k_knn_cov on the scan-local map, with k_make_sources before it):
-            # each source is read as a query and once as a candidate (the local map holds exactly
-            # the sources), and its covariance is written: 16 + 16 + 32 B
-            knn_ms.append(ins_t["sources"]["cov_ms"])
-            knn_bytes.append(64.0 * res_p["n_src"])
-            n_src, u_v, p_touched = mp.gn_footprint()
-            nblk = min((scans[t].shape[0] * 4 + 127) // 128, 152 * 5)
-            # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B; 12 + 12 + 1
-            # in precision mode), each probed voxel's slot (16 B; + 4 B exponent), its points (12 B xyz
-            # + 4 B id + 24 B covariance; 12 B FP16 covariance), the FP64 block partials (28 doubles)
-            if args.precision:
-                gn_bytes.append(29.0 * n_src + 20.0 * u_v + 28.0 * p_touched + 224.0 * nblk)
-            else:
-                gn_bytes.append(36.0 * n_src + 16.0 * u_v + 40.0 * p_touched + 224.0 * nblk)
-            gn_ms.append(st["gn_launch_ms"])
-            gn_launches.append(st["gn_launches"])
-    mp.close()
-    pts = float(sum(scans[t].shape[0] for t in range(1 + args.warmup, n_total)))
-    dev_s = sum(step_ms) / 1e3
+    def count_launches(t, _m, _res):
+        launches[t] = far.launch_count()
+
+    l_start = far.launch_count()
+    t_wall0 = time.perf_counter()
+    clk = ClockSampler(local)
+    recs = run_sequence(m, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, args.prior, stream, flush, n_seq,
+                        timed_from, clk=clk, on_step=count_launches)
+    wall = time.perf_counter() - t_wall0
+    m.close()
+    tr = timed(recs)
+    launches_in_steps = launches[n_seq - 1] - launches.get(timed_from - 1, l_start)
+    pts = float(sum(r["n"] for r in tr))
+    dev_s = sum(r["ms"] for r in tr) / 1e3
     dev_s_all, pts_all = aggregate_ranks(dev_s, pts, world, "cuda")
     value = pts_all / dev_s_all / 1e6
-    lat = np.array(step_ms)
+    lat = np.array([r["ms"] for r in tr])
+    lat_all = np.array([r["ms"] for r in recs])
+    ests = [veh.pose(0)] + [r["pose"] for r in recs]
+    rpe = []     # per-frame relative pose error of the estimates against the true motion
+    for t in range(1, n_seq):
+        D = np.linalg.inv(np.linalg.inv(veh.pose(t - 1)) @ veh.pose(t)) @ (np.linalg.inv(ests[t - 1]) @ ests[t])
+        rpe.append((float(np.linalg.norm(D[:3, 3])), rot_angle(D[:3, :3])))
+    drift = np.linalg.inv(veh.pose(n_seq - 1)) @ ests[-1]
 
-    # roofline of the dominant kernel (k_gn_lin)
+    # ---- profiled pass over the same sequence (stage times, per-launch kernel durations for the
+    # rooflines): the library records CUDA events between its kernels on the map's stream
+    acc = {"gn_ms": 0.0, "gn_launches": 0, "gn_bytes": 0.0, "knn_ms": 0.0, "knn_bytes": 0.0, "knn_launches": 0,
+           "admit_ms": 0.0, "admit_bytes": 0.0, "admit_launches": 0}
+    stage_acc, ins_acc = {}, {}
+
+    def profile_step(t, mp, res):
+        if t < timed_from:
+            return
+        st = mp.stage_times()
+        for k_, v_ in st.items():
+            stage_acc[k_] = stage_acc.get(k_, 0.0) + v_
+        ins_t = mp.insert_times()
+        for w_, parts in ins_t.items():
+            for k_, v_ in parts.items():
+                ins_acc.setdefault(w_, {})[k_] = ins_acc.get(w_, {}).get(k_, 0.0) + v_
+        n_src, u_v, p_touched = mp.gn_footprint()
+        nblk = min((dev[t].shape[0] * 4 + 127) // 128, 152 * 5)
+        # algorithmic bytes of one Gauss-Newton launch: source point + covariance (36 B; 12 + 12 + 1
+        # in precision mode), each probed voxel's slot (16 B; + 4 B exponent), its points (12 B xyz
+        # + 4 B id + 24 B covariance; 12 B FP16 covariance), the FP64 block partials (28 doubles)
+        if args.precision:
+            b = 29.0 * n_src + 20.0 * u_v + 28.0 * p_touched + 224.0 * nblk
+        else:
+            b = 36.0 * n_src + 16.0 * u_v + 40.0 * p_touched + 224.0 * nblk
+        acc["gn_ms"] += st["gn_launch_ms"] * st["gn_launches"]
+        acc["gn_launches"] += st["gn_launches"]
+        acc["gn_bytes"] += b * st["gn_launches"]
+        # k-NN covariances (k_knn_cov): the sources against the scan-local map and the added points
+        # against the map: each query read (16 B) and its covariance written (32 B), each candidate
+        # point read once (16 B) with its voxel's slot (16 B); a lower bound: the scan-local voxels
+        # touched are counted as the sources' voxels
+        acc["knn_ms"] += ins_t["sources"]["cov_ms"] + ins_t["map"]["cov_ms"]
+        acc["knn_bytes"] += 64.0 * res["n_src"] + 48.0 * res["n_inserted"]
+        acc["knn_launches"] += 2
+        # admission (k_admit): every point of the two inserts read once as a candidate (16 B)
+        n_raw = float(dev[t].shape[0])
+        acc["admit_ms"] += ins_t["sources"]["admit_ms"] + ins_t["map"]["admit_ms"]
+        acc["admit_bytes"] += 2 * 16.0 * n_raw
+        acc["admit_launches"] += 2
+
+    mp = make_map()
+    mp.set_profiling(True)
+    run_sequence(mp, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, args.prior, stream, flush, n_seq,
+                 timed_from, on_step=profile_step)
+    mp.close()
+
     peak, peak_kind = measured_peaks()
-    tot_b = sum(b * n for b, n in zip(gn_bytes, gn_launches))
-    tot_t = sum(ms * n for ms, n in zip(gn_ms, gn_launches)) / 1e3
-    achieved = tot_b / tot_t / 1e9 if tot_t > 0 else 0.0
-    per_launch_bytes = tot_b / max(1, sum(gn_launches))
-    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": ncu_traffic(), "kernel": "k_gn_lin",
+
+    def roofline(kernel, ms, nbytes, nlaunch, what):
+        t_s = ms / 1e3
+        ach = nbytes / t_s / 1e9 if t_s > 0 else 0.0
+        return {"bound": "hbm", "achieved": round(ach, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 5), "traffic": ncu_traffic(kernel), "kernel": kernel,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": round(per_launch_bytes),
-                "mean_launch_us": round(1e3 * tot_t / max(1, sum(gn_launches)) * 1e3, 2),
-                "launches": int(sum(gn_launches)),
-                "measured_in": "profiled pass over the same scans (per-launch CUDA events on the map's stream)"}
+                "algorithmic_bytes_per_launch": round(nbytes / max(1, nlaunch)),
+                "mean_launch_us": round(1e3 * ms / max(1, nlaunch), 2), "launches": int(nlaunch),
+                "ms_per_scan": round(ms / args.steps, 4), "bytes": what,
+                "measured_in": "profiled pass over the same scans (CUDA events inside the library on the "
+                               "map's stream)"}
 
-    knn_t = sum(knn_ms) / 1e3
-    knn_achieved = sum(knn_bytes) / knn_t / 1e9 if knn_t > 0 else 0.0
-    roofline_knn = {"bound": "hbm", "achieved": round(knn_achieved, 2), "peak": peak, "unit": "GB/s",
-                    "frac": round(knn_achieved / peak, 5), "traffic": None,
-                    "kernel": "k_knn_cov<5> (source covariances, the largest share of the launch list)",
-                    "algorithmic_bytes_per_launch": round(sum(knn_bytes) / max(1, len(knn_bytes))),
-                    "mean_launch_us": round(1e3 * knn_t / max(1, len(knn_ms)) * 1e3, 2), "launches": len(knn_ms),
-                    "measured_in": "profiled pass: events around k_make_sources + k_knn_cov of each scan; bytes "
-                                   "exclude the hash slots (a lower bound)"}
+    rooflines = [
+        roofline("k_gn_lin", acc["gn_ms"], acc["gn_bytes"], acc["gn_launches"],
+                 "36 B per source + 16 B per probed voxel + 40 B per point in them + 224 B per block"),
+        roofline("k_knn_cov", acc["knn_ms"], acc["knn_bytes"], acc["knn_launches"],
+                 "64 B per source (query, candidate, covariance) + 48 B per added map point"),
+        roofline("k_admit", acc["admit_ms"], acc["admit_bytes"], acc["admit_launches"],
+                 "16 B per input point per insert"),
+    ]
+    dominant = max(rooflines, key=lambda r: r["ms_per_scan"])
 
     # ---- end-to-end pass through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
-        pinned = [torch.from_numpy(s).pin_memory() for s in scans]
+        pinned = [torch.from_numpy(s_).pin_memory() for s_ in scans]
         m2 = make_map()
-        thr2 = far.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-        est2 = veh.pose(0)
-        with torch.cuda.stream(stream):
-            for t in range(1, 1 + args.warmup):
-                est2, _ = step(m2, thr2, t, est2, pinned[t])
-            torch.cuda.synchronize()
-            if world > 1:
-                dist.barrier()
-            e2e_s = 0.0
-            for t in range(1 + args.warmup, n_total):
-                flush.zero_()
-                torch.cuda.synchronize()
-                w0 = time.perf_counter()
-                est2, _ = step(m2, thr2, t, est2, pinned[t])
-                e2e_s += time.perf_counter() - w0
+        if world > 1:
+            dist.barrier()
+        recs2 = run_sequence(m2, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), pinned, args.prior, stream,
+                             flush, n_seq, timed_from, e2e=True)
+        m2.close()
+        e2e_s = sum(r["ms"] for r in timed(recs2)) / 1e3
         if world > 1:
             tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -375,52 +516,124 @@ def run_ours(args):
         e2e = {"value": round(pts_all / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": round(h2d),
                "d2h_bytes_per_step": d2h, "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
                "api": "far_process_scan with pinned host points"}
-        m2.close()
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_sample_steps)
-    accuracy = None
+    # ---- the other priors, as labelled secondary lines
+    secondary = []
+    for other in [k_ for k_ in PRIOR_LABELS if k_ != args.prior]:
+        m3 = make_map()
+        recs3 = run_sequence(m3, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, other, stream, flush, n_seq,
+                             timed_from, rng=np.random.default_rng(1000 + rank))
+        m3.close()
+        tr3 = timed(recs3)
+        it3 = np.array([r["res"]["iters"] for r in recs3])
+        secondary.append({"init_prior": PRIOR_LABELS[other],
+                          "value": round(sum(r["n"] for r in tr3) / (sum(r["ms"] for r in tr3) / 1e3) / 1e6, 3),
+                          "unit": UNIT, "gn_iters_mean_timed": round(float(np.mean([r["res"]["iters"] for r in tr3])), 3),
+                          "gn_iters_mean_sequence": round(float(it3.mean()), 3),
+                          "gn_iters_at_cap_sequence": int((it3 >= MAX_ITERS).sum()),
+                          "status_ok": int(sum(1 for r in recs3 if r["res"]["status"] == 0))})
+
+    cpu = cpu1 = accuracy = None
+    if rank == 0 and not args.no_cpu_baseline and args.precision == 0 and offset == [0.0, 0.0, 0.0]:
+        cpu, cpu1, accuracy = oracle_lockstep(veh, recs, args.cpu_sample_steps)
     n_acc = args.accuracy_scans if args.accuracy_scans is not None else (6 if args.precision else 0)
-    if rank == 0 and n_acc > 0:
-        accuracy = precision_accuracy(n_acc, stream)
+    prec_acc = precision_accuracy(n_acc, stream) if (rank == 0 and n_acc > 0) else None
 
-    n_iter = np.mean([r["reg"]["iters"] if "reg" in r else r["iters"] for r in results])
     st_mean = {k_: round(v_ / args.steps, 4) for k_, v_ in stage_acc.items()}
+    iters = np.array([r["res"]["iters"] for r in recs])
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s_all / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast LiDAR; the paper's datasets are not available)",
-        "config": dict(workload_config(args.steps, args.warmup, world), precision_mode=args.precision,
-                       world_offset_m=offset),
+        "config": dict(workload_config(args.steps, args.warmup, world, args.prior, n_seq),
+                       precision_mode=args.precision, world_offset_m=offset),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                        "p99": round(float(np.percentile(lat, 99)), 4),
                        "max": round(float(lat.max()), 4), "mean": round(float(lat.mean()), 4)},
+        "full_sequence": {"scans": len(recs), "p50_ms": round(float(np.percentile(lat_all, 50)), 4),
+                          "p99_ms": round(float(np.percentile(lat_all, 99)), 4),
+                          "max_ms": round(float(lat_all.max()), 4), "mean_ms": round(float(lat_all.mean()), 4),
+                          "mpoints_per_s": round(sum(r["n"] for r in recs) / (lat_all.sum() / 1e3) / 1e6, 3),
+                          "gn_iters_mean": round(float(iters.mean()), 3),
+                          "gn_iters_at_cap": int((iters >= MAX_ITERS).sum()),
+                          "status_ok": int(sum(1 for r in recs if r["res"]["status"] == 0)),
+                          "map_points_max": int(max(r["res"]["n_points"] for r in recs)),
+                          "drift_end_m": round(float(np.linalg.norm(drift[:3, 3])), 4)},
         "stages_ms_mean": st_mean,
         "insert_parts_ms_mean": {w_: {k_: round(v_ / args.steps, 4) for k_, v_ in d_.items()} for w_, d_ in ins_acc.items()},
-        "gn_iters_mean": round(float(n_iter), 3),
+        "gn_iters_mean": round(float(np.mean([r["res"]["iters"] for r in tr])), 3),
+        "secondary_priors": secondary,
         "points_per_scan": round(pts / args.steps),
-        "n_src_mean": round(float(np.mean([r["n_src"] for r in results]))),
+        "n_src_mean": round(float(np.mean([r["res"]["n_src"] for r in tr]))),
         "relative_pose_error_per_frame": {"median_trans_m": round(float(np.median([e[0] for e in rpe])), 5),
                                           "max_trans_m": round(float(np.max([e[0] for e in rpe])), 5),
                                           "median_rot_rad": round(float(np.median([e[1] for e in rpe])), 7)},
-        "map_points_end": int(results[-1]["n_points"]),
-        "roofline": roofline,
-        "roofline_knn_cov": roofline_knn,
+        "map_points_end": int(recs[-1]["res"]["n_points"]),
+        "roofline": dominant,
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
+        "cpu_baseline_single_thread": cpu1,
+        "pose_vs_oracle": accuracy,
         "e2e": e2e,
         "gpu_launches": int(launches_in_steps),
         "clocks": clk.summary(),
-        "wall_s_timed_region": round(wall, 3),
+        "wall_s_sequence_pass": round(wall, 3),
     }
-    if accuracy is not None:
-        out["accuracy_vs_fp64_oracle"] = accuracy
+    if prec_acc is not None:
+        out["accuracy_vs_fp64_oracle"] = prec_acc
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def oracle_lockstep(veh, recs, n_scans):
+    """The oracle on the first n_scans scans in lockstep with the GPU run: each scan registered
+    from the GPU's initial pose against a map that was updated at the GPU's registered poses
+    (so it holds exactly the GPU's map), then inserted and evicted at the GPU's pose. Reports the
+    per-scan pose difference (the registration's own error) and times the oracle's register +
+    insert + evict per scan, once single-threaded and once on all host cores."""
+    import oracle
+    recs = recs[:n_scans]
+    out = {}
+    for threads in (1, os.cpu_count() or 1):
+        oracle.set_threads(threads)
+        m = oracle.OracleMap(V, NMAX, K_COV)
+        m.insert(veh.seq.scan(0), veh.pose(0), asmd=True, r_c=R_NEAR, r_max=R_MAX)
+        thr = oracle.Threshold(SIGMA0, MIN_MOTION, R_MAX)
+        secs, errs, iters_ok = 0.0, [], 0
+        for r in recs:
+            scan = veh.seq.scan(r["t"])
+            t0 = time.perf_counter()
+            tau, kappa = thr.get()
+            Po, _, so = m.register(scan, r["init"], MAX_ITERS, CONV_EPS, tau, kappa)
+            thr.update(r["init"], r["pose"])
+            if r["res"]["status"] == 0:      # a failed registration is not inserted
+                m.insert(scan, r["pose"], asmd=True, r_c=R_NEAR, r_max=R_MAX)
+            m.evict(r["pose"][:3, 3], EVICT_R)
+            secs += time.perf_counter() - t0
+            errs.append(pose_error(Po, r["pose"]))
+            iters_ok += int(so["iters"] == r["res"]["iters"])
+        out[threads] = (secs, errs, iters_ok)
+    oracle.set_threads(1)
+    pts = float(sum(r["n"] for r in recs))
+    model = cpu_model()
+
+    def base(threads):
+        secs = out[threads][0]
+        return {"value": round(pts / secs / 1e6, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                "ms_per_scan": round(1e3 * secs / len(recs), 2), "cpu_model": model, "nproc": os.cpu_count(),
+                "sample": f"scans 1-{len(recs)} of the same sequence (register + threshold + ASMD insert + "
+                          f"evict, in lockstep with the GPU's poses), FP64 oracle"
+                          + (f", per-point loops on {threads} threads" if threads > 1 else ", single thread")}
+    errs = np.array(out[1][1])
+    acc = {"scans": len(recs), "mode": "lockstep (same initial pose and the same map at every scan)",
+           "trans_m_max": float(errs[:, 0].max()), "trans_m_median": float(np.median(errs[:, 0])),
+           "rot_rad_max": float(errs[:, 1].max()), "same_iterations": out[1][2],
+           "target": "1e-4 m / 1e-5 rad"}
+    return base(max(out)), base(1), acc
 
 
 # --------------------------------------------------------------------------------------- precision report
@@ -447,7 +660,7 @@ def precision_accuracy(n_scans: int, stream):
             for t in range(n_scans + 1):
                 scan = veh.seq.scan(t)
                 if t > 0:
-                    init = veh.prior(t, veh.pose(t - 1), rng)
+                    init = veh.prior(t, [veh.pose(t - 1)], "noisy-truth", rng)
                     kw = dict(max_iters=MAX_ITERS, conv_eps=0.0, tau=2.0, kappa=2.0 / 9)
                     Tp, _, _ = gp.register(scan, init, **kw)
                     T0, _, _ = g0.register(scan, init, **kw)
@@ -479,61 +692,56 @@ def pose_error(A, B):
 
 
 # --------------------------------------------------------------------------------------- CPU oracle
-def oracle_steps(n_steps: int, rank: int = 0, time_cap_s: float = 1e9):
-    """Run the oracle over the same workload: first scan at its true pose (untimed),
-    then n_steps scans of register + threshold update + ASMD insert + eviction (timed)."""
-    import oracle
-    veh = Vehicle(rank)
-    m = oracle.OracleMap(V, NMAX, K_COV)
-    m.insert(veh.seq.scan(0), veh.seq.pose(0), asmd=True, r_c=R_NEAR, r_max=R_MAX)
-    thr = oracle.Threshold(SIGMA0, MIN_MOTION, R_MAX)
-    est = veh.seq.pose(0)
-    times, pts = [], []
-    for t in range(1, n_steps + 1):
-        scan = veh.seq.scan(t)
-        init = veh.prior(t, est)
-        t0 = time.perf_counter()
-        tau, kappa = thr.get()
-        est, _, _ = m.register(scan, init, MAX_ITERS, CONV_EPS, tau, kappa)
-        thr.update(init, est)
-        m.insert(scan, est, asmd=True, r_c=R_NEAR, r_max=R_MAX)
-        m.evict(est[:3, 3], EVICT_R)
-        times.append(time.perf_counter() - t0)
-        pts.append(scan.shape[0])
-        if sum(times) > time_cap_s:
-            break
-    return times, pts
-
-
-def cpu_baseline(n_steps: int):
-    times, pts = oracle_steps(n_steps)
-    v = sum(pts) / sum(times) / 1e6
-    return {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "ms_per_scan": round(1e3 * sum(times) / len(times), 2),
-            "sample": f"first {len(times)} scans of the same sequence (register + ASMD insert + evict), "
-                      f"single-threaded FP64 oracle on the host"}
-
-
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle (per-point loops on all host cores) over the same
+    sequence, driven by its own estimates with the same prior; the first scans run untimed
+    and the last `steps` scans are timed (register + threshold update + ASMD insert +
+    eviction per step)."""
     rank, world, local = rank_env()
     if rank != 0:
         return
-    # warm-up: build the oracle library and touch the generator
     import oracle
     oracle.build()
-    if args.warmup > 0:
-        oracle_steps(min(args.warmup, 1))
-    times, pts = oracle_steps(args.steps, time_cap_s=150.0)
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    veh = Vehicle(0)
+    n_seq = max(args.scans, 2 + args.warmup + args.steps)
+    timed_from = n_seq - args.steps
+    m = oracle.OracleMap(V, NMAX, K_COV)
+    m.insert(veh.seq.scan(0), veh.pose(0), asmd=True, r_c=R_NEAR, r_max=R_MAX)
+    thr = oracle.Threshold(SIGMA0, MIN_MOTION, R_MAX)
+    ests = [veh.pose(0)]
+    times, pts = [], []
+    prior = Prior(veh, args.prior, "oracle")
+    for t in range(1, n_seq):
+        scan = veh.seq.scan(t)
+        init = prior.init(t, ests)
+        t0 = time.perf_counter()
+        tau, kappa = thr.get()
+        est, _, st = m.register(scan, init, MAX_ITERS, CONV_EPS, tau, kappa)
+        thr.update(init, est)
+        if st["status"] == 0:
+            m.insert(scan, est, asmd=True, r_c=R_NEAR, r_max=R_MAX)
+        m.evict(est[:3, 3], EVICT_R)
+        dt = time.perf_counter() - t0
+        ests.append(est)
+        prior.observe(t, ests, st["status"] == 0)
+        if t >= timed_from:
+            times.append(dt)
+            pts.append(scan.shape[0])
     v = sum(pts) / sum(times) / 1e6
     lat = np.array(times) * 1e3
+    sample = (f"scans {timed_from}-{n_seq - 1} of the {n_seq}-scan sequence after an untimed run of the "
+              f"scans before them, FP64 oracle with its per-point loops on {threads} threads ({cpu_model()})")
     out = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": len(times),
            "warmup": args.warmup, "ms_per_step": round(float(lat.mean()), 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
-           "data": "synthetic (seeded ray-cast LiDAR)", "config": workload_config(len(times), args.warmup, world),
+           "data": "synthetic (seeded ray-cast LiDAR)",
+           "config": dict(workload_config(len(times), args.warmup, world, args.prior, n_seq), precision_mode=0,
+                          world_offset_m=[0.0, 0.0, 0.0]),
            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                           "p99": round(float(np.percentile(lat, 99)), 3)},
-           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{len(times)} consecutive scans of the sequence (capped at 150 s)"},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -450,25 +450,15 @@ __device__ __forceinline__ bool nearest27(const MapView& m, u32 max_probe, float
     return nearest27q<false>(m, max_probe, f, limit2, best_d2, best_id, best_pos, bv);
 }
 
-// Eq. 1 from k neighbour positions: Sigma-hat (1/k, about the neighbour mean),
-// C = Sigma-hat + 1e-3 I, Sigma = ||C^-1||_F C (equal to (C^-1 / ||C^-1||_F)^-1).
-// Coordinates are taken relative to the query point for FP32 accuracy.
-// pts are the neighbours' stored coordinates; off_of(p, ...) gives the frame offset of a
-// neighbour (zero for plain maps; see TileOffset).
-template <int K, class Off>
-__device__ __forceinline__ void covariance_from_neighbours_f(const float4* __restrict__ pts, const u32 (&bpos)[K],
-                                                             float qx, float qy, float qz, const Off& off_of,
-                                                             float (&c)[6]) {
+// Eq. 1 from the K neighbours' offsets r_j = p_j - q from the query point (FP32 accuracy):
+// Sigma-hat (1/K, about the neighbour mean), C = Sigma-hat + 1e-3 I, Sigma = ||C^-1||_F C
+// (equal to (C^-1 / ||C^-1||_F)^-1).
+template <int K>
+__device__ __forceinline__ void covariance_eq1_rel(const float (&rx)[K], const float (&ry)[K], const float (&rz)[K],
+                                                   float (&c)[6]) {
     float mx = 0.f, my = 0.f, mz = 0.f;
-    float rx[K], ry[K], rz[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const float4 p = __ldg(pts + bpos[j]);
-        float ox, oy, oz;
-        off_of(p, qx, qy, qz, ox, oy, oz);
-        rx[j] = __fadd_rn(p.x, ox) - qx;
-        ry[j] = __fadd_rn(p.y, oy) - qy;
-        rz[j] = __fadd_rn(p.z, oz) - qz;
         mx += rx[j];
         my += ry[j];
         mz += rz[j];
@@ -502,6 +492,26 @@ __device__ __forceinline__ void covariance_from_neighbours_f(const float4* __res
     c[3] = d * s;
     c[4] = e * s;
     c[5] = f * s;
+}
+
+// Eq. 1 from k neighbour positions read from the map: pts are the neighbours' stored
+// coordinates; off_of(p, ...) gives the frame offset of a neighbour (zero for plain maps;
+// see TileOffset).
+template <int K, class Off>
+__device__ __forceinline__ void covariance_from_neighbours_f(const float4* __restrict__ pts, const u32 (&bpos)[K],
+                                                             float qx, float qy, float qz, const Off& off_of,
+                                                             float (&c)[6]) {
+    float rx[K], ry[K], rz[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const float4 p = __ldg(pts + bpos[j]);
+        float ox, oy, oz;
+        off_of(p, qx, qy, qz, ox, oy, oz);
+        rx[j] = __fadd_rn(p.x, ox) - qx;
+        ry[j] = __fadd_rn(p.y, oy) - qy;
+        rz[j] = __fadd_rn(p.z, oz) - qz;
+    }
+    covariance_eq1_rel<K>(rx, ry, rz, c);
 }
 
 struct NoOffset {
