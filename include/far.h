@@ -236,6 +236,46 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
                             double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result);
 
 /*
+ * Motion undistortion (Sec. III-A.1). A spinning LiDAR fires its points over a sweep while
+ * it moves; each record carries its firing time tau (FP32 seconds, relative to the sweep's
+ * reference time, the last point's time stamp, so tau <= 0) at byte `time_offset_bytes`. The
+ * LiDAR's angular and linear velocity in its own frame are modelled as lines in tau,
+ * w(tau) = w0 + w1 tau and v(tau) = v0 + v1 tau (from a regression over the velocity history:
+ * far_motion_fit). A point fired at tau is moved to the reference frame by the SE(3)
+ * exponential of the twist integrated from 0 to tau:
+ *   p_ref = R p + V rho,  [phi; rho] = [w0 tau + w1 tau^2 / 2; v0 tau + v1 tau^2 / 2],
+ *   R = exp([phi]x) (Rodrigues), V the matching left Jacobian (exact for a constant twist).
+ * The kernel computes in FP32 (Taylor series of R and V below |phi| = 0.25 rad).
+ */
+typedef struct far_motion {
+    double w0[3], w1[3];          /* rad/s, rad/s^2 */
+    double v0[3], v1[3];          /* m/s, m/s^2 */
+    uint32_t time_offset_bytes;   /* offset of tau in each record: a multiple of 4, 12..stride_bytes - 4 */
+} far_motion;
+/*
+ * Least-squares lines through n samples (times t[i] in seconds, rates w[3 i..], velocities
+ * v[3 i..], LiDAR frame) as functions of t - t_ref; one distinct time stamp gives constants.
+ * Host code; fills every field of `out` (time_offset_bytes as given).
+ */
+far_status far_motion_fit(const double* t, const double* w, const double* v, uint32_t n, double t_ref,
+                          uint32_t time_offset_bytes, far_motion* out);
+/*
+ * The de-skew alone (parity): n records of stride_bytes (>= 16) on the device -> out_xyz
+ * (device, 3 n floats, the points at the reference time). Runs on cuda_stream, synchronises it.
+ */
+far_status far_undistort(const float* xyz, uint64_t n, uint32_t stride_bytes, const far_motion* motion,
+                         float* out_xyz, void* cuda_stream);
+/*
+ * far_process_scan with the de-skew fused into the ingest of the scan (motion NULL: none).
+ * Host records wider than 32 bytes need time_offset_bytes <= 28. The registered pose is
+ * the pose at the sweep's reference time.
+ */
+far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                                   const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
+                                   const far_insert_params* ins, double evict_radius, double out_pose[16],
+                                   double out_cov[36], far_step_result* result);
+
+/*
  * Batched registration: many independent problems (each scan against its own map) run
  * together. Per problem the scan-local sources are built on worker streams; then every
  * Gauss-Newton iteration is ONE linearisation launch whose resident grid is shared by all

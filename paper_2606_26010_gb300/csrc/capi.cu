@@ -267,21 +267,50 @@ bool is_device_pointer(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// a1: bring the caller's points (host or device, AoS with stride) into s.in4.
-far_status ingest(far_map* m, const float* xyz, u32 n, u32 stride) {
+// The FP32 copy of a sweep's motion model, checked: finite, and a time offset that lies inside
+// the record after x, y, z, 4-byte aligned.
+far_status sweep_motion(const far_motion* mo, uint32_t stride, SweepMotion* out) {
+    for (int a = 0; a < 3; ++a) {
+        const double v[4] = {mo->w0[a], mo->w1[a], mo->v0[a], mo->v1[a]};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(FAR_ERR_INVALID, "motion: velocities must be finite");
+        out->w0[a] = (float)mo->w0[a];
+        out->w1[a] = (float)mo->w1[a];
+        out->v0[a] = (float)mo->v0[a];
+        out->v1[a] = (float)mo->v1[a];
+    }
+    if (mo->time_offset_bytes < 12 || mo->time_offset_bytes % 4 != 0 || mo->time_offset_bytes + 4 > stride)
+        return fail(FAR_ERR_INVALID, "motion: time_offset_bytes must be a multiple of 4 in [12, stride_bytes - 4]");
+    out->time_offset = mo->time_offset_bytes;
+    return FAR_OK;
+}
+
+// a1: bring the caller's points (host or device, AoS with stride) into s.in4; with a motion
+// model, each point is first moved to the sweep's reference time (Sec. III-A.1).
+far_status ingest(far_map* m, const float* xyz, u32 n, u32 stride, const far_motion* motion = nullptr) {
     if (n == 0) return FAR_OK;
+    SweepMotion mo;
+    if (motion) {
+        far_status st = sweep_motion(motion, stride, &mo);
+        if (st != FAR_OK) return st;
+    }
     const void* src = xyz;
     u32 eff = stride;
     if (!is_device_pointer(xyz)) {
         if (stride <= 32) {
             CK(cudaMemcpyAsync(m->s.staging, xyz, (size_t)n * stride, cudaMemcpyHostToDevice, m->stream));
         } else {
-            CK(cudaMemcpy2DAsync(m->s.staging, 16, xyz, stride, 12, n, cudaMemcpyHostToDevice, m->stream));
-            eff = 16;
+            // copy x, y, z (and the time stamp) of each record into 32-byte staging records
+            const u32 width = motion ? mo.time_offset + 4 : 12;
+            if (width > 32)
+                return fail(FAR_ERR_INVALID, "host records wider than 32 bytes need time_offset_bytes <= 28");
+            CK(cudaMemcpy2DAsync(m->s.staging, 32, xyz, stride, width, n, cudaMemcpyHostToDevice, m->stream));
+            eff = 32;
         }
         src = m->s.staging;
     }
-    CK(pack_points(src, n, eff, m->s.in4, m->stream));
+    if (motion) CK(pack_points_deskew(src, n, eff, mo, m->s.in4, m->stream));
+    else CK(pack_points(src, n, eff, m->s.in4, m->stream));
     return FAR_OK;
 }
 
@@ -921,6 +950,14 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
 far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
                             const double init_pose[16], const far_reg_params* reg, const far_insert_params* ins,
                             double evict_radius, double out_pose[16], double out_cov[36], far_step_result* result) {
+    return far_process_scan_motion(map, xyz, n, stride_bytes, nullptr, init_pose, reg, ins, evict_radius, out_pose,
+                                   out_cov, result);
+}
+
+far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                                   const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
+                                   const far_insert_params* ins, double evict_radius, double out_pose[16],
+                                   double out_cov[36], far_step_result* result) {
     far_status st = check_points(map, xyz, n, stride_bytes);
     if (st != FAR_OK) return st;
     if (!reg || !init_pose || !finite_pose(init_pose) || !out_pose)
@@ -939,7 +976,7 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     const u32 nn = (u32)n;
     reset_marks(map);
     mark(map, EV_INGEST);
-    if ((st = ingest(map, xyz, nn, stride_bytes)) != FAR_OK) return st;
+    if ((st = ingest(map, xyz, nn, stride_bytes, motion)) != FAR_OK) return st;
     mark(map, EV_SOURCES);
     if (nn) {
         if ((st = build_sources(map, nn, nullptr)) != FAR_OK) return st;
@@ -997,6 +1034,65 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
     }
     if (res == FAR_OK) return check_device_errors(map, "far_process_scan");
     return res;
+}
+
+// ---------------------------------------------------------------- motion undistortion (Sec. III-A.1)
+far_status far_motion_fit(const double* t, const double* w, const double* v, uint32_t n, double t_ref,
+                          uint32_t time_offset_bytes, far_motion* out) {
+    if (!t || !w || !v || !out) return fail(FAR_ERR_INVALID, "far_motion_fit: NULL argument");
+    if (n < 1) return fail(FAR_ERR_INVALID, "far_motion_fit: no samples");
+    if (!std::isfinite(t_ref)) return fail(FAR_ERR_INVALID, "far_motion_fit: t_ref not finite");
+    for (uint32_t i = 0; i < n; ++i)
+        if (!std::isfinite(t[i]) || !std::isfinite(w[3 * i]) || !std::isfinite(w[3 * i + 1]) ||
+            !std::isfinite(w[3 * i + 2]) || !std::isfinite(v[3 * i]) || !std::isfinite(v[3 * i + 1]) ||
+            !std::isfinite(v[3 * i + 2]))
+            return fail(FAR_ERR_INVALID, "far_motion_fit: non-finite sample");
+    // least-squares line y = a + b (t - t_ref) per component, about the mean time for accuracy
+    double tm = 0.0;
+    for (uint32_t i = 0; i < n; ++i) tm += t[i] - t_ref;
+    tm /= n;
+    double stt = 0.0;
+    for (uint32_t i = 0; i < n; ++i) stt += (t[i] - t_ref - tm) * (t[i] - t_ref - tm);
+    far_motion m{};
+    for (int a = 0; a < 6; ++a) {
+        const double* y = a < 3 ? w : v;
+        const int c = a % 3;
+        double ym = 0.0;
+        for (uint32_t i = 0; i < n; ++i) ym += y[3 * i + c];
+        ym /= n;
+        double sty = 0.0;
+        for (uint32_t i = 0; i < n; ++i) sty += (t[i] - t_ref - tm) * (y[3 * i + c] - ym);
+        const double slope = stt > 0.0 ? sty / stt : 0.0;   // one time stamp: a constant
+        const double icpt = ym - slope * tm;
+        if (a < 3) {
+            m.w0[c] = icpt;
+            m.w1[c] = slope;
+        } else {
+            m.v0[c] = icpt;
+            m.v1[c] = slope;
+        }
+    }
+    m.time_offset_bytes = time_offset_bytes;
+    *out = m;
+    return FAR_OK;
+}
+
+far_status far_undistort(const float* xyz, uint64_t n, uint32_t stride_bytes, const far_motion* motion,
+                         float* out_xyz, void* cuda_stream) {
+    if (!motion) return fail(FAR_ERR_INVALID, "far_undistort: motion is NULL");
+    if (n == 0) return FAR_OK;
+    if (!xyz || !out_xyz || !is_device_pointer(xyz) || !is_device_pointer(out_xyz))
+        return fail(FAR_ERR_INVALID, "far_undistort: xyz and out_xyz must be device pointers");
+    if (n > 0xFFFFFFFFull) return fail(FAR_ERR_INVALID, "far_undistort: n exceeds 2^32 - 1");
+    if (stride_bytes < 16 || stride_bytes % 4 != 0)
+        return fail(FAR_ERR_INVALID, "far_undistort: stride_bytes must be >= 16 and a multiple of 4");
+    SweepMotion mo;
+    far_status st = sweep_motion(motion, stride_bytes, &mo);
+    if (st != FAR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CK(deskew_points(xyz, (u32)n, stride_bytes, mo, out_xyz, s));
+    CK(cudaStreamSynchronize(s));
+    return FAR_OK;
 }
 
 // ---------------------------------------------------------------- batched registration

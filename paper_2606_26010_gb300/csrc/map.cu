@@ -32,6 +32,61 @@ __global__ void k_pack(const char* __restrict__ src, u32 n, u32 stride, float4* 
     out[i] = make_float4(p[0], p[1], p[2], __uint_as_float(i));
 }
 
+// Sec. III-A.1 motion undistortion of one point (FP32): the LiDAR pose at its firing time tau,
+// relative to the reference time, is the SE(3) exponential of the twist integrated from 0 to
+// tau, [phi; rho] = [w0 tau + w1 tau^2 / 2; v0 tau + v1 tau^2 / 2]; the point moves to
+// p_ref = R(phi) p + V(phi) rho with R = I + A [phi]x + B [phi]x^2, V = I + B [phi]x + C [phi]x^2,
+// A = sin(t)/t, B = (1 - cos t)/t^2, C = (t - sin t)/t^3, t = |phi| (Taylor series below t = 0.25,
+// terms to t^6; the first omitted term is below 1e-8 of the leading one).
+__device__ __forceinline__ float3 deskew_point(float x, float y, float z, float tau, const SweepMotion& mo) {
+    const float h = 0.5f * tau * tau;
+    float ph[3], ro[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ph[a] = fmaf(mo.w1[a], h, mo.w0[a] * tau);
+        ro[a] = fmaf(mo.v1[a], h, mo.v0[a] * tau);
+    }
+    const float t2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
+    float A, B, C;
+    if (t2 < 0.0625f) {
+        A = 1.0f - t2 * (1.0f / 6.0f) * (1.0f - t2 * (1.0f / 20.0f) * (1.0f - t2 * (1.0f / 42.0f)));
+        B = 0.5f * (1.0f - t2 * (1.0f / 12.0f) * (1.0f - t2 * (1.0f / 30.0f) * (1.0f - t2 * (1.0f / 56.0f))));
+        C = (1.0f / 6.0f) * (1.0f - t2 * (1.0f / 20.0f) * (1.0f - t2 * (1.0f / 42.0f) * (1.0f - t2 * (1.0f / 72.0f))));
+    } else {
+        const float t = sqrtf(t2);
+        float sn, cs;
+        sincosf(t, &sn, &cs);
+        A = sn / t;
+        B = (1.0f - cs) / t2;
+        C = (t - sn) / (t2 * t);
+    }
+    // [phi]x p and [phi]x^2 p = phi x (phi x p)
+    const float c1x = ph[1] * z - ph[2] * y, c1y = ph[2] * x - ph[0] * z, c1z = ph[0] * y - ph[1] * x;
+    const float c2x = ph[1] * c1z - ph[2] * c1y, c2y = ph[2] * c1x - ph[0] * c1z, c2z = ph[0] * c1y - ph[1] * c1x;
+    const float r1x = ph[1] * ro[2] - ph[2] * ro[1], r1y = ph[2] * ro[0] - ph[0] * ro[2], r1z = ph[0] * ro[1] - ph[1] * ro[0];
+    const float r2x = ph[1] * r1z - ph[2] * r1y, r2y = ph[2] * r1x - ph[0] * r1z, r2z = ph[0] * r1y - ph[1] * r1x;
+    const float tx = ro[0] + B * r1x + C * r2x, ty = ro[1] + B * r1y + C * r2y, tz = ro[2] + B * r1z + C * r2z;
+    return make_float3(x + A * c1x + B * c2x + tx, y + A * c1y + B * c2y + ty, z + A * c1z + B * c2z + tz);
+}
+
+__global__ void k_pack_deskew(const char* __restrict__ src, u32 n, u32 stride, SweepMotion mo,
+                              float4* __restrict__ out4, float* __restrict__ out3) {
+    pdl_wait();
+    pdl_trigger();
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const char* rec = src + (size_t)i * stride;
+    const float* p = reinterpret_cast<const float*>(rec);
+    const float tau = *reinterpret_cast<const float*>(rec + mo.time_offset);
+    const float3 q = deskew_point(p[0], p[1], p[2], tau, mo);
+    if (out4) out4[i] = make_float4(q.x, q.y, q.z, __uint_as_float(i));
+    if (out3) {
+        out3[3 * (size_t)i] = q.x;
+        out3[3 * (size_t)i + 1] = q.y;
+        out3[3 * (size_t)i + 2] = q.z;
+    }
+}
+
 // a11: x_w = fp32(((R0 x + R1 y) + R2 z) + t) in FP64 without contraction; then the key.
 // Precision variant (tv > 0): x_w stays FP64, the key follows the tile reading and `world`
 // receives the coordinates relative to the tile origin.
@@ -210,9 +265,9 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
 }
 
 // Sort of one group's input indices by one warp (values are distinct): up to 512 in
-// registers (bitonic network over 32 lanes x R values), larger groups as chunks of GS_SMEM
-// sorted in the warp's shared memory and merged through `tmp` (at most 32 chunks). Returns
-// false when the group is too large.
+// registers (bitonic network over 32 lanes x R values), up to 1024 as two such halves merged
+// along the merge path, larger groups as chunks of GS_SMEM sorted in the warp's shared memory
+// and merged through `tmp` (at most 32 chunks). Returns false when the group is too large.
 constexpr int GS_SMEM = 1024;
 constexpr int GS_WARPS = TPB / 32;
 
@@ -296,6 +351,39 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
     }
     if (size <= 512) {
         sort_group_regs<16>(a, size, lane);
+        return true;
+    }
+    if (size <= 1024) {
+        // two halves sorted in registers, then merged from shared memory: lane l produces the
+        // outputs [32 l, 32 l + 32) of the merge, starting where the merge path crosses that
+        // diagonal (binary search; the values are distinct)
+        sort_group_regs<16>(a, 512, lane);
+        sort_group_regs<16>(a + 512, size - 512, lane);
+        for (u32 i = lane; i < size; i += 32) buf[i] = a[i];
+        __syncwarp();
+        const u32 na = 512, nb = size - 512;
+        const u32* A = buf;
+        const u32* B = buf + 512;
+        const u32 d = (u32)lane * 32u;
+        if (d < size) {
+            u32 lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+            while (lo < hi) {
+                const u32 mid = (lo + hi) >> 1;
+                if (A[mid] < B[d - mid - 1]) lo = mid + 1;
+                else hi = mid;
+            }
+            u32 i = lo, j = d - lo;
+            const u32 end = min(d + 32u, size);
+            for (u32 o = d; o < end; ++o) {
+                const bool take_a = j >= nb || (i < na && A[i] < B[j]);
+                tmp[o] = take_a ? A[i] : B[j];
+                if (take_a) ++i;
+                else ++j;
+            }
+        }
+        __syncwarp();
+        for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
+        __syncwarp();
         return true;
     }
     const u32 chunks = (size + GS_SMEM - 1) / GS_SMEM;
@@ -1102,6 +1190,21 @@ cudaError_t knn_cov_tile(const DeviceMap& m, const u32* qpos, const u64* qkey, u
         cudaError_t e__ = (x);                      \
         if (e__ != cudaSuccess) return e__;         \
     } while (0)
+
+cudaError_t pack_points_deskew(const void* src, u32 n, u32 stride, const SweepMotion& mo, float4* out,
+                               cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_pack_deskew, blocks_for(n), TPB, 0, st, static_cast<const char*>(src), n, stride, mo, out,
+               (float*)nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t deskew_points(const void* src, u32 n, u32 stride, const SweepMotion& mo, float* out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    FAR_LAUNCH(k_pack_deskew, blocks_for(n), TPB, 0, st, static_cast<const char*>(src), n, stride, mo,
+               (float4*)nullptr, out);
+    return cudaGetLastError();
+}
 
 cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

@@ -111,6 +111,23 @@ struct Pose12 {
     double m[12];
 };
 
+// Motion of the LiDAR during a sweep (Sec. III-A.1): angular and linear velocity in the LiDAR
+// frame as lines in the time tau relative to the reference time, w(tau) = w0 + w1 tau,
+// v(tau) = v0 + v1 tau (FP32 copies of the caller's values), and the byte offset of each
+// record's FP32 tau.
+struct SweepMotion {
+    float w0[3], w1[3], v0[3], v1[3];
+    u32 time_offset;
+};
+
+// Pack `n` records of `stride` bytes (first 12 bytes xyz) into s.in4 (w = index), each point
+// first moved to the reference time of the sweep: p_ref = exp(integral of the twist from 0 to
+// tau) p, the exponential of [phi; rho] = [w0 tau + w1 tau^2 / 2; v0 tau + v1 tau^2 / 2].
+cudaError_t pack_points_deskew(const void* src, u32 n, u32 stride, const SweepMotion& mo, float4* out,
+                               cudaStream_t st);
+// The same de-skew into a dense (n, 3) FP32 array (the stage entry point).
+cudaError_t deskew_points(const void* src, u32 n, u32 stride, const SweepMotion& mo, float* out, cudaStream_t st);
+
 // Pack `n` records of `stride` bytes (first 12 bytes xyz) into s.in4 (w = index).
 cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStream_t st);
 

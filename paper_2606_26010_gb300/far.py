@@ -90,6 +90,23 @@ class ThresholdState(ctypes.Structure):
                 ("sse", ctypes.c_double), ("n", ctypes.c_int64)]
 
 
+class Motion(ctypes.Structure):
+    """far_motion: w(tau) = w0 + w1 tau, v(tau) = v0 + v1 tau (LiDAR frame), tau at time_offset_bytes."""
+    _fields_ = [("w0", ctypes.c_double * 3), ("w1", ctypes.c_double * 3), ("v0", ctypes.c_double * 3),
+                ("v1", ctypes.c_double * 3), ("time_offset_bytes", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: (list(getattr(self, f)) if f != "time_offset_bytes" else self.time_offset_bytes)
+                for f, _ in self._fields_}
+
+
+def make_motion(w0=(0, 0, 0), w1=(0, 0, 0), v0=(0, 0, 0), v1=(0, 0, 0), time_offset_bytes=12) -> Motion:
+    m = Motion()
+    m.w0[:], m.w1[:], m.v0[:], m.v1[:] = ([float(x) for x in a] for a in (w0, w1, v0, v1))
+    m.time_offset_bytes = int(time_offset_bytes)
+    return m
+
+
 class EkfParams(ctypes.Structure):
     _fields_ = [("gravity", ctypes.c_double), ("acc_bias", ctypes.c_double * 3), ("gyro_bias", ctypes.c_double * 3),
                 ("q", ctypes.c_double * 9), ("r", ctypes.c_double * 9), ("history", ctypes.c_uint32)]
@@ -137,6 +154,10 @@ _SIGS = {
     "far_ekf_predict": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
     "far_ekf_update": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
     "far_ekf_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "far_motion_fit": (ctypes.c_int, [_vp, _vp, _vp, _u32, ctypes.c_double, _u32, _vp]),
+    "far_undistort": (ctypes.c_int, [_vp, _u64, _u32, _vp, _vp, _vp]),
+    "far_process_scan_motion": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, ctypes.c_double, _vp,
+                                               _vp, _vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -341,7 +362,8 @@ class VoxelMap:
         return pose.reshape(4, 4), cov.reshape(6, 6), st.as_dict()
 
     def process_scan(self, xyz, init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0, time_budget_s=0.0,
-                     asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0, want_cov=False, threads_per_point=0):
+                     asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0, want_cov=False, threads_per_point=0,
+                     motion=None):
         """Register, insert at the registered pose and evict, all on the device (one sync).
         Returns (pose 4x4, cov 6x6 or None, result dict); degenerate/timed-out scans are
         reported in result['status'] and not inserted."""
@@ -351,9 +373,15 @@ class VoxelMap:
         pose = np.zeros(16)
         cov = np.zeros(36) if want_cov else None
         res = StepResult()
-        _check(self._L.far_process_scan(self._h, ptr, n, stride, _p(_pose(init)), ctypes.byref(prm),
-                                        ctypes.byref(ins), float(evict_radius), _p(pose), _p(cov),
-                                        ctypes.byref(res)), allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
+        if motion is None:
+            _check(self._L.far_process_scan(self._h, ptr, n, stride, _p(_pose(init)), ctypes.byref(prm),
+                                            ctypes.byref(ins), float(evict_radius), _p(pose), _p(cov),
+                                            ctypes.byref(res)), allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
+        else:
+            _check(self._L.far_process_scan_motion(self._h, ptr, n, stride, ctypes.byref(motion), _p(_pose(init)),
+                                                   ctypes.byref(prm), ctypes.byref(ins), float(evict_radius),
+                                                   _p(pose), _p(cov), ctypes.byref(res)),
+                   allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
         return pose.reshape(4, 4), (cov.reshape(6, 6) if want_cov else None), res.as_dict()
 
     # ---- instrumentation
@@ -473,6 +501,28 @@ class Threshold:
 
     def update(self, init, result):
         _check(self._L.far_threshold_update(ctypes.byref(self._s), _p(_pose(init)), _p(_pose(result))))
+
+
+def motion_fit(t, w, v, t_ref, time_offset_bytes=12) -> Motion:
+    """far_motion_fit: least-squares lines of the rates and velocities about t_ref."""
+    t = np.ascontiguousarray(t, np.float64).reshape(-1)
+    w = np.ascontiguousarray(w, np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+    m = Motion()
+    _check(lib().far_motion_fit(_p(t), _p(w), _p(v), t.shape[0], float(t_ref), int(time_offset_bytes), ctypes.byref(m)))
+    return m
+
+
+def undistort(points, motion: Motion, stream=None):
+    """far_undistort on a device tensor of (n, >= 4) float32 records; returns a (n, 3) device tensor."""
+    import torch
+    if not isinstance(points, torch.Tensor) or not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor")
+    ptr, n, stride, keep = _points(points)
+    out = torch.empty((n, 3), dtype=torch.float32, device=points.device)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().far_undistort(ptr, n, stride, ctypes.byref(motion), out.data_ptr() if n else None, s))
+    return out
 
 
 def lidar_velocity(T_prev, T_cur, dt) -> np.ndarray:

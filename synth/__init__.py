@@ -49,6 +49,12 @@ def _load():
             ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
             ctypes.c_void_p, ctypes.c_int32]
+        lib.synth_raycast_columns.restype = ctypes.c_int64
+        lib.synth_raycast_columns.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -312,6 +318,38 @@ class TrackSequence:
         return self._cache[t]
 
 
+def raycast_sweep(scene: Scene, lidar: Lidar, column_poses: np.ndarray, seed: int, scan_id: int, reach: float,
+                  nthreads: int | None = None):
+    """A sweep whose azimuth columns fire from their own poses (column_poses: az_bins x 4 x 4).
+    Returns (points (n, 3) float32 in each column's sensor frame, column index (n,) int32)."""
+    lib = _load()
+    prims = scene.prims
+    poses = np.ascontiguousarray(column_poses, dtype=np.float64).reshape(lidar.az_bins, 16)
+    out = np.empty((lidar.n_rays, 3), dtype=np.float32)
+    col = np.empty(lidar.n_rays, dtype=np.int32)
+    nth = nthreads or min(16, os.cpu_count() or 1)
+    n = lib.synth_raycast_columns(prims.ctypes.data, prims.shape[0], poses.ctypes.data, reach, lidar.beams,
+                                  lidar.az_bins, lidar.el_min_deg, lidar.el_max_deg, lidar.r_min, lidar.r_max,
+                                  lidar.sigma, seed & (2**64 - 1), scan_id, out.ctypes.data, col.ctypes.data, nth)
+    return np.ascontiguousarray(out[:n]), np.ascontiguousarray(col[:n])
+
+
+def skewed_scan(seq: "TrackSequence", t: int) -> np.ndarray:
+    """Scan t of the sequence taken by a spinning sensor that moves during its 0.1 s sweep:
+    (n, 4) float32 records (x, y, z, tau), tau the firing time relative to the scan's last
+    column (the reference time t / 10 s; -0.1 s < tau <= 0), each point in the sensor frame
+    of its firing time."""
+    az = seq.lidar.az_bins
+    period = 1.0 / FRAME_RATE_HZ
+    taus = -period + period * (np.arange(az) + 1) / az
+    poses = np.stack([sequence_pose_at(seq, t * period + tau) for tau in taus])
+    pts, col = raycast_sweep(seq.scene, seq.lidar, poses, seq.seed, t, reach=seq.step * 1.5)
+    out = np.empty((pts.shape[0], 4), np.float32)
+    out[:, :3] = pts
+    out[:, 3] = taus[col].astype(np.float32)
+    return out
+
+
 def constant_velocity_guess(prev2: np.ndarray, prev1: np.ndarray) -> np.ndarray:
     """T_{t} ~= T_{t-1} (T_{t-2}^-1 T_{t-1})."""
     return prev1 @ (np.linalg.inv(prev2) @ prev1)
@@ -354,6 +392,16 @@ def track_imu(seq: "TrackSequence", t0: float, t1: float, rate_hz: float = 100.0
         acc.append(f + rng.normal(scale=acc_sigma, size=3) if acc_sigma > 0 else f)
         gyro.append(w + rng.normal(scale=gyro_sigma, size=3) if gyro_sigma > 0 else w)
     return np.array(times), np.array(acc).reshape(-1, 3), np.array(gyro).reshape(-1, 3)
+
+
+def track_body_twist(seq: "TrackSequence", time_s: float):
+    """(angular rate, linear velocity) of the sensor in its own frame at a continuous time,
+    from central differences of the analytic pose."""
+    h = 1e-4
+    Tm, T0, Tp = sequence_pose_at(seq, time_s - h), sequence_pose_at(seq, time_s), sequence_pose_at(seq, time_s + h)
+    W = T0[:3, :3].T @ ((Tp[:3, :3] - Tm[:3, :3]) / (2 * h))
+    w = 0.5 * np.array([W[2, 1] - W[1, 2], W[0, 2] - W[2, 0], W[1, 0] - W[0, 1]])
+    return w, T0[:3, :3].T @ ((Tp[:3, 3] - Tm[:3, 3]) / (2 * h))
 
 
 def track_body_velocity(seq: "TrackSequence", time_s: float) -> np.ndarray:

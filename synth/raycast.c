@@ -194,3 +194,74 @@ int64_t synth_raycast(const double* prims, int64_t nprims, const double* pose,
     free(keep);
     return n;
 }
+
+
+/*
+ * A spinning sweep with motion: azimuth column a is fired from the sensor pose
+ * poses[16 a .. 16 a + 15] (row-major 4x4, sensor to world) and its hits are written
+ * in that pose's sensor frame, with the column index in out_col. Primitives are culled
+ * around the first and last poses with r_max + reach. Same noise stream as
+ * synth_raycast (seed, scan id, ray index).
+ */
+int64_t synth_raycast_columns(const double* prims, int64_t nprims, const double* poses, double reach,
+                              int32_t beams, int32_t az_bins, double el_min_deg, double el_max_deg,
+                              double r_min, double r_max, double sigma, uint64_t seed, uint64_t scan_id,
+                              float* out_xyz, int32_t* out_col, int32_t nthreads) {
+    const double deg = 3.14159265358979323846 / 180.0;
+    int64_t nrays = (int64_t)beams * az_bins;
+    const double* last = poses + 16 * (int64_t)(az_bins - 1);
+    int64_t* keep = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nprims > 0 ? nprims : 1));
+    int64_t nkeep = 0;
+    for (int64_t i = 0; i < nprims; ++i) {
+        double cx, cy, rad;
+        prim_bound(prims + i * PRIM_STRIDE, &cx, &cy, &rad);
+        if (hypot(cx - last[3], cy - last[7]) - rad <= r_max + reach ||
+            hypot(cx - poses[3], cy - poses[7]) - rad <= r_max + reach)
+            keep[nkeep++] = i;
+    }
+    float* tmp = (float*)malloc(sizeof(float) * 3 * (size_t)nrays);
+    unsigned char* hit = (unsigned char*)malloc((size_t)nrays);
+
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+    for (int32_t a = 0; a < az_bins; ++a) {
+        const double* pose = poses + 16 * (int64_t)a;
+        double o[3] = {pose[3], pose[7], pose[11]};
+        double az = 2.0 * 3.14159265358979323846 * (double)a / (double)az_bins;
+        for (int32_t b = 0; b < beams; ++b) {
+            int64_t ray = (int64_t)a * beams + b;
+            double el = (beams > 1) ? (el_min_deg + (el_max_deg - el_min_deg) * (double)b / (double)(beams - 1)) * deg
+                                    : el_min_deg * deg;
+            double ds[3] = {cos(el) * cos(az), cos(el) * sin(az), sin(el)};
+            double dw[3];
+            for (int k = 0; k < 3; ++k)
+                dw[k] = pose[4 * k + 0] * ds[0] + pose[4 * k + 1] * ds[1] + pose[4 * k + 2] * ds[2];
+            double best = INFINITY;
+            if (dw[2] < -1e-12) best = -o[2] / dw[2];
+            for (int64_t j = 0; j < nkeep; ++j) {
+                double t = hit_prim(prims + keep[j] * PRIM_STRIDE, o, dw);
+                if (t < best) best = t;
+            }
+            hit[ray] = 0;
+            if (best >= r_min && best <= r_max) {
+                double rng = best + sigma * gauss(seed, scan_id, (uint64_t)ray);
+                if (rng > 0.0) {
+                    tmp[3 * ray + 0] = (float)(ds[0] * rng);
+                    tmp[3 * ray + 1] = (float)(ds[1] * rng);
+                    tmp[3 * ray + 2] = (float)(ds[2] * rng);
+                    hit[ray] = 1;
+                }
+            }
+        }
+    }
+    int64_t n = 0;
+    for (int64_t r = 0; r < nrays; ++r) {
+        if (!hit[r]) continue;
+        memcpy(out_xyz + 3 * n, tmp + 3 * r, 3 * sizeof(float));
+        out_col[n] = (int32_t)(r / beams);
+        ++n;
+    }
+    free(tmp);
+    free(hit);
+    free(keep);
+    return n;
+}
