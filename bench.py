@@ -53,7 +53,7 @@ PRIOR_NOISE = (0.05, 0.1)   # IMU-like prior: metres, degrees per frame
 SEQ_SCANS = 200             # the high-speed sequence: 200 scans (1.4 km)
 
 
-def workload_config(steps, warmup, n_gpus, prior="ekf", n_seq=SEQ_SCANS):
+def workload_config(steps, warmup, n_gpus, prior="ekf", n_seq=SEQ_SCANS, skew=True):
     return {
         "workload": "high-speed sequence: 128x2048 LiDAR (~260k pts/scan, sigma 0.03 m), 70 m/s at 10 Hz "
                     "on a walled oval (700 m straights, R 120 m), per-scan register + ASMD insert + evict",
@@ -61,6 +61,9 @@ def workload_config(steps, warmup, n_gpus, prior="ekf", n_seq=SEQ_SCANS):
         "conv_eps": CONV_EPS, "asmd": {"r_near_m": R_NEAR, "r_max_m": R_MAX}, "evict_radius_m": EVICT_R,
         "threshold": {"sigma0_m": SIGMA0, "min_motion_m": MIN_MOTION},
         "init_prior": PRIOR_LABELS[prior],
+        "sweep": ("each sweep taken while moving (0.1 s, 2048 azimuth columns fired from their own poses, "
+                  "records x, y, z, tau); de-skewed in the scan ingest from lines fitted to the EKF's velocity "
+                  "history (Sec. III-A.1)") if skew else "every point at the frame pose (no de-skew)",
         "scans_timed": steps, "scans_warmup": warmup,
         "timed_window": f"scans {n_seq - steps}-{n_seq - 1} (the end of the sequence; scans 1-{n_seq - steps - 1} "
                         f"run first, untimed, the last {warmup} of them as warm-up)",
@@ -80,6 +83,9 @@ def parse_args():
                     help="sequence: the 128x2048 high-speed sequence (default); batched: 64 uneven problems; "
                          "serving: 16 vehicles streaming scans")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
+    ap.add_argument("--load-compression", type=float, default=8.0,
+                    help="serving: the fleet's arrivals (and motion) replayed this many times faster as a second "
+                         "run near the server's capacity (0 = skip)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
                     help="1 = tile-relative points, FP16 covariances (precision_mode 1); default: 0 for the "
                          "sequence, 1 for the batched workload")
@@ -93,6 +99,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-steps", type=int, default=20,
                     help="scans of the oracle comparison and CPU baseline (lockstep with the GPU's poses)")
     ap.add_argument("--prior", choices=["ekf", "cv", "noisy-truth"], default="ekf")
+    ap.add_argument("--no-skew", dest="skew", action="store_false",
+                    help="scans taken at rest at the frame pose (no motion during the sweep, no de-skew)")
     ap.add_argument("--scans", type=int, default=SEQ_SCANS, help="sequence length (scans)")
     ap.add_argument("--max-voxels", type=int, default=MAX_VOXELS,
                     help="bucket pool of the map (smaller values shrink the device footprint for profiling)")
@@ -157,14 +165,14 @@ EKF_R = [1e-4] * 3 + [1e-6] * 3 + [0.05] * 3
 
 
 class Prior:
-    """Initial poses of the scans of one run: `init(t, ests)` before scan t, `observe(t, ests)`
-    after it (ests: the estimates of scans 0..t). For the EKF prior the filter is the library's
-    (product arm) or the oracle's (reference arm); both run on the host."""
+    """Initial poses and sweep motion models of the scans of one run: `init(t, ests)` before
+    scan t, `motion(t)` for its de-skew, `observe(t, ests)` after it (ests: the estimates of
+    scans 0..t). The kinematic EKF always runs on the host (the library's for the product arm,
+    the oracle's for the reference arm): it supplies the velocity history that the de-skew's
+    motion lines are fitted to, and with the "ekf" prior also the initial pose."""
 
     def __init__(self, veh: Vehicle, kind: str, impl: str = "library", rng=None):
-        self.veh, self.kind, self.rng = veh, kind, rng
-        if kind != "ekf":
-            return
+        self.veh, self.kind, self.rng, self.impl = veh, kind, rng, impl
         seq = veh.seq
         self.frame_dt = 1.0 / synth.FRAME_RATE_HZ
         x0 = np.concatenate([veh.pose(0)[:3, 3], euler_zyx(veh.pose(0)[:3, :3]), synth.track_body_velocity(seq, 0.0)])
@@ -172,27 +180,47 @@ class Prior:
             from paper_2606_26010_gb300 import far
             self.ekf = far.Ekf(x0, np.diag(EKF_P0), EKF_Q, EKF_R, t0=0.0, history=64)
             self.vel = far.lidar_velocity
+            self.state_v = lambda: self.ekf.get()[1][6:9]
         else:
             from oracle import ekf as oe
             self.ekf = oe.KinematicEKF(x0, np.diag(EKF_P0), EKF_Q, EKF_R, t0=0.0, history=64)
             self.vel = oe.lidar_velocity
+            self.state_v = lambda: self.ekf.x[6:9].copy()
         self.imu = imu_stream(veh)
-        self.k = 0   # next IMU sample
+        self.k = 0            # next IMU sample
+        self.samples = []     # (time, measured rate, filtered body velocity) after each prediction
 
     def _predict_to(self, t_s: float):
         times, acc, gyro = self.imu
         while self.k < len(times) and times[self.k] <= t_s + 1e-9:
             self.ekf.predict(times[self.k], acc[self.k], gyro[self.k])
+            self.samples.append((times[self.k], gyro[self.k], self.state_v()))
             self.k += 1
+        if len(self.samples) > 64:
+            del self.samples[:-64]
 
     def init(self, t: int, ests) -> np.ndarray:
+        self._predict_to(t * self.frame_dt)
         if self.kind == "ekf":
-            self._predict_to(t * self.frame_dt)
             return self.ekf.pose()
         return self.veh.prior(t, ests, self.kind, self.rng)
 
+    def motion(self, t: int):
+        """Lines through the rates and velocities of scan t's sweep (its 0.1 s up to t / 10 s):
+        far_motion_fit (library) or the oracle's fit, as a far.Motion or a dict."""
+        t_ref = t * self.frame_dt
+        sel = [s_ for s_ in self.samples if t_ref - self.frame_dt - 1e-9 < s_[0] <= t_ref + 1e-9]
+        tt = np.array([s_[0] for s_ in sel])
+        w = np.array([s_[1] for s_ in sel])
+        v = np.array([s_[2] for s_ in sel])
+        if self.impl == "library":
+            from paper_2606_26010_gb300 import far
+            return far.motion_fit(tt, w, v, t_ref, time_offset_bytes=12)
+        from oracle import deskew as od
+        return od.motion_fit(tt, w, v, t_ref)
+
     def observe(self, t: int, ests, ok: bool = True):
-        if self.kind != "ekf" or not ok:
+        if not ok:
             return
         self._predict_to(t * self.frame_dt + 1.0 / IMU_RATE)      # the result arrives one IMU step later
         self.ekf.update(t * self.frame_dt, ests[-1], self.vel(ests[-2], ests[-1], self.frame_dt))
@@ -215,8 +243,14 @@ def euler_zyx(R) -> np.ndarray:
                      math.atan2(R[1, 0], R[0, 0])])
 
 
-def sequence_scans(veh: Vehicle, n: int):
-    return [veh.seq.scan(t) for t in range(n)]
+def sequence_scans(veh: Vehicle, n: int, skew: bool = True):
+    """The sequence's scans: sweeps taken while moving, as (n, 4) records (x, y, z, tau), or
+    (with skew False) every point at the frame pose. Scan 0 (the map's first frame) is taken
+    at rest."""
+    if not skew:
+        return [veh.seq.scan(t) for t in range(n)]
+    out = [np.concatenate([veh.seq.scan(0), np.zeros((veh.seq.scan(0).shape[0], 1), np.float32)], axis=1)]
+    return out + [synth.skewed_scan(veh.seq, t) for t in range(1, n)]
 
 
 def rot_angle(R):
@@ -316,7 +350,7 @@ def ncu_traffic(kernel="k_gn_lin"):
 
 # --------------------------------------------------------------------------------------- GPU arm
 def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from, clk=None, rng=None,
-                 on_step=None, e2e=False):
+                 on_step=None, e2e=False, skew=True):
     """Scans 1..n_seq-1 through far_process_scan, each from `prior` of the estimates so far.
     Every step is bracketed by CUDA events on the map's stream after an L2 flush (device
     time) or, with e2e, timed on the host around the call (pinned host input). The clock
@@ -339,8 +373,10 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
                 w0 = time.perf_counter()
             else:
                 ev0.record(stream)
+            mo = prior.motion(t) if skew else None
             pose, _, res = m.process_scan(dev[t], init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau,
-                                          kappa=kappa, asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R)
+                                          kappa=kappa, asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R,
+                                          motion=mo)
             thr.update(init, pose)
             if e2e:
                 ms = 1e3 * (time.perf_counter() - w0)
@@ -348,7 +384,7 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
                 ev1.record(stream)
                 ev1.synchronize()
                 ms = ev0.elapsed_time(ev1)
-            recs.append(dict(t=t, ms=ms, init=init, pose=pose, res=res, n=int(dev[t].shape[0])))
+            recs.append(dict(t=t, ms=ms, init=init, pose=pose, res=res, n=int(dev[t].shape[0]), motion=mo))
             ests.append(pose)
             prior.observe(t, ests, res["status"] == 0)
             if on_step is not None:
@@ -376,7 +412,7 @@ def run_ours(args):
     veh = Vehicle(rank, offset)
     n_seq = max(args.scans, 2 + args.warmup + args.steps)
     timed_from = n_seq - args.steps
-    scans = sequence_scans(veh, n_seq)
+    scans = sequence_scans(veh, n_seq, args.skew)
     dev = [torch.from_numpy(s).cuda() for s in scans]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -405,7 +441,7 @@ def run_ours(args):
     t_wall0 = time.perf_counter()
     clk = ClockSampler(local)
     recs = run_sequence(m, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, args.prior, stream, flush, n_seq,
-                        timed_from, clk=clk, on_step=count_launches)
+                        timed_from, clk=clk, on_step=count_launches, skew=args.skew)
     wall = time.perf_counter() - t_wall0
     m.close()
     tr = timed(recs)
@@ -467,7 +503,7 @@ def run_ours(args):
     mp = make_map()
     mp.set_profiling(True)
     run_sequence(mp, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, args.prior, stream, flush, n_seq,
-                 timed_from, on_step=profile_step)
+                 timed_from, on_step=profile_step, skew=args.skew)
     mp.close()
 
     peak, peak_kind = measured_peaks()
@@ -503,14 +539,14 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         recs2 = run_sequence(m2, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), pinned, args.prior, stream,
-                             flush, n_seq, timed_from, e2e=True)
+                             flush, n_seq, timed_from, e2e=True, skew=args.skew)
         m2.close()
         e2e_s = sum(r["ms"] for r in timed(recs2)) / 1e3
         if world > 1:
             tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_s = float(tt[0])
-        h2d = pts / args.steps * 12.0
+        h2d = pts / args.steps * (16.0 if args.skew else 12.0)
         # pose (128 B) + registration state (~700 B) + map counters (96 B) read back per step
         d2h = 128 + 704 + 96
         e2e = {"value": round(pts_all / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": round(h2d),
@@ -522,7 +558,7 @@ def run_ours(args):
     for other in [k_ for k_ in PRIOR_LABELS if k_ != args.prior]:
         m3 = make_map()
         recs3 = run_sequence(m3, veh, far.Threshold(SIGMA0, MIN_MOTION, R_MAX), dev, other, stream, flush, n_seq,
-                             timed_from, rng=np.random.default_rng(1000 + rank))
+                             timed_from, rng=np.random.default_rng(1000 + rank), skew=args.skew)
         m3.close()
         tr3 = timed(recs3)
         it3 = np.array([r["res"]["iters"] for r in recs3])
@@ -535,7 +571,7 @@ def run_ours(args):
 
     cpu = cpu1 = accuracy = None
     if rank == 0 and not args.no_cpu_baseline and args.precision == 0 and offset == [0.0, 0.0, 0.0]:
-        cpu, cpu1, accuracy = oracle_lockstep(veh, recs, args.cpu_sample_steps)
+        cpu, cpu1, accuracy = oracle_lockstep(veh, recs, args.cpu_sample_steps, dev, args.skew)
     n_acc = args.accuracy_scans if args.accuracy_scans is not None else (6 if args.precision else 0)
     prec_acc = precision_accuracy(n_acc, stream) if (rank == 0 and n_acc > 0) else None
 
@@ -546,7 +582,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s_all / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast LiDAR; the paper's datasets are not available)",
-        "config": dict(workload_config(args.steps, args.warmup, world, args.prior, n_seq),
+        "config": dict(workload_config(args.steps, args.warmup, world, args.prior, n_seq, args.skew),
                        precision_mode=args.precision, world_offset_m=offset),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                        "p99": round(float(np.percentile(lat, 99)), 4),
@@ -589,14 +625,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def oracle_lockstep(veh, recs, n_scans):
+def oracle_lockstep(veh, recs, n_scans, dev, skew):
     """The oracle on the first n_scans scans in lockstep with the GPU run: each scan registered
     from the GPU's initial pose against a map that was updated at the GPU's registered poses
-    (so it holds exactly the GPU's map), then inserted and evicted at the GPU's pose. Reports the
-    per-scan pose difference (the registration's own error) and times the oracle's register +
-    insert + evict per scan, once single-threaded and once on all host cores."""
+    (so it holds exactly the GPU's map), then inserted and evicted at the GPU's pose. With skewed
+    sweeps the oracle takes the points the GPU's de-skew produced (far_undistort with the same
+    motion lines), so both register the same FP32 points. Reports the per-scan pose difference
+    (the registration's own error) and times the oracle's register + insert + evict per scan,
+    once single-threaded and once on all host cores."""
     import oracle
+    from paper_2606_26010_gb300 import far
     recs = recs[:n_scans]
+    points = {}
+    for r in recs:
+        if skew:
+            points[r["t"]] = far.undistort(dev[r["t"]], r["motion"]).cpu().numpy()
+        else:
+            points[r["t"]] = veh.seq.scan(r["t"])
     out = {}
     for threads in (1, os.cpu_count() or 1):
         oracle.set_threads(threads)
@@ -605,7 +650,7 @@ def oracle_lockstep(veh, recs, n_scans):
         thr = oracle.Threshold(SIGMA0, MIN_MOTION, R_MAX)
         secs, errs, iters_ok = 0.0, [], 0
         for r in recs:
-            scan = veh.seq.scan(r["t"])
+            scan = points[r["t"]]
             t0 = time.perf_counter()
             tau, kappa = thr.get()
             Po, _, so = m.register(scan, r["init"], MAX_ITERS, CONV_EPS, tau, kappa)
@@ -712,10 +757,16 @@ def run_reference(args):
     ests = [veh.pose(0)]
     times, pts = [], []
     prior = Prior(veh, args.prior, "oracle")
+    from oracle import deskew as od
     for t in range(1, n_seq):
-        scan = veh.seq.scan(t)
+        rec = synth.skewed_scan(veh.seq, t) if args.skew else veh.seq.scan(t)
         init = prior.init(t, ests)
         t0 = time.perf_counter()
+        if args.skew:     # Sec. III-A.1 in the oracle: FP64 de-skew, rounded once to FP32
+            mo = prior.motion(t)
+            scan = od.undistort(rec[:, :3], rec[:, 3], mo["w0"], mo["w1"], mo["v0"], mo["v1"]).astype(np.float32)
+        else:
+            scan = rec
         tau, kappa = thr.get()
         est, _, st = m.register(scan, init, MAX_ITERS, CONV_EPS, tau, kappa)
         thr.update(init, est)
@@ -736,8 +787,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": round(float(lat.mean()), 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
            "data": "synthetic (seeded ray-cast LiDAR)",
-           "config": dict(workload_config(len(times), args.warmup, world, args.prior, n_seq), precision_mode=0,
-                          world_offset_m=[0.0, 0.0, 0.0]),
+           "config": dict(workload_config(len(times), args.warmup, world, args.prior, n_seq, args.skew),
+                          precision_mode=0, world_offset_m=[0.0, 0.0, 0.0]),
            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                           "p99": round(float(np.percentile(lat, 99)), 3)},
            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -952,6 +1003,26 @@ def run_serving(args):
     server = serving.Server(cfg, prior)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
         rep = server.run(vehicles, args.duration)
+    slowest = sorted(range(len(server.steps)), key=lambda i: -server.steps[i][1])[:3]
+    slow_steps = [{"step": i, "t_s": round(server.steps[i][0], 4), "ms": round(1e3 * server.steps[i][1], 3),
+                   "batch": server.steps[i][2]} for i in slowest]
+    under_load = None
+    c = args.load_compression
+    if c and c > 0:
+        # the same fleet with every vehicle c times faster in time (the same frames at the same poses,
+        # arriving c times more often): a run near the server's capacity
+        specs_c = [dataclasses.replace(sp, rate_hz=sp.rate_hz * c, speed=sp.speed * c, join_s=sp.join_s / c,
+                                       leave_s=sp.leave_s / c) for sp in specs]
+        veh_c = serving.make_vehicles(specs_c, scan_fn, pose_fn, args.duration / c, np.random.default_rng(13),
+                                      jitter_s=0.004 / c)
+        server_c = serving.Server(cfg, prior)
+        rep_c = server_c.run(veh_c, args.duration / c)
+        under_load = {"time_compression": c, "offered_scans_per_s": round(
+                          sum(len(v.arrivals) - 1 for v in veh_c) / (args.duration / c), 2),
+                      "served_scans_per_s": round(rep_c["scans_per_s_simulated"], 2),
+                      "latency_ms": rep_c["latency_ms"], "busy_fraction": round(rep_c["busy_fraction"], 4),
+                      "batch_size": {"mean": round(rep_c["mean_batch"], 2), "max": rep_c["max_batch"]},
+                      "capacity_scans_per_s": round(rep_c["scans_per_s_device"], 2), "scans": rep_c["scans"]}
     errs = []        # frame-to-frame relative pose error (drift per frame), registered frames
     for v in vehicles:
         for f, (P, st) in v.poses.items():
@@ -985,6 +1056,8 @@ def run_serving(args):
             "p99_trans_m": round(float(np.percentile([e[0] for e in errs], 99)), 5) if errs else None,
             "median_rot_rad": round(float(np.median([e[1] for e in errs])), 7) if errs else None},
         "latency_clock": "server clock advances by each step's measured wall time (arrival -> pose on host)",
+        "slowest_steps": slow_steps,
+        "under_load": under_load,
         "clocks": clk.summary(),
     }
     print(json.dumps(out))

@@ -114,3 +114,18 @@ def test_batch_process_matches_process_scan(far):
         a, b = m.export(), m2.export()
         for key in a:
             assert np.array_equal(a[key], b[key]), (i, key)
+
+
+def test_batch_replay_is_one_graph_launch(far):
+    """After the first call (which captures the batch), a call with the same inputs replays one
+    instantiated graph: the scan-local sources of every problem, the batched Gauss-Newton chain
+    and the state gather all run from it, and the library issues no kernel launch of its own."""
+    import torch
+    probs = make_problems(far, torch, [14, 15, 16], [(32, 1024), (16, 512), (64, 512)])
+    batch = far.Batch([m for _, m, _ in probs])
+    qs, inits = [q for _, _, q in probs], [p.init for p, _, _ in probs]
+    first, _ = batch.register(qs, inits, max_iters=10, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+    l0 = far.launch_count()
+    again, stats = batch.register(qs, inits, max_iters=10, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9)
+    assert far.launch_count() == l0
+    assert np.array_equal(first, again) and all(s["status"] == 0 for s in stats)
