@@ -84,7 +84,7 @@ def parse_args():
                     help="sequence: the 128x2048 high-speed sequence (default); batched: 64 uneven problems; "
                          "serving: 16 vehicles streaming scans")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: simulated seconds")
-    ap.add_argument("--load-compression", type=float, default=8.0,
+    ap.add_argument("--load-compression", type=float, default=16.0,
                     help="serving: the fleet's arrivals (and motion) replayed this many times faster as a second "
                          "run near the server's capacity (0 = skip)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
@@ -378,6 +378,8 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
             else:
                 ev0.record(stream)
             mo = prior.motion(t) if skew else None
+            if e2e and t + 1 < n_seq:
+                m.prefetch(dev[t + 1])     # the next scan's copy overlaps this scan's kernels
             pose, _, res = m.process_scan(dev[t], init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau,
                                           kappa=kappa, asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R,
                                           motion=mo)
@@ -555,7 +557,8 @@ def run_ours(args):
         d2h = 128 + 704 + 96
         e2e = {"value": round(pts_all / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": round(h2d),
                "d2h_bytes_per_step": d2h, "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
-               "api": "far_process_scan with pinned host points"}
+               "api": "far_process_scan_motion with pinned host points, the next scan's copy started by "
+                      "far_prefetch_points before each call"}
 
     # ---- the other priors, as labelled secondary lines
     secondary = []
@@ -1087,7 +1090,8 @@ def run_latency(args):
     times, acc, gyro = imu_stream(veh)
     frame_dt = 1.0 / synth.FRAME_RATE_HZ
     rows = []
-    for delay_ms in (10, 20, 50, 80):
+    delays = (0, 10, 20, 50, 80)
+    for delay_ms in delays:
         for comp in (True, False):
             with torch.cuda.stream(stream):
                 m = far.VoxelMap(V, NMAX, K_COV, -1.0, max_voxels=args.max_voxels, load_factor=0.5,
@@ -1121,6 +1125,9 @@ def run_latency(args):
                         ests.append(P)
                         vl = far.lidar_velocity(ests[-2], ests[-1], frame_dt)
                         pending.append((t * frame_dt + delay_ms / 1e3, t * frame_dt, P, vl))
+                        if delay_ms == 0:      # no delay: fused at the scan's own time
+                            _, t_meas, P0, vl0 = pending.pop(0)
+                            prior.ekf.update(t_meas, P0, vl0)
                     else:
                         ests.append(init)
                 advance(n_seq * frame_dt)
@@ -1137,7 +1144,9 @@ def run_latency(args):
            "data": "synthetic (seeded ray-cast LiDAR, 100 Hz IMU with white noise)",
            "config": {"workload": f"the {n_seq}-scan high-speed sequence, EKF prior and de-skew as in the default "
                                   "bench; each registration reaches the EKF d ms after its scan's time stamp",
-                      "delays_ms": [10, 20, 50, 80], "voxel_m": V, "n_max": NMAX, "k_cov": K_COV},
+                      "delays_ms": list(delays), "voxel_m": V, "n_max": NMAX, "k_cov": K_COV,
+                      "error": "|EKF position - true position| at every 100 Hz output; with the compensation it "
+                               "is the odometry's own drift from the truth"},
            "rows": rows}
     print(json.dumps(out))
 

@@ -222,6 +222,18 @@ typedef struct far_step_result {
 } far_step_result;
 
 /*
+ * Start copying a host scan to the device ahead of the call that will use it: the copy runs on
+ * the map's own copy stream into one of two staging buffers (set up on the first call), so it
+ * overlaps the map's kernels of the scan in progress (for pinned host memory). Up to two
+ * prefetched scans are kept; a third replaces the older one. A later call on this map that
+ * ingests points (far_process_scan, far_register_scan, far_map_insert, ...) with exactly a kept
+ * xyz, n and stride_bytes uses that copy instead of making its own; any other call copies as
+ * usual. The caller must not change the host array in between. Device pointers and n = 0 are
+ * accepted and do nothing. Records wider than 32 bytes are staged as their first 32 bytes.
+ */
+far_status far_prefetch_points(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes);
+
+/*
  * One scan of the LiDAR pipeline on the device (Sec. III-A.2 then III-A.3):
  * far_register_scan from `init_pose`, then - when the registration succeeded -
  * the insert of the same scan at the registered pose with the cap of `ins`

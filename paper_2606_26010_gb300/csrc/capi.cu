@@ -104,6 +104,17 @@ struct far_map {
     bool ins_used[2] = {false, false};
     far_insert_times ins_last[2] = {};
     bool local_dirty = false;        // the scan-local map may hold a scan (see build_sources)
+    // prefetch of the next host scan (far_prefetch_points): two staging buffers filled on a copy
+    // stream; a buffer is reused only after the map's stream has packed what it held
+    cudaStream_t copy_stream = nullptr;
+    void* pre_buf[2] = {nullptr, nullptr};
+    cudaEvent_t pre_ready[2] = {nullptr, nullptr};
+    cudaEvent_t pre_used[2] = {nullptr, nullptr};
+    bool pre_used_recorded[2] = {false, false};
+    const void* pre_ptr[2] = {nullptr, nullptr};   // the host array each buffer holds (null: none pending)
+    uint64_t pre_n[2] = {0, 0};
+    uint32_t pre_stride[2] = {0, 0}, pre_width[2] = {0, 0};
+    int pre_last = 1;                              // the buffer filled last
 };
 
 namespace {
@@ -217,6 +228,18 @@ Plan make_plan(const far_map_params& p, far_map* m) {
 void release(far_map* m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
+    if (m->copy_stream) {
+        cudaStreamSynchronize(m->copy_stream);
+        cudaStreamDestroy(m->copy_stream);
+        m->copy_stream = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (m->pre_buf[b]) cudaFree(m->pre_buf[b]);
+        if (m->pre_ready[b]) cudaEventDestroy(m->pre_ready[b]);
+        if (m->pre_used[b]) cudaEventDestroy(m->pre_used[b]);
+        m->pre_buf[b] = nullptr;
+        m->pre_ready[b] = m->pre_used[b] = nullptr;
+    }
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     m->ev.clear();
     for (int w = 0; w < 2; ++w) {
@@ -296,7 +319,19 @@ far_status ingest(far_map* m, const float* xyz, u32 n, u32 stride, const far_mot
     }
     const void* src = xyz;
     u32 eff = stride;
-    if (!is_device_pointer(xyz)) {
+    const u32 need_width = motion ? mo.time_offset + 4 : 12;
+    int used_slot = -1;
+    for (int b = 0; b < 2; ++b)
+        if (m->pre_ptr[b] == (const void*)xyz && m->pre_n[b] == n && m->pre_stride[b] == stride &&
+            m->pre_width[b] >= need_width)
+            used_slot = b;
+    if (used_slot >= 0) {
+        // prefetched on the copy stream (far_prefetch_points): wait for that copy, not for a new one
+        CK(cudaStreamWaitEvent(m->stream, m->pre_ready[used_slot], 0));
+        src = m->pre_buf[used_slot];
+        eff = stride <= 32 ? stride : 32;
+        m->pre_ptr[used_slot] = nullptr;
+    } else if (!is_device_pointer(xyz)) {
         if (stride <= 32) {
             CK(cudaMemcpyAsync(m->s.staging, xyz, (size_t)n * stride, cudaMemcpyHostToDevice, m->stream));
         } else {
@@ -311,6 +346,10 @@ far_status ingest(far_map* m, const float* xyz, u32 n, u32 stride, const far_mot
     }
     if (motion) CK(pack_points_deskew(src, n, eff, mo, m->s.in4, m->stream));
     else CK(pack_points(src, n, eff, m->s.in4, m->stream));
+    if (used_slot >= 0) {
+        CK(cudaEventRecord(m->pre_used[used_slot], m->stream));
+        m->pre_used_recorded[used_slot] = true;
+    }
     return FAR_OK;
 }
 
@@ -945,6 +984,44 @@ far_status far_register_scan(far_map* map, const float* xyz, uint64_t n, uint32_
         stats->chi2 = r.chi2;
     }
     return result;
+}
+
+far_status far_prefetch_points(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes) {
+    far_status st = check_points(map, xyz, n, stride_bytes);
+    if (st != FAR_OK) return st;
+    if (n == 0 || is_device_pointer(xyz)) return FAR_OK;   // nothing to copy ahead
+    if (!map->copy_stream) {
+        // set up once: a copy stream, two staging buffers of the map's largest scan, four events
+        const size_t bytes = (size_t)map->p.max_scan_points * 32;
+        CK(cudaStreamCreateWithFlags(&map->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = cudaMalloc(&map->pre_buf[b], bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FAR_ERR_OOM, "far_prefetch_points: staging allocation failed: %s", cudaGetErrorString(e));
+            }
+            CK(cudaEventCreateWithFlags(&map->pre_ready[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&map->pre_used[b], cudaEventDisableTiming));
+        }
+    }
+    // a free buffer, else the one filled earlier (its pending copy is dropped)
+    const int slot = !map->pre_ptr[0] ? 0 : (!map->pre_ptr[1] ? 1 : 1 - map->pre_last);
+    // the buffer's previous contents must have been packed by the map's stream
+    if (map->pre_used_recorded[slot]) CK(cudaStreamWaitEvent(map->copy_stream, map->pre_used[slot], 0));
+    const uint32_t width = stride_bytes <= 32 ? stride_bytes : 32;
+    if (stride_bytes <= 32)
+        CK(cudaMemcpyAsync(map->pre_buf[slot], xyz, (size_t)n * stride_bytes, cudaMemcpyHostToDevice,
+                           map->copy_stream));
+    else
+        CK(cudaMemcpy2DAsync(map->pre_buf[slot], 32, xyz, stride_bytes, 32, n, cudaMemcpyHostToDevice,
+                             map->copy_stream));
+    CK(cudaEventRecord(map->pre_ready[slot], map->copy_stream));
+    map->pre_ptr[slot] = xyz;
+    map->pre_n[slot] = n;
+    map->pre_stride[slot] = stride_bytes;
+    map->pre_width[slot] = width;
+    map->pre_last = slot;
+    return FAR_OK;
 }
 
 far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,

@@ -265,9 +265,9 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
 }
 
 // Sort of one group's input indices by one warp (values are distinct): up to 512 in
-// registers (bitonic network over 32 lanes x R values), up to 1024 as two such halves merged
-// along the merge path, larger groups as chunks of GS_SMEM sorted in the warp's shared memory
-// and merged through `tmp` (at most 32 chunks). Returns false when the group is too large.
+// registers (bitonic network over 32 lanes x R values), up to 1024 in the warp's shared buffer
+// (bitonic over compare pairs), larger groups as chunks of GS_SMEM sorted in shared memory and
+// merged through `tmp` (at most 32 chunks). Returns false when the group is too large.
 constexpr int GS_SMEM = 1024;
 constexpr int GS_WARPS = TPB / 32;
 
@@ -320,18 +320,32 @@ __device__ __forceinline__ void sort_group_regs(u32* a, u32 size, int lane) {
     }
 }
 
-__device__ __forceinline__ void bitonic_smem(u32* buf, int len, int lane) {   // len a power of two <= GS_SMEM
-    for (int k = 2; k <= len; k <<= 1) {
+// Bitonic sort of 1024 values in shared memory by one warp: every stage's 512 compare pairs
+// (i, i + j) are split over the lanes, 16 each, and loaded 8 at a time so that the loads of a
+// batch are in flight together.
+__device__ __forceinline__ void bitonic_smem_pairs(u32* buf, int lane) {
+#pragma unroll 1
+    for (int k = 2; k <= 1024; k <<= 1) {
+#pragma unroll 1
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < len; i += 32) {
-                const int p = i ^ j;
-                if (p > i) {
-                    const u32 a = buf[i], b = buf[p];
-                    const bool up = ((i & k) == 0);
-                    if ((a > b) == up) {
-                        buf[i] = b;
-                        buf[p] = a;
-                    }
+#pragma unroll
+            for (int bt = 0; bt < 2; ++bt) {
+                u32 va[8], vb[8];
+                int ia[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int q = lane + 32 * (8 * bt + t);          // pair 0..511
+                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    ia[t] = i;
+                    va[t] = buf[i];
+                    vb[t] = buf[i + j];
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const bool up = (ia[t] & k) == 0;
+                    const u32 lo = min(va[t], vb[t]), hi = max(va[t], vb[t]);
+                    buf[ia[t]] = up ? lo : hi;
+                    buf[ia[t] + j] = up ? hi : lo;
                 }
             }
             __syncwarp();
@@ -354,35 +368,12 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
         return true;
     }
     if (size <= 1024) {
-        // two halves sorted in registers, then merged from shared memory: lane l produces the
-        // outputs [32 l, 32 l + 32) of the merge, starting where the merge path crosses that
-        // diagonal (binary search; the values are distinct)
-        sort_group_regs<16>(a, 512, lane);
-        sort_group_regs<16>(a + 512, size - 512, lane);
-        for (u32 i = lane; i < size; i += 32) buf[i] = a[i];
+        // in the warp's shared buffer, padded to 1024: a bitonic network over compare pairs,
+        // each lane taking 16 of a stage's 512 pairs, their loads issued in batches of 8
+        for (u32 i = lane; i < 1024; i += 32) buf[i] = i < size ? a[i] : 0xFFFFFFFFu;
         __syncwarp();
-        const u32 na = 512, nb = size - 512;
-        const u32* A = buf;
-        const u32* B = buf + 512;
-        const u32 d = (u32)lane * 32u;
-        if (d < size) {
-            u32 lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
-            while (lo < hi) {
-                const u32 mid = (lo + hi) >> 1;
-                if (A[mid] < B[d - mid - 1]) lo = mid + 1;
-                else hi = mid;
-            }
-            u32 i = lo, j = d - lo;
-            const u32 end = min(d + 32u, size);
-            for (u32 o = d; o < end; ++o) {
-                const bool take_a = j >= nb || (i < na && A[i] < B[j]);
-                tmp[o] = take_a ? A[i] : B[j];
-                if (take_a) ++i;
-                else ++j;
-            }
-        }
-        __syncwarp();
-        for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
+        bitonic_smem_pairs(buf, lane);
+        for (u32 i = lane; i < size; i += 32) a[i] = buf[i];
         __syncwarp();
         return true;
     }
@@ -390,11 +381,9 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
     if (chunks > 32) return false;
     for (u32 c = 0; c < chunks; ++c) {
         const u32 c0 = c * GS_SMEM, len = min((u32)GS_SMEM, size - c0);
-        int p2 = 32;
-        while ((u32)p2 < len) p2 <<= 1;
-        for (int i = lane; i < p2; i += 32) buf[i] = (u32)i < len ? a[c0 + i] : 0xFFFFFFFFu;
+        for (u32 i = lane; i < (u32)GS_SMEM; i += 32) buf[i] = i < len ? a[c0 + i] : 0xFFFFFFFFu;
         __syncwarp();
-        bitonic_smem(buf, p2, lane);
+        bitonic_smem_pairs(buf, lane);
         for (u32 i = lane; i < len; i += 32) a[c0 + i] = buf[i];
         __syncwarp();
     }

@@ -158,6 +158,7 @@ _SIGS = {
     "far_undistort": (ctypes.c_int, [_vp, _u64, _u32, _vp, _vp, _vp]),
     "far_process_scan_motion": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, ctypes.c_double, _vp,
                                                _vp, _vp]),
+    "far_prefetch_points": (ctypes.c_int, [_vp, _vp, _u64, _u32]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -383,6 +384,13 @@ class VoxelMap:
                                                    _p(pose), _p(cov), ctypes.byref(res)),
                    allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
         return pose.reshape(4, 4), (cov.reshape(6, 6) if want_cov else None), res.as_dict()
+
+    def prefetch(self, xyz):
+        """far_prefetch_points: start copying the next host scan while the current one runs. The
+        array must stay alive and unchanged until the call that ingests it."""
+        ptr, n, stride, keep = _points(xyz)
+        self._prefetched = keep
+        _check(self._L.far_prefetch_points(self._h, ptr, n, stride))
 
     # ---- instrumentation
     def set_profiling(self, enable=True):

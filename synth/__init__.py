@@ -435,7 +435,7 @@ def sensor_for_points(rng: np.random.Generator, n_target: float) -> Lidar:
 
 
 def batched_problems(seed: int = 7, count: int = 64, scan_range=(5e3, 3e5), map_range=(1e5, 3e6),
-                     max_prior: int = 80, sequence: "TrackSequence | None" = None):
+                     max_prior: int = 250, sequence: "TrackSequence | None" = None):
     """Problems with log-uniform scan sizes (mixed 16/32/64/128-beam sensors) and log-uniform
     map targets, placed at random positions of the oval; priors are the preceding frames."""
     seq = sequence or TrackSequence(seed=42)

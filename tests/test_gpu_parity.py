@@ -382,6 +382,36 @@ def test_strides_and_device_inputs_agree(far, problem1, maps1):
     assert np.array_equal(g.register(problem1.query, problem1.init)[0], base)  # deterministic
 
 
+def test_prefetched_host_scans_give_the_same_results(far, problem1):
+    """far_prefetch_points: a scan copied ahead on the copy stream is used by the next call with the
+    same array (bitwise the same pose and map as a plain copy); two scans can be pending; a call
+    with another array copies as usual."""
+    import torch
+    scans = [torch.from_numpy(np.ascontiguousarray(s)).pin_memory() for s in problem1.map_scans[:4]]
+    kw = dict(max_iters=5, conv_eps=0.0, tau=2.0, kappa=2.0 / 9, asmd=True, evict_radius=0.0)
+    out = []
+    for use_prefetch in (False, True):
+        g = far.VoxelMap(0.5, 20, 5, max_voxels=1 << 17, max_scan_points=40_000)
+        g.insert(scans[0], problem1.map_poses[0])
+        poses = []
+        for i in range(1, 4):
+            if use_prefetch and i == 1:
+                g.prefetch(scans[1])
+                g.prefetch(scans[2])           # two pending
+            elif use_prefetch and i + 1 < 4:
+                g.prefetch(scans[i + 1])
+            if use_prefetch and i == 3:
+                g.prefetch(scans[0])           # a prefetch that no call uses
+            T, _, _ = g.process_scan(scans[i], problem1.map_poses[i], **kw)
+            poses.append(T)
+        out.append((poses, g.export()))
+        g.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    for key in out[0][1]:
+        assert np.array_equal(out[0][1][key], out[1][1][key]), key
+
+
 def test_graph_loop_equals_explicit_launches(far, problem1, maps1):
     """With conv_eps > 0 the loop runs as a graph with a device-side while loop; with profiling it
     runs as explicit launches. Both apply the same kernels in the same order: identical results."""
