@@ -550,6 +550,12 @@ struct AdmitArgs {
 // closer than d_min (FP32 d^2 >= d_min^2). The voxel's points sit in the warp's shared buffer;
 // each lane holds one candidate of a window of 32 (in input order) and tests it against them
 // (broadcast reads), then the passing candidates are admitted in input order.
+// Candidate windows of 32 a warp tests at once in the admission (see k_admit).
+#ifndef FAR_ADMIT_U
+#define FAR_ADMIT_U 2
+#endif
+constexpr int ADMIT_U = FAR_ADMIT_U;
+
 __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     pdl_wait();
     pdl_trigger();
@@ -650,38 +656,56 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
             if (lane < (int)c_n) vp[lane] = bp[lane];
             if (lane + 32 < (int)c_n) vp[lane + 32] = bp[lane + 32];
             __syncwarp();
-            for (u32 w0 = w_start; w0 < w_end && c_n < w_cap; w0 += 32) {
-                // lane l holds candidate w0 + l and tests it against the points held at window start
-                const u32 i = w0 + lane;
-                const bool in_window = i < w_end;
-                const u32 my_idx = in_window ? a.sv[i] : 0u;
-                const float4 my_c = in_window ? a.world[my_idx] : far4;
-                bool pass = in_window;
+            for (u32 w0 = w_start; w0 < w_end && c_n < w_cap; w0 += 32u * ADMIT_U) {
+                // ADMIT_U windows of 32 candidates at once, candidate w0 + 32 u + l on lane l: their
+                // loads are in flight together, and each broadcast read of a voxel point is tested
+                // against all of them
+                u32 my_idx[ADMIT_U];
+                float4 my_c[ADMIT_U];
+                bool pass[ADMIT_U];
+#pragma unroll
+                for (int u = 0; u < ADMIT_U; ++u) {
+                    const u32 i = w0 + 32u * u + lane;
+                    pass[u] = i < w_end;
+                    my_idx[u] = pass[u] ? a.sv[i] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < ADMIT_U; ++u) my_c[u] = pass[u] ? a.world[my_idx[u]] : far4;
                 for (u32 j = 0; j < c_n; ++j) {
                     const float4 e = vp[j];   // the same address for every lane: one broadcast read
-                    pass = pass && (dist2_rn(my_c.x, my_c.y, my_c.z, e.x, e.y, e.z) >= a.dmin2);
+#pragma unroll
+                    for (int u = 0; u < ADMIT_U; ++u)
+                        pass[u] = pass[u] && (dist2_rn(my_c[u].x, my_c[u].y, my_c[u].z, e.x, e.y, e.z) >= a.dmin2);
                 }
-                // resolve in input order: the first passing lane is admitted, later lanes are
-                // re-tested against it only (earlier lanes already failed against a subset)
-                while (c_n < w_cap) {
-                    const u32 ballot = __ballot_sync(0xffffffffu, pass);
-                    if (ballot == 0u) break;
-                    const int fl = __ffs(ballot) - 1;
-                    const float cx = __shfl_sync(0xffffffffu, my_c.x, fl);
-                    const float cy = __shfl_sync(0xffffffffu, my_c.y, fl);
-                    const float cz = __shfl_sync(0xffffffffu, my_c.z, fl);
-                    const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
-                    if (lane == fl) {
-                        bp[c_n] = c;
-                        vp[c_n] = c;
-                        a.pos[my_idx] = w_bucket * a.nmax + c_n;
-                        a.admitted[my_idx] = 1u;
-                        a.a_ord[my_idx] = w_ord;
-                        a.a_j[my_idx] = c_n - cnt0;
+                // resolve in input order (window u before u + 1, lanes in order): the first passing
+                // candidate is admitted, the later ones are re-tested against it only (the earlier
+                // ones already failed against a subset)
+#pragma unroll
+                for (int u = 0; u < ADMIT_U; ++u) {
+                    while (c_n < w_cap) {
+                        const u32 ballot = __ballot_sync(0xffffffffu, pass[u]);
+                        if (ballot == 0u) break;
+                        const int fl = __ffs(ballot) - 1;
+                        const float cx = __shfl_sync(0xffffffffu, my_c[u].x, fl);
+                        const float cy = __shfl_sync(0xffffffffu, my_c[u].y, fl);
+                        const float cz = __shfl_sync(0xffffffffu, my_c[u].z, fl);
+                        const float4 c = make_float4(cx, cy, cz, __uint_as_float(NO_ID));
+                        if (lane == fl) {
+                            bp[c_n] = c;
+                            vp[c_n] = c;
+                            a.pos[my_idx[u]] = w_bucket * a.nmax + c_n;
+                            a.admitted[my_idx[u]] = 1u;
+                            a.a_ord[my_idx[u]] = w_ord;
+                            a.a_j[my_idx[u]] = c_n - cnt0;
+                        }
+                        ++c_n;
+                        if (lane <= fl) pass[u] = false;
+                        else if (pass[u]) pass[u] = dist2_rn(my_c[u].x, my_c[u].y, my_c[u].z, cx, cy, cz) >= a.dmin2;
+#pragma unroll
+                        for (int v2 = u + 1; v2 < ADMIT_U; ++v2)
+                            if (pass[v2])
+                                pass[v2] = dist2_rn(my_c[v2].x, my_c[v2].y, my_c[v2].z, cx, cy, cz) >= a.dmin2;
                     }
-                    ++c_n;
-                    if (lane <= fl) pass = false;
-                    else if (pass) pass = dist2_rn(my_c.x, my_c.y, my_c.z, cx, cy, cz) >= a.dmin2;
                 }
                 __syncwarp();   // this window's admitted points are visible to the next window
             }
