@@ -515,7 +515,7 @@ far_status build_sources(far_map* m, u32 n, u32* knn_ids) {
     if (m->local_dirty) CK(map_clear(m->local, m->stream));
     m->local_dirty = true;
     InsertCfg cfg;
-    CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream, DevicePose(), insert_marks(m, 0)));
+    CK(map_insert_batch(m->local, m->s, n, nullptr, cfg, false, m->stream, DevicePose(), insert_marks(m, 0), true));
     CK(make_sources(m->local, m->s, n, knn_ids, m->stream));
     if (m->profiling) cudaEventRecord(m->src_end, m->stream);
     CK(map_local_reset(m->local, m->s, n, m->stream));

@@ -75,7 +75,6 @@ enum ErrFlag : u32 {
     ERR_BUCKETS_FULL = 2u,
     ERR_ID_OVERFLOW = 4u,
     ERR_TIMEOUT = 8u,
-    ERR_GROUP_SIZE = 16u,   // a voxel received more than 32768 points in one insert (not grouped)
 };
 
 struct __align__(16) Slot {

@@ -87,84 +87,16 @@ __global__ void k_pack_deskew(const char* __restrict__ src, u32 n, u32 stride, S
     }
 }
 
-// a11: x_w = fp32(((R0 x + R1 y) + R2 z) + t) in FP64 without contraction; then the key.
-// Precision variant (tv > 0): x_w stays FP64, the key follows the tile reading and `world`
-// receives the coordinates relative to the tile origin.
-__global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
-                             float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys,
-                             u32* __restrict__ scal, MapCounters* ctr, u32* __restrict__ admitted,
-                             u32* __restrict__ flags) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-    // the insert's first kernel clears its per-insert state (scalars, ASMD sums, admitted flags)
-    // and records the first id it will assign
-    if (i < SCAL_COUNT) scal[i] = (i == SCAL_IDBASE) ? ctr->next_id : 0u;
-    if (i == 0) {
-        ctr->near_sum = 0ull;
-        ctr->near_cnt = 0ull;
-        ctr->n_added = 0u;
-    }
-    if (i >= n) return;
-    admitted[i] = 0u;
-    flags[i] = 0u;
-    if (dp.T) {
-#pragma unroll
-        for (int j = 0; j < 12; ++j) T.m[j] = dp.T[j];
-    }
-    const float4 p = in[i];
-    float w[3] = {p.x, p.y, p.z};
-    const bool finite = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && !(dp.status && *dp.status != 0);
-    if (tv > 0) {
-        u64 key = KEY_INVALID;
-        int k[3];
-        bool ok = finite;
-        for (int r = 0; r < 3 && ok; ++r) {
-            double x = (&p.x)[r];
-            if (has_pose) {
-                const double px = p.x, py = p.y, pz = p.z;
-                double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], px), __dmul_rn(T.m[4 * r + 1], py));
-                s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], pz));
-                x = __dadd_rn(s, T.m[4 * r + 3]);
-            }
-            ok = tile_key_axis(x, inv_v, tv, k[r], w[r]);
-        }
-        if (ok) key = pack_key(k[0], k[1], k[2]);
-        world[i] = make_float4(w[0], w[1], w[2], p.w);
-        keys[i] = key;
-        return;
-    }
-    if (has_pose && finite) {
-        const double x = p.x, y = p.y, z = p.z;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], x), __dmul_rn(T.m[4 * r + 1], y));
-            s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], z));
-            s = __dadd_rn(s, T.m[4 * r + 3]);
-            w[r] = __double2float_rn(s);
-        }
-    }
-    world[i] = make_float4(w[0], w[1], w[2], p.w);
-    u64 key = KEY_INVALID;
-    int kx, ky, kz;
-    if (finite && voxel_key3(w[0], w[1], w[2], inv_v, kx, ky, kz)) key = pack_key(kx, ky, kz);
-    keys[i] = key;
-}
-
-// Slot of each point's voxel (inserting new keys), and the point's arrival rank among the
-// points of this batch in that slot (out_rank, from the per-slot counter slot_cnt). The lanes
-// of a warp that found the same slot take their ranks with one atomic (points of a voxel
-// arrive together in scan order).
-__global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slots, u32 mask,
-                                 u32* __restrict__ out_slot, u32* __restrict__ out_rank, MapCounters* ctr,
-                                 u32* __restrict__ slot_cnt) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+// Slot of a point's voxel (inserting new keys), and the point's arrival rank among the points of
+// this batch in that slot (out_rank, from the per-slot counter slot_cnt). The lanes of a warp that
+// found the same slot take their ranks with one atomic (points of a voxel arrive together in scan
+// order). Every lane of the warp calls this (key KEY_INVALID and i >= n for lanes without a point).
+__device__ __forceinline__ void find_or_insert_slot(u64 key, u32 i, u32 n, Slot* slots, u32 mask,
+                                                    u32* __restrict__ out_slot, u32* __restrict__ out_rank,
+                                                    MapCounters* ctr, u32* __restrict__ slot_cnt) {
     const int lane = threadIdx.x & 31;
     const u32 sentinel = mask + 1u;
     u32 found = sentinel, probes = 0;
-    const u64 key = i < n ? keys[i] : KEY_INVALID;
     if (key != KEY_INVALID) {
         int kx, ky, kz;
         unpack_key(key, kx, ky, kz);
@@ -201,6 +133,71 @@ __global__ void k_find_or_insert(const u64* __restrict__ keys, u32 n, Slot* slot
     if (i >= n) return;
     out_slot[i] = found;
     if (found != sentinel) out_rank[i] = base + (u32)__popc(peers & ((1u << lane) - 1u));
+}
+
+// a11: x_w = fp32(((R0 x + R1 y) + R2 z) + t) in FP64 without contraction; then the key, and the
+// slot of the key in the map with the point's rank in it (find_or_insert_slot).
+// Precision variant (tv > 0): x_w stays FP64, the key follows the tile reading and `world`
+// receives the coordinates relative to the tile origin.
+__global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int has_pose, DevicePose dp,
+                             float inv_v, int tv, float4* __restrict__ world, u64* __restrict__ keys,
+                             u32* __restrict__ scal, MapCounters* ctr, u32* __restrict__ admitted,
+                             u32* __restrict__ flags, Slot* slots, u32 mask, u32* __restrict__ out_slot,
+                             u32* __restrict__ out_rank, u32* __restrict__ slot_cnt) {
+    pdl_wait();
+    pdl_trigger();
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the insert's first kernel clears its per-insert state (scalars, ASMD sums, admitted flags)
+    // and records the first id it will assign
+    if (i < SCAL_COUNT) scal[i] = (i == SCAL_IDBASE) ? ctr->next_id : 0u;
+    if (i == 0) {
+        ctr->near_sum = 0ull;
+        ctr->near_cnt = 0ull;
+        ctr->n_added = 0u;
+    }
+    u64 key = KEY_INVALID;
+    if (i < n) {
+        admitted[i] = 0u;
+        flags[i] = 0u;
+        if (dp.T) {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) T.m[j] = dp.T[j];
+        }
+        const float4 p = in[i];
+        float w[3] = {p.x, p.y, p.z};
+        const bool finite = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && !(dp.status && *dp.status != 0);
+        if (tv > 0) {
+            int k[3];
+            bool ok = finite;
+            for (int r = 0; r < 3 && ok; ++r) {
+                double x = (&p.x)[r];
+                if (has_pose) {
+                    const double px = p.x, py = p.y, pz = p.z;
+                    double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], px), __dmul_rn(T.m[4 * r + 1], py));
+                    s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], pz));
+                    x = __dadd_rn(s, T.m[4 * r + 3]);
+                }
+                ok = tile_key_axis(x, inv_v, tv, k[r], w[r]);
+            }
+            if (ok) key = pack_key(k[0], k[1], k[2]);
+        } else {
+            if (has_pose && finite) {
+                const double x = p.x, y = p.y, z = p.z;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    double s = __dadd_rn(__dmul_rn(T.m[4 * r + 0], x), __dmul_rn(T.m[4 * r + 1], y));
+                    s = __dadd_rn(s, __dmul_rn(T.m[4 * r + 2], z));
+                    s = __dadd_rn(s, T.m[4 * r + 3]);
+                    w[r] = __double2float_rn(s);
+                }
+            }
+            int kx, ky, kz;
+            if (finite && voxel_key3(w[0], w[1], w[2], inv_v, kx, ky, kz)) key = pack_key(kx, ky, kz);
+        }
+        world[i] = make_float4(w[0], w[1], w[2], p.w);
+        keys[i] = key;
+    }
+    find_or_insert_slot(key, i, n, slots, mask, out_slot, out_rank, ctr, slot_cnt);
 }
 
 // Groups: the first point of each slot (rank 0) opens the slot's group, a contiguous range
@@ -264,10 +261,11 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Sort of one group's input indices by one warp (values are distinct): up to 512 in
-// registers (bitonic network over 32 lanes x R values), up to 1024 in the warp's shared buffer
-// (bitonic over compare pairs), larger groups as chunks of GS_SMEM sorted in shared memory and
-// merged through `tmp` (at most 32 chunks). Returns false when the group is too large.
+// Sort of one group's input indices by one warp (values are distinct). Groups of up to 128 are
+// sorted in registers (bitonic network over 32 lanes x R values). Larger ones take the cheaper
+// of a bitmap of their index range (sort_group_bitmap; its cost grows with the range) and a
+// comparison sort: up to 1024 in the warp's shared buffer (bitonic over compare pairs), else
+// chunks of GS_SMEM sorted in shared memory and merged through `tmp` (at most 32 chunks).
 constexpr int GS_SMEM = 1024;
 constexpr int GS_WARPS = TPB / 32;
 
@@ -353,19 +351,84 @@ __device__ __forceinline__ void bitonic_smem_pairs(u32* buf, int lane) {
     }
 }
 
-__device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf, int lane) {
-    if (size <= 1) return true;
+// Sort of distinct values through a bitmap of their range [lo, hi]: each pass marks the members
+// that fall in a window of 32768 values in the warp's shared buffer (1024 words), then reads
+// the marks back in order, one row of 32 consecutive words (one per lane) at a time; a warp
+// scan of the row's popcounts gives each lane its output position. With one pass the output
+// goes to `a` in place (every member is marked before any is written), else through `tmp`.
+__device__ __forceinline__ void sort_group_bitmap(u32* a, u32 size, u32 lo, u32 hi, u32* tmp, u32* buf,
+                                                  int lane) {
+    const u32 passes = ((hi - lo) >> 15) + 1u;
+    u32* out = passes == 1u ? a : tmp;
+    u32 pos = 0;   // outputs of the rows done so far (the same on every lane)
+    for (u32 p = 0; p < passes; ++p) {
+        const u32 w0 = lo + (p << 15);
+        const u32 span = min(hi - w0, 32767u);   // the window's last offset that can hold a member
+        const u32 rows = (span >> 10) + 1u;
+        for (u32 r = 0; r < rows; ++r) buf[r * 32u + lane] = 0u;
+        __syncwarp();
+        for (u32 i = lane; i < size; i += 32) {
+            const u32 d = a[i] - w0;
+            if (d <= span) atomicOr(&buf[d >> 5], 1u << (d & 31u));
+        }
+        __syncwarp();
+        for (u32 r = 0; r < rows; ++r) {
+            u32 word = buf[r * 32u + lane];
+            if (__ballot_sync(0xffffffffu, word != 0u) == 0u) continue;
+            const u32 c = __popc(word);
+            u32 incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            u32 q = pos + incl - c;
+            const u32 base = w0 + ((r * 32u + (u32)lane) << 5);
+            while (word) {
+                out[q++] = base + (u32)(__ffs(word) - 1);
+                word &= word - 1u;
+            }
+            pos += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        __syncwarp();
+    }
+    if (passes > 1u) {
+        for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void sort_group(u32* a, u32 size, u32* tmp, u32* buf, int lane) {
+    if (size <= 1) return;
     if (size <= 32) {
         sort_group_regs<1>(a, size, lane);
-        return true;
+        return;
     }
     if (size <= 128) {
         sort_group_regs<4>(a, size, lane);
-        return true;
+        return;
     }
-    if (size <= 512) {
-        sort_group_regs<16>(a, size, lane);
-        return true;
+    u32 lo = 0xFFFFFFFFu, hi = 0u;
+    for (u32 i = lane; i < size; i += 32) {
+        const u32 x = a[i];
+        lo = min(lo, x);
+        hi = max(hi, x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    // estimated instructions per lane of each way: the bitmap ~512 per 32768 values of range
+    // plus ~8 per 32 members and pass; the shared-memory network ~3300 per 1024 values and the
+    // serial merge of its chunks ~15 per member
+    const unsigned long long chunks = (size + GS_SMEM - 1) / GS_SMEM;
+    const unsigned long long bitmap_cost = (unsigned long long)(((hi - lo) >> 15) + 1u) * (512ull + size / 4u);
+    const unsigned long long other_cost = size <= 1024 ? 3300ull
+                                        : chunks > 32 ? ~0ull : chunks * 3300ull + 15ull * size;
+    if (bitmap_cost <= other_cost) {
+        sort_group_bitmap(a, size, lo, hi, tmp, buf, lane);
+        return;
     }
     if (size <= 1024) {
         // in the warp's shared buffer, padded to 1024: a bitonic network over compare pairs,
@@ -375,10 +438,8 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
         bitonic_smem_pairs(buf, lane);
         for (u32 i = lane; i < size; i += 32) a[i] = buf[i];
         __syncwarp();
-        return true;
+        return;
     }
-    const u32 chunks = (size + GS_SMEM - 1) / GS_SMEM;
-    if (chunks > 32) return false;
     for (u32 c = 0; c < chunks; ++c) {
         const u32 c0 = c * GS_SMEM, len = min((u32)GS_SMEM, size - c0);
         for (u32 i = lane; i < (u32)GS_SMEM; i += 32) buf[i] = i < len ? a[c0 + i] : 0xFFFFFFFFu;
@@ -387,7 +448,6 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
         for (u32 i = lane; i < len; i += 32) a[c0 + i] = buf[i];
         __syncwarp();
     }
-    if (chunks == 1) return true;
     // merge: lane c follows chunk c; the warp takes the smallest head each step
     u32 pc = (u32)lane < chunks ? (u32)lane * GS_SMEM : 0u;
     const u32 ec = (u32)lane < chunks ? min((u32)(lane + 1) * GS_SMEM, size) : 0u;
@@ -404,8 +464,14 @@ __device__ __forceinline__ bool sort_group(u32* a, u32 size, u32* tmp, u32* buf,
     __syncwarp();
     for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
     __syncwarp();
-    return true;
 }
+
+// Groups of more candidates than this are admitted by a whole block of k_admit rather than one
+// warp (their serial walk would outlast the rest of the launch).
+#ifndef FAR_ADMIT_BIG
+#define FAR_ADMIT_BIG 192
+#endif
+constexpr u32 ADMIT_BIG = FAR_ADMIT_BIG;
 
 // Warp w of W takes the groups w, w + W, w + 2W, ... (32 per pass, one per lane), so that the
 // large groups, which lie close together in group order, spread over the warps.
@@ -435,9 +501,11 @@ __device__ __forceinline__ void sort_lane(u32* a, u32 size, u32& head) {
 // flag the group's first input index (its voxel ordinal follows from a scan of the flags),
 // clear the slot's counter for the next insert and, with ASMD (a10), add the group to the
 // near-voxel sums when its voxel centre lies within r_c of the sensor. Groups larger than
-// GS_LANE_MAX are sorted afterwards by the whole warp, one at a time.
+// GS_LANE_MAX are sorted afterwards by the whole warp, one at a time; groups larger than
+// ADMIT_BIG are listed in big_list for the admission.
 __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u32* __restrict__ tmp,
-                                                    const u32* __restrict__ scal, const u32* __restrict__ gstart,
+                                                    u32* __restrict__ scal, u32* __restrict__ big_list,
+                                                    const u32* __restrict__ gstart,
                                                     const u32* __restrict__ gsize, const u32* __restrict__ gslot,
                                                     u32* __restrict__ slot_cnt, u32* __restrict__ flags,
                                                     const Slot* __restrict__ slots, double v, InsertCfg cfg,
@@ -470,15 +538,14 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
             const int f = __ffs(big) - 1;
             big &= big - 1u;
             const u32 fb = __shfl_sync(0xffffffffu, base, f), fs = __shfl_sync(0xffffffffu, size, f);
-            if (!sort_group(members + fb, fs, tmp + fb, sbuf[warp], lane)) {
-                if (lane == 0) atomicOr(&ctr->err, (u32)ERR_GROUP_SIZE);
-            }
+            sort_group(members + fb, fs, tmp + fb, sbuf[warp], lane);
             __syncwarp();
             if (lane == f) head = members[fb];
         }
         if (gv) {
             flags[head] = 1u;
             slot_cnt[h] = 0u;
+            if (size > ADMIT_BIG) big_list[atomicAdd(&scal[SCAL_NBIG], 1u)] = g;
             if (cfg.asmd) {
                 int kx, ky, kz;
                 unpack_key(slots[h].key, kx, ky, kz);
@@ -541,6 +608,8 @@ struct AdmitArgs {
     u32* grp_bucket;
     u32* grp_cnt0;
     int* grp_exp0;
+    const u32* big_list;  // groups above ADMIT_BIG members (SCAL_NBIG of them)
+    u32* big_next;        // the claim counter over big_list
 };
 
 // a11 admission. A warp takes 32 voxel groups at a time (strided over the group range): each
@@ -555,6 +624,141 @@ struct AdmitArgs {
 #define FAR_ADMIT_U 2
 #endif
 constexpr int ADMIT_U = FAR_ADMIT_U;
+
+// Admission of one large group by the whole block, the same decisions as the warp's walk in
+// k_admit: a candidate enters while the voxel holds fewer than its cap and every point in it is
+// at least d_min away, in input order. The candidates go in tiles of TPB * BIG_PER_THREAD
+// (candidate tile + r TPB + t on thread t). Each is tested once against the voxel's points so
+// far; then, round after round, the first candidate of the tile that still passes (a block
+// minimum of r TPB + t) is admitted, the ones before it are settled, and the later ones are
+// re-tested against it only. Thread 0 does the header steps of a lane of the warp path.
+constexpr int BIG_PER_THREAD = 4;
+
+__device__ __forceinline__ void admit_big_group(const AdmitArgs& a, u32 g, double n_near, u32 ring_tail,
+                                                float4* s_pts, u32* s_red, u32* s_hdr) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        const u32 start = a.gstart[g], size = a.gsize[g], slot = a.gslot[g];
+        const u32 ord = a.head_ord[a.sv[start]];
+        Slot* sp = a.slots + slot;
+        u32 bucket = sp->bucket;
+        const u32 cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
+        u32 cap = 0;
+        if (bucket == NO_BUCKET) {
+            const u32 h = atomicAdd(&a.ctr->ring_head, 1u);
+            if (h < ring_tail) {
+                bucket = a.ring[h % a.max_buckets];
+                sp->bucket = bucket;
+                sp->count = 0;
+                if (a.cexp) a.cexp[bucket] = EXP_NONE;
+                atomicAdd(&a.ctr->n_voxels, 1u);
+            } else {
+                atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
+                atomicAdd(&a.ctr->n_dropped, size);
+            }
+        }
+        if (bucket != NO_BUCKET) {
+            cap = a.nmax;
+            if (a.cfg.asmd) {
+                int kx, ky, kz;
+                unpack_key(sp->key, kx, ky, kz);
+                cap = asmd_cap(kx, ky, kz, a.v, a.cfg, n_near, a.k, a.nmax);
+            }
+            if (a.cexp) {
+                a.grp_bucket[ord] = bucket;
+                a.grp_cnt0[ord] = cnt;
+                a.grp_exp0[ord] = a.cexp[bucket];
+            }
+        }
+        if (cnt >= cap) a.grp_cnt[ord] = 0;
+        s_hdr[0] = start;
+        s_hdr[1] = start + size;
+        s_hdr[2] = slot;
+        s_hdr[3] = ord;
+        s_hdr[4] = bucket;
+        s_hdr[5] = cnt;
+        s_hdr[6] = cap;
+    }
+    __syncthreads();
+    const u32 start = s_hdr[0], end = s_hdr[1], slot = s_hdr[2], ord = s_hdr[3], bucket = s_hdr[4];
+    const u32 cnt0 = s_hdr[5], cap = s_hdr[6];
+    if (cnt0 >= cap) {
+        __syncthreads();   // s_hdr is read by every thread before the next group's header
+        return;
+    }
+    float4* bp = a.pts + (size_t)bucket * a.nmax;
+    for (u32 i = t; i < cnt0; i += TPB) s_pts[i] = bp[i];
+    __syncthreads();
+    u32 c_n = cnt0;
+    constexpr u32 TILE = TPB * BIG_PER_THREAD;
+    for (u32 tile = start; tile < end && c_n < cap; tile += TILE) {
+        float cx[BIG_PER_THREAD], cy[BIG_PER_THREAD], cz[BIG_PER_THREAD];
+        u32 pass = 0;
+#pragma unroll
+        for (int r = 0; r < BIG_PER_THREAD; ++r) {
+            const u32 i = tile + (u32)r * TPB + (u32)t;
+            cx[r] = cy[r] = cz[r] = 0.f;
+            if (i < end) {
+                const float4 p = a.world[a.sv[i]];
+                cx[r] = p.x;
+                cy[r] = p.y;
+                cz[r] = p.z;
+                pass |= 1u << r;
+            }
+        }
+        for (u32 j = 0; j < c_n && pass; ++j) {
+            const float4 e = s_pts[j];
+#pragma unroll
+            for (int r = 0; r < BIG_PER_THREAD; ++r)
+                if (((pass >> r) & 1u) && !(dist2_rn(cx[r], cy[r], cz[r], e.x, e.y, e.z) >= a.dmin2))
+                    pass &= ~(1u << r);
+        }
+        while (c_n < cap) {
+            // the tile's first passing candidate, as its tile order r TPB + t
+            u32 key = pass ? (u32)(__ffs(pass) - 1) * TPB + (u32)t : 0xFFFFFFFFu;
+            key = __reduce_min_sync(0xffffffffu, key);
+            if (lane == 0) s_red[warp] = key;
+            __syncthreads();
+            u32 best = s_red[0];
+#pragma unroll
+            for (int w = 1; w < TPB / 32; ++w) best = min(best, s_red[w]);
+            if (best == 0xFFFFFFFFu) break;
+            if ((u32)t == best % TPB) {
+                const u32 rb = best / TPB, i = tile + best, idx = a.sv[i];
+                float x = 0.f, y = 0.f, z = 0.f;
+#pragma unroll
+                for (int r = 0; r < BIG_PER_THREAD; ++r)
+                    if ((u32)r == rb) {
+                        x = cx[r];
+                        y = cy[r];
+                        z = cz[r];
+                    }
+                const float4 c = make_float4(x, y, z, __uint_as_float(NO_ID));
+                bp[c_n] = c;
+                s_pts[c_n] = c;
+                a.pos[idx] = bucket * a.nmax + c_n;
+                a.admitted[idx] = 1u;
+                a.a_ord[idx] = ord;
+                a.a_j[idx] = c_n - cnt0;
+            }
+            __syncthreads();   // the admitted point is in s_pts; every thread has read s_red
+            const float4 e = s_pts[c_n];
+            ++c_n;
+#pragma unroll
+            for (int r = 0; r < BIG_PER_THREAD; ++r) {
+                if (!((pass >> r) & 1u)) continue;
+                if ((u32)r * TPB + (u32)t <= best || !(dist2_rn(cx[r], cy[r], cz[r], e.x, e.y, e.z) >= a.dmin2))
+                    pass &= ~(1u << r);
+            }
+        }
+        __syncthreads();   // the last round's reads of s_red come before the next tile's writes
+    }
+    if (t == 0) {
+        if (c_n != cnt0) a.slots[slot].count = c_n;
+        a.grp_cnt[ord] = c_n - cnt0;
+    }
+    __syncthreads();   // s_pts and s_hdr are free for the next group
+}
 
 __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     pdl_wait();
@@ -582,9 +786,9 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
     const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     for (u32 j0 = 0; w + j0 * warps_total < ng; j0 += 32) {
-        // --- lane-parallel headers
+        // --- lane-parallel headers (large groups are left to whole blocks, below)
         const u32 g = w + (j0 + lane) * warps_total;
-        const bool gv = g < ng;
+        const bool gv = g < ng && a.gsize[g] <= ADMIT_BIG;
         u32 start = 0, end = 0, slot = 0, ord = 0, bucket = NO_BUCKET, cnt = 0, cap = 0;
         Slot* sp = nullptr;
         if (gv) {
@@ -715,6 +919,21 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
             }
         }
     }
+    // large groups, each by a whole block, claimed after the block's small groups (blocks
+    // without small groups start with them)
+    const u32 nbig = a.scal[SCAL_NBIG];
+    if (nbig) {
+        __shared__ u32 s_claim, s_red[TPB / 32], s_hdr[8];
+        __syncthreads();   // the warps' use of s_vox is over
+        for (;;) {
+            if (threadIdx.x == 0) s_claim = atomicAdd(a.big_next, 1u);
+            __syncthreads();
+            const u32 b = s_claim;
+            __syncthreads();   // read by every thread before thread 0 claims again
+            if (b >= nbig) break;
+            admit_big_group(a, a.big_list[b], n_near, ring_tail, s_vox[0], s_red, s_hdr);
+        }
+    }
 }
 
 // Admitted points after the two scans: the id (first id + rank in input order), the position
@@ -726,7 +945,8 @@ __global__ void k_place_admitted(const u32* __restrict__ admitted, const u32* __
                                  const u32* __restrict__ grp_base, const u32* __restrict__ pos, u32 n,
                                  float4* pts, u32* __restrict__ dest, u32* __restrict__ added,
                                  const u64* __restrict__ keys, u64* __restrict__ added_key,
-                                 const u32* __restrict__ scal, MapCounters* ctr) {
+                                 const u32* __restrict__ scal, MapCounters* ctr, const float4* __restrict__ in4,
+                                 float4* __restrict__ src, u32* __restrict__ src_index) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -744,6 +964,14 @@ __global__ void k_place_admitted(const u32* __restrict__ admitted, const u32* __
     dest[i] = d;
     if (added) added[d] = p;
     if (added_key) added_key[d] = keys[i];
+    if (src) {
+        // scan-local insert: the registration sources in the same grouped order (consecutive
+        // threads of the registration kernels then share their 27-neighbourhoods), w = the
+        // admission rank (the local id)
+        const float4 v = in4[i];
+        src[d] = make_float4(v.x, v.y, v.z, __uint_as_float(rank[i]));
+        src_index[d] = i;
+    }
 }
 
 // Lanes cooperating on one k-NN query (group_knn); every grid-stride step is warp-uniform.
@@ -913,21 +1141,6 @@ __global__ void k_src_encode(const u32* __restrict__ grp_base, const u32* __rest
             e_out[r] = (signed char)(E == EXP_NONE ? 0 : E);
         }
     }
-}
-
-// Sources in voxel-grouped order: consecutive threads of the registration kernels then
-// share their 27-neighbourhoods. w carries the admission rank (the local id).
-__global__ void k_make_sources(const u32* __restrict__ admitted, const u32* __restrict__ dest,
-                               const u32* __restrict__ rank, const float4* __restrict__ in4, u32 n,
-                               float4* __restrict__ src, u32* __restrict__ src_index) {
-    pdl_wait();
-    pdl_trigger();
-    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !admitted[i]) return;
-    const u32 d = dest[i];
-    const float4 v = in4[i];
-    src[d] = make_float4(v.x, v.y, v.z, __uint_as_float(rank[i]));
-    src_index[d] = i;
 }
 
 __global__ void k_iota(u32* a, u32 n) {
@@ -1226,7 +1439,8 @@ cudaError_t pack_points(const void* src, u32 n, u32 stride, float4* out, cudaStr
 }
 
 cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
-                             bool covariances, cudaStream_t st, DevicePose dpose, const InsertMarks* marks) {
+                             bool covariances, cudaStream_t st, DevicePose dpose, const InsertMarks* marks,
+                             bool emit_sources) {
     auto mark = [&](int i) {
         if (marks) cudaEventRecord(marks->ev[i], st);
     };
@@ -1241,8 +1455,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     Pose12 T{};
     if (pose) T = *pose;
     FAR_LAUNCH(k_world_keys, blocks_for(n), TPB, 0, st, s.in4, n, T, pose != nullptr || dpose.T != nullptr, dpose,
-               m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted, s.flags);
-    FAR_LAUNCH(k_find_or_insert, blocks_for(n), TPB, 0, st, s.keys, n, m.slots, m.mask, s.sk, s.sv, m.ctr,
+               m.inv_v, m.tv, s.world, s.keys, s.scal, m.ctr, s.admitted, s.flags, m.slots, m.mask, s.sk, s.sv,
                s.slot_cnt);
     mark(0);
     // groups by slot: contiguous ranges of s.sv_alt, each sorted by input index
@@ -1253,7 +1466,8 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     {
         // one resident wave (3 blocks of 8 warps per SM at 77 registers)
         const u32 warps = min(n, 152u * 24u);
-        FAR_LAUNCH(k_group_sort, blocks_for(warps * 32u), TPB, 0, st, s.sv_alt, s.sk_alt, s.scal, s.gstart, s.gsize,
+        FAR_LAUNCH(k_group_sort, blocks_for(warps * 32u), TPB, 0, st, s.sv_alt, s.sk_alt, s.scal, s.rank, s.gstart,
+                   s.gsize,
                    s.gslot, s.slot_cnt, s.flags, m.slots, (double)m.v, cfg, dpose.T, m.ctr);
     }
     // voxel ordinals in first-input-index order (k_world_keys cleared the flags)
@@ -1287,6 +1501,8 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     a.grp_bucket = s.grp_bucket;
     a.grp_cnt0 = s.grp_cnt0;
     a.grp_exp0 = s.grp_exp0;
+    a.big_list = s.rank;   // listed by k_group_sort; the ranks are written after the admission
+    a.big_next = s.scal + SCAL_BIGNEXT;
     // groups <= n, up to 32 per warp and pass; one resident wave (4 blocks of 8 warps per SM at
     // 64 registers)
     const u32 warps = min(n, 152u * 32u);
@@ -1299,7 +1515,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     const bool covs = covariances && (m.cov || prec);
     FAR_LAUNCH(k_place_admitted, blocks_for(n), TPB, 0, st, s.admitted, s.rank, s.a_ord, s.a_j, s.grp_cnt, s.pos, n,
                m.pts, s.dest, covs ? s.added : nullptr, s.keys, (covs && prec) ? s.added_key : nullptr, s.scal,
-               m.ctr);
+               m.ctr, s.in4, emit_sources ? s.src : nullptr, s.src_index);
     mark(4);
     if (covs && !prec)
         FAR_TRY(knn_cov(m, nullptr, s.added, n, s.scal + SCAL_NADMIT, m.cov, s.added, nullptr, st));
@@ -1315,7 +1531,6 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
 
 cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    FAR_LAUNCH(k_make_sources, blocks_for(n), TPB, 0, st, s.admitted, s.dest, s.rank, s.in4, n, s.src, s.src_index);
     FAR_TRY(knn_cov(local, s.src, nullptr, n, s.scal + SCAL_NADMIT, s.src_cov, nullptr, knn_ids_out, st));
     if (s.src_h4) {
         // precision variant: FP16 copies with one exponent per scan-local voxel

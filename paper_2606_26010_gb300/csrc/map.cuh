@@ -90,7 +90,10 @@ struct Scratch {
 };
 
 // SCAL_IDBASE: the map's next point id when the insert began (the first id it assigns)
-enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_IDBASE = 3, SCAL_COUNT = 8 };
+// SCAL_NBIG: groups above ADMIT_BIG members (listed by k_group_sort, admitted by whole blocks);
+// SCAL_BIGNEXT: the next of them a block of k_admit claims
+enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_IDBASE = 3, SCAL_NBIG = 4, SCAL_BIGNEXT = 5,
+       SCAL_COUNT = 8 };
 
 struct InsertCfg {
     int asmd = 0;
@@ -140,18 +143,19 @@ struct InsertMarks {
 
 // Insert the packed points s.in4[0..n) into m (Sec. III-A.3). pose == nullptr keys the
 // raw points (scan-local map). Ids start at m.ctr->next_id. With `covariances`, Eq. 1
-// covariances of the added points are computed against the updated map.
+// covariances of the added points are computed against the updated map. With `emit_sources`
+// (scan-local map), the admitted points are also written to s.src / s.src_index in
+// voxel-grouped order (s.src[j].w = admission rank).
 cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose, const InsertCfg& cfg,
                              bool covariances, cudaStream_t st, DevicePose dpose = DevicePose(),
-                             const InsertMarks* marks = nullptr);
+                             const InsertMarks* marks = nullptr, bool emit_sources = false);
 
 // Empty the scan-local map m after an insert of n points through scratch s (only the slots that
 // insert used), so that it can serve the next scan without a full clear.
 cudaError_t map_local_reset(DeviceMap& m, const Scratch& s, u32 n, cudaStream_t st);
 
-// Scan-local sources after map_insert_batch on the local map: s.src / s.src_index in
-// voxel-grouped order (s.src[j].w = admission rank), then their covariances from the
-// local map; knn_ids_out rows are indexed by rank.
+// Covariances of the scan-local sources (s.src, written by map_insert_batch on the local map
+// with emit_sources) from the local map; knn_ids_out rows are indexed by rank.
 cudaError_t make_sources(DeviceMap& local, Scratch& s, u32 n, u32* knn_ids_out, cudaStream_t st);
 
 // Reset a map to empty (keys, counters, free ring).

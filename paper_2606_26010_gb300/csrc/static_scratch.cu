@@ -191,7 +191,7 @@ extern "C" far_status far_scan_sources_static(const float* xyz, uint64_t n, uint
     if (e == cudaSuccess) e = pack_points(xyz, (u32)n, stride_bytes, s.in4, st);
     if (e == cudaSuccess) e = map_clear(local, st);
     InsertCfg cfg;
-    if (e == cudaSuccess) e = map_insert_batch(local, s, (u32)n, nullptr, cfg, false, st);
+    if (e == cudaSuccess) e = map_insert_batch(local, s, (u32)n, nullptr, cfg, false, st, DevicePose(), nullptr, true);
     if (e == cudaSuccess) e = make_sources(local, s, (u32)n, out_knn_ids, st);
     if (e == cudaSuccess) e = export_sources(s, (u32)n, out_index, out_cov, out_valid, st);
     u32 h_n = 0;

@@ -156,14 +156,47 @@ def test_no_spacing_and_single_voxel_cap(far):
 
 @pytest.mark.parametrize("size", [33, 513, 2500, 6000, 9000])
 def test_large_voxel_groups_admit_in_input_order(far, size):
-    """All points of a batch in a few voxels: groups above 32, 128 and 512 points (register sorts)
-    and above 1024 (chunks sorted in shared memory and merged) still admit in input order."""
+    """All points of a batch in a few voxels: groups above 32 and 128 points (register sorts; the
+    larger ones through a bitmap of their compact index range, and above 192 admitted by a whole
+    block) still admit in input order."""
     rng = np.random.default_rng(size)
     pts = rng.uniform(0.01, 0.99, size=(size, 3)).astype(np.float32)   # voxels (0|1, 0|1, 0|1) at v = 0.5
     for spacing in (0.0, 0.03):
         g, o = build_pair(far, [pts, pts[::-1].copy()], [np.eye(4), np.eye(4)], nmax=64, spacing=spacing,
                           max_scan=20_000)
         assert_maps_equal(g.export(), o.export())
+
+
+@pytest.mark.parametrize("n_total,stride", [(40_000, 1), (90_000, 10), (300_000, 200), (300_000, 500),
+                                            (1_200_000, 1000)])
+def test_voxel_groups_spread_over_the_input(far, n_total, stride):
+    """Every stride-th point falls in one voxel and the rest scatter over a 400 m cube (about one
+    per voxel), so that voxel's group spans the whole input order: 40000 points in one voxel and
+    groups of 9000 and 1500 whose ranges take 3 and 10 bitmap passes; 600 and 1200 points over
+    ranges wide enough that the shared-memory network and the chunk merge are the cheaper sorts.
+    All admit in input order (with ASMD caps for the 9000-point group)."""
+    rng = np.random.default_rng(n_total + stride)
+    pts = rng.uniform(-200.0, 200.0, size=(n_total, 3))
+    pts[::stride] = rng.uniform(0.01, 0.49, size=(len(pts[::stride]), 3))
+    g, o = build_pair(far, [pts.astype(np.float32)], [np.eye(4)], nmax=20, spacing=0.03, max_scan=n_total,
+                      max_voxels=1 << 21, asmd=stride == 10, r_near=5.0, r_max=150.0)
+    assert_maps_equal(g.export(), o.export())
+
+
+@pytest.mark.parametrize("spacing", [0.1, 0.0])
+def test_large_groups_that_never_fill_their_voxel(far, spacing):
+    """Large groups admitted by a whole block: 5000 points in a 5 cm cluster admit one point (with
+    d_min = 0.1 m) and walk every other candidate; a second insert adds a cluster 0.4 m away to the
+    partly filled voxel, and 3000 points in each of 8 voxels fill them (d_min = 0: to the cap)."""
+    rng = np.random.default_rng(21)
+    a = rng.uniform(0.02, 0.07, size=(5000, 3))
+    b = rng.uniform(0.30, 0.35, size=(5000, 3))
+    c = rng.uniform(0.51, 1.49, size=(24000, 3))
+    filler = rng.uniform(-30.0, 30.0, size=(3000, 3))
+    s1 = np.concatenate([a, filler, c])[rng.permutation(32000)].astype(np.float32)
+    s2 = np.concatenate([b, filler]).astype(np.float32)
+    g, o = build_pair(far, [s1, s2], [np.eye(4), np.eye(4)], nmax=20, spacing=spacing, max_scan=40_000)
+    assert_maps_equal(g.export(), o.export())
 
 
 # ------------------------------------------------------------------ searches

@@ -100,6 +100,18 @@ def test_prec_asmd_evict_and_growing_voxels(far):
     assert_prec_maps_equal(g, o)
 
 
+def test_prec_large_voxel_groups(far):
+    """Groups above 192 candidates (admitted by a whole block) in a precision map: 8 voxels of
+    ~1100 points each, then a second insert into the full voxels and 5000 points in a 5 cm
+    cluster of a new voxel (one admitted with d_min = v / sqrt(N_max), the rest walked)."""
+    rng = np.random.default_rng(11)
+    s1 = rng.uniform(0.01, 0.99, size=(9000, 3)).astype(np.float32)
+    s2 = np.concatenate([rng.uniform(0.01, 0.99, size=(3000, 3)),
+                         rng.uniform(1.52, 1.57, size=(5000, 3))]).astype(np.float32)
+    g, o = build_prec_pair(far, [s1, s2], [np.eye(4), np.eye(4)], max_scan=20_000)
+    assert_prec_maps_equal(g, o)
+
+
 @pytest.mark.parametrize("offset", [np.zeros(3), ODD_OFFSET])
 def test_prec_nearest_and_knn_bit_exact(far, offset):
     p = synth.single_scan_problem(2)
