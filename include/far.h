@@ -451,6 +451,20 @@ far_status far_ekf_create(const far_ekf_params* params, double t0, const double 
 far_status far_ekf_destroy(far_ekf* ekf);
 far_status far_ekf_predict(far_ekf* ekf, double t, const double acc[3], const double gyro[3]);
 far_status far_ekf_update(far_ekf* ekf, double t_meas, const double pose[16], const double v_L[3]);
+/*
+ * The upsampled update of Sec. III-B (end): the measurement is projected by Eq. 11 and its
+ * Kalman gain and covariance update are those of far_ekf_update, but the state correction
+ * K y is spread in `cycles` equal shares over as many update cycles: one share now, one
+ * after each of the next cycles - 1 far_ekf_predict calls (added after that call's
+ * propagation, before its state enters the history), so the odometry moves smoothly
+ * instead of jumping at each LiDAR measurement. cycles = 1 is far_ekf_update. A new update
+ * first adds the shares still pending at once. Choose cycles so that the shares are added
+ * before the next measurement's time stamp: Eq. 11 compares that measurement with the
+ * stored state at its time, which holds only the shares added by then.
+ * FAR_ERR_INVALID when cycles is outside 1..1000.
+ */
+far_status far_ekf_update_spread(far_ekf* ekf, double t_meas, const double pose[16], const double v_L[3],
+                                 uint32_t cycles);
 /* Current time, state, covariance (row-major 9x9) and pose (row-major 4x4); any may be NULL. */
 far_status far_ekf_get(const far_ekf* ekf, double* t, double x[9], double P[81], double pose[16]);
 

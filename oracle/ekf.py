@@ -18,6 +18,10 @@ far_ekf_* calls) never does and shares no code with it.
                           h(x) = x (the reference roll/pitch of the cited filter is not built)
   delay compensation .... Eq. 11: z_k = z_s + h(x_{k|k-1}) - h(x_s), x_s the filter's state
                           at the measurement's time stamp
+  upsampling ............ Sec. III-B (end), read as: the correction K y of one measurement is
+                          added in U equal shares over U update cycles (one now, one after
+                          each of the next U - 1 predictions); the covariance is updated at
+                          once; a new measurement first adds the shares still pending
 
 The linearisation of the transition uses five-point central differences here (the library uses
 the analytic Jacobian), so the two implementations share no derivative code.
@@ -110,6 +114,12 @@ class KinematicEKF:
         self.time = float(t0)
         self.hist = [(self.time, self.x.copy())]
         self.history = int(history)
+        self.pending = []                      # shares of a spread correction still to add
+
+    def _add_share(self):
+        self.x = self.x + self.pending.pop(0)
+        for a in (3, 4, 5):
+            self.x[a] = wrap(self.x[a])
 
     def predict(self, t: float, acc, gyro):
         dt = float(t) - self.time
@@ -123,6 +133,8 @@ class KinematicEKF:
         self.x = f(self.x)
         self.P = F @ self.P @ F.T + np.diag(self.q) * dt
         self.time = float(t)
+        if self.pending:
+            self._add_share()
         self.hist.append((self.time, self.x.copy()))
         if len(self.hist) > self.history:
             self.hist.pop(0)
@@ -135,7 +147,9 @@ class KinematicEKF:
                 best = xs
         return best
 
-    def update(self, t_meas: float, T_L, v_L):
+    def update(self, t_meas: float, T_L, v_L, cycles: int = 1):
+        while self.pending:
+            self._add_share()
         z_s = np.concatenate([np.asarray(T_L, float)[:3, 3], euler_from_rot(np.asarray(T_L, float)[:3, :3]),
                               np.asarray(v_L, float)])
         x_s = self.state_at(t_meas)
@@ -147,9 +161,8 @@ class KinematicEKF:
         S = self.P + np.diag(self.r)
         K = self.P @ np.linalg.inv(S)
         I_K = np.eye(9) - K
-        self.x = self.x + K @ y
-        for a in (3, 4, 5):
-            self.x[a] = wrap(self.x[a])
+        self.pending = [K @ y / cycles for _ in range(cycles)]
+        self._add_share()
         self.P = I_K @ self.P @ I_K.T + K @ np.diag(self.r) @ K.T
         return y
 

@@ -109,6 +109,20 @@ struct far_ekf {
     std::vector<double> hist_t;   // ring of (time, state) for delay compensation
     std::vector<double> hist_x;
     uint32_t hist_n = 0, hist_head = 0;
+    // a state correction spread over update cycles: `share` is added after each of the next
+    // `shares_left` predictions
+    double share[9] = {};
+    uint32_t shares_left = 0;
+
+    void add_share() {
+        for (int i = 0; i < 9; ++i) x[i] += share[i];
+        for (int a = 3; a < 6; ++a) x[a] = wrap_angle(x[a]);
+        --shares_left;
+    }
+    // a new measurement first takes the remaining shares of the previous one at once
+    void flush_shares() {
+        while (shares_left) add_share();
+    }
 
     void push() {
         const uint32_t cap = p.history;
@@ -236,14 +250,22 @@ far_status far_ekf_predict(far_ekf* e, double t, const double acc[3], const doub
         }
     std::memcpy(e->P, Pn, sizeof(Pn));
     e->t = t;
+    if (e->shares_left) e->add_share();   // this cycle's share of a spread correction
     e->push();
     return FAR_OK;
 }
 
 far_status far_ekf_update(far_ekf* e, double t_meas, const double pose[16], const double v_L[3]) {
+    return far_ekf_update_spread(e, t_meas, pose, v_L, 1u);
+}
+
+far_status far_ekf_update_spread(far_ekf* e, double t_meas, const double pose[16], const double v_L[3],
+                                 uint32_t cycles) {
     if (!e || !pose || !v_L) return bad("far_ekf_update: NULL argument");
     if (!std::isfinite(t_meas) || !finite_n(pose, 12) || !finite_n(v_L, 3))
         return bad("far_ekf_update: non-finite input");
+    if (cycles < 1 || cycles > 1000) return bad("far_ekf_update_spread: cycles must be in 1..1000");
+    e->flush_shares();
     // measurement at its own time s: z_s = [t_L, theta_L, v_L]
     double z[9];
     z[0] = pose[3];
@@ -272,12 +294,22 @@ far_status far_ekf_update(far_ekf* e, double t_meas, const double pose[16], cons
     double K[81];
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j < 9; ++j) K[9 * i + j] = Kt[9 * j + i];
+    // the correction K y, all at once or in equal shares over `cycles` update cycles (this one
+    // and the next cycles - 1 predictions); the covariance takes the whole update now
+    double dx[9];
     for (int i = 0; i < 9; ++i) {
         double s = 0.0;
         for (int j = 0; j < 9; ++j) s += K[9 * i + j] * y[j];
-        e->x[i] += s;
+        dx[i] = s;
     }
-    for (int a = 3; a < 6; ++a) e->x[a] = wrap_angle(e->x[a]);
+    if (cycles == 1) {
+        for (int i = 0; i < 9; ++i) e->x[i] += dx[i];
+        for (int a = 3; a < 6; ++a) e->x[a] = wrap_angle(e->x[a]);
+    } else {
+        for (int i = 0; i < 9; ++i) e->share[i] = dx[i] / (double)cycles;
+        e->shares_left = cycles;
+        e->add_share();
+    }
     // Joseph form: P = (I - K) P (I - K)^T + K R K^T
     double IK[81], A[81], Pn[81];
     for (int i = 0; i < 9; ++i)

@@ -153,6 +153,7 @@ _SIGS = {
     "far_ekf_destroy": (ctypes.c_int, [_vp]),
     "far_ekf_predict": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
     "far_ekf_update": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
+    "far_ekf_update_spread": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, ctypes.c_uint32]),
     "far_ekf_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "far_motion_fit": (ctypes.c_int, [_vp, _vp, _vp, _u32, ctypes.c_double, _u32, _vp]),
     "far_undistort": (ctypes.c_int, [_vp, _u64, _u32, _vp, _vp, _vp]),
@@ -575,9 +576,12 @@ class Ekf:
         g = np.ascontiguousarray(gyro, np.float64).reshape(3)
         _check(self._L.far_ekf_predict(self._h, float(t), _p(a), _p(g)))
 
-    def update(self, t_meas, pose, v_l):
+    def update(self, t_meas, pose, v_l, cycles=1):
         v = np.ascontiguousarray(v_l, np.float64).reshape(3)
-        _check(self._L.far_ekf_update(self._h, float(t_meas), _p(_pose(pose)), _p(v)))
+        if cycles == 1:
+            _check(self._L.far_ekf_update(self._h, float(t_meas), _p(_pose(pose)), _p(v)))
+        else:
+            _check(self._L.far_ekf_update_spread(self._h, float(t_meas), _p(_pose(pose)), _p(v), int(cycles)))
 
     def get(self):
         t = ctypes.c_double(0)

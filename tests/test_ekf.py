@@ -142,6 +142,50 @@ def test_angle_innovation_wraps_across_pi():
     assert abs(y[5] - 0.02) < 1e-12
 
 
+def test_spread_update_adds_equal_shares_of_the_scalar_correction():
+    """Upsampling (Sec. III-B, end): with zero-length cycles between them (F = I, no process
+    noise) the j-th of U shares leaves the state at x0 + (j / U) p / (p + r) (z - x0), the
+    scalar filter's correction in equal parts, and the covariance takes its whole update at
+    once: p r / (p + r)."""
+    p = np.array([0.5, 0.2, 0.1, 0.01, 0.02, 0.03, 1.0, 2.0, 0.5])
+    r = np.array([0.1, 0.1, 0.2, 0.001, 0.004, 0.002, 0.5, 0.5, 1.0])
+    x0 = np.array([1.0, 2.0, 3.0, 0.01, -0.02, 0.5, 0.0, 0.0, 0.0])
+    z = np.array([1.3, 1.9, 3.2, 0.015, -0.01, 0.45, 0.5, -0.2, 0.1])
+    U = 4
+    f = oe.KinematicEKF(x0, np.diag(p), np.zeros(9), r)
+    f.update(0.0, make_pose(oe.rot_zyx(z[3:6]), z[:3]), z[6:9], cycles=U)
+    full = p / (p + r) * (z - x0)
+    np.testing.assert_allclose(f.P, np.diag(p * r / (p + r)), atol=1e-14)
+    for j in range(1, U + 2):
+        np.testing.assert_allclose(f.x, x0 + min(j, U) / U * full, atol=1e-12)
+        f.predict(0.0, [0.0, 0.0, G], [0.0, 0.0, 0.0])   # a zero-length cycle (at rest, level)
+
+
+def test_spread_update_divides_the_jump_of_the_odometry():
+    """On a straight line with exact IMU, a measurement offset from the true state moves the
+    filter's output at the update cycle by K y with one cycle and by K y / U when spread; the
+    shares then follow one per cycle."""
+    dt, U = 0.01, 5
+    x0 = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.2, 20.0, 0.0, 0.0])
+    offset = np.array([0.3, -0.1, 0.05, 0.0, 0.0, 0.01, 0.2, 0.0, 0.0])
+    jumps = {}
+    for cycles in (1, U):
+        f = oe.KinematicEKF(x0, np.eye(9) * 0.1, np.zeros(9), np.ones(9) * 0.1)
+        for k in range(1, 31):
+            f.predict(k * dt, [0.5, 0.0, G], [0.0, 0.0, 0.0])
+        before = f.x.copy()
+        xs = before + offset
+        f.update(30 * dt, make_pose(oe.rot_zyx(xs[3:6]), xs[:3]), xs[6:9], cycles=cycles)
+        jumps[cycles] = f.x - before
+        if cycles == U:
+            assert len(f.pending) == U - 1
+            for k in range(31, 31 + U - 1):
+                f.predict(k * dt, [0.5, 0.0, G], [0.0, 0.0, 0.0])
+            assert not f.pending
+    np.testing.assert_allclose(jumps[U], jumps[1] / U, atol=1e-13)
+    assert np.linalg.norm(jumps[1]) > 0.1
+
+
 # ----------------------------------------------------------------------------- library vs oracle
 def test_library_lidar_velocity_matches_oracle():
     from paper_2606_26010_gb300 import far
@@ -152,11 +196,12 @@ def test_library_lidar_velocity_matches_oracle():
                                    atol=1e-12)
 
 
-@pytest.mark.parametrize("t_start", [0.0, 10.05])   # a straight, then the entry into the curve
-def test_library_ekf_matches_oracle_on_the_track(t_start):
+@pytest.mark.parametrize("t_start,cycles", [(0.0, 1), (10.05, 1), (10.05, 4), (0.0, 15)])
+def test_library_ekf_matches_oracle_on_the_track(t_start, cycles):
     """Two seconds of noisy 100 Hz IMU along the track (the curve entry included for the second
     start), LiDAR updates every 0.1 s from noisy poses, each applied 30 ms after its time stamp
-    (delay compensation)."""
+    (delay compensation), at once or spread over `cycles` IMU cycles (15: shares still pending
+    when the next update comes, which adds them at once first)."""
     from paper_2606_26010_gb300 import far
     seq = synth.TrackSequence(42)
     rng = np.random.default_rng(5)
@@ -180,12 +225,12 @@ def test_library_ekf_matches_oracle_on_the_track(t_start):
             pending.append((t, Tn, synth.track_body_velocity(seq, t) + rng.normal(scale=0.05, size=3)))
         while pending and pending[0][0] + 0.03 <= t + 1e-9:
             ts, Tn, vn = pending.pop(0)
-            lib.update(ts, Tn, vn)
-            ora.update(ts, Tn, vn)
-            _, xl, Pl, Tl = lib.get()
-            np.testing.assert_allclose(xl, ora.x, rtol=1e-10, atol=1e-9)
-            np.testing.assert_allclose(Pl, ora.P, rtol=1e-6, atol=1e-8)
-            np.testing.assert_allclose(Tl, ora.pose(), rtol=1e-10, atol=1e-9)
+            lib.update(ts, Tn, vn, cycles=cycles)
+            ora.update(ts, Tn, vn, cycles=cycles)
+        _, xl, Pl, Tl = lib.get()   # every cycle, so the spread shares are compared too
+        np.testing.assert_allclose(xl, ora.x, rtol=1e-10, atol=1e-9)
+        np.testing.assert_allclose(Pl, ora.P, rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(Tl, ora.pose(), rtol=1e-10, atol=1e-9)
     # the filter tracks the truth (positions to centimetres, heading to a milliradian)
     T_true = synth.sequence_pose_at(seq, times[-1])
     _, xl, _, _ = lib.get()
@@ -202,3 +247,6 @@ def test_library_ekf_rejects_bad_input():
         e.predict(0.5, [0, 0, G], [0, 0, 0])                             # time going back
     with pytest.raises(far.FarError):
         far.lidar_velocity(np.eye(4), np.eye(4), 0.0)
+    for cycles in (0, 1001):
+        with pytest.raises(far.FarError):
+            e.update(1.0, np.eye(4), [0, 0, 0], cycles=cycles)
