@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import csv
 import dataclasses
+import gc
 import hashlib
 import io
 import json
@@ -192,16 +193,16 @@ class Prior:
             self.state_v = lambda: self.ekf.x[6:9].copy()
         self.imu = imu_stream(veh)
         self.k = 0            # next IMU sample
-        self.samples = []     # (time, measured rate, filtered body velocity) after each prediction
+        # the filtered body velocity after each prediction (with the IMU's time and measured rate
+        # of the same sample, the velocity history that the de-skew lines are fitted to)
+        self.vel_hist = np.zeros((len(self.imu[0]), 3))
 
     def _predict_to(self, t_s: float):
         times, acc, gyro = self.imu
         while self.k < len(times) and times[self.k] <= t_s + 1e-9:
             self.ekf.predict(times[self.k], acc[self.k], gyro[self.k])
-            self.samples.append((times[self.k], gyro[self.k], self.state_v()))
+            self.vel_hist[self.k] = self.state_v()
             self.k += 1
-        if len(self.samples) > 64:
-            del self.samples[:-64]
 
     def init(self, t: int, ests) -> np.ndarray:
         self._predict_to(t * self.frame_dt)
@@ -213,10 +214,11 @@ class Prior:
         """Lines through the rates and velocities of scan t's sweep (its 0.1 s up to t / 10 s):
         far_motion_fit (library) or the oracle's fit, as a far.Motion or a dict."""
         t_ref = t * self.frame_dt
-        sel = [s_ for s_ in self.samples if t_ref - self.frame_dt - 1e-9 < s_[0] <= t_ref + 1e-9]
-        tt = np.array([s_[0] for s_ in sel])
-        w = np.array([s_[1] for s_ in sel])
-        v = np.array([s_[2] for s_ in sel])
+        times, _, gyro = self.imu
+        # the samples predicted so far with t_ref - frame_dt < time <= t_ref (times ascending)
+        i0 = int(np.searchsorted(times[:self.k], t_ref - self.frame_dt - 1e-9, side="right"))
+        i1 = int(np.searchsorted(times[:self.k], t_ref + 1e-9, side="right"))
+        tt, w, v = times[i0:i1], gyro[i0:i1], self.vel_hist[i0:i1]
         if self.impl == "library":
             from paper_2606_26010_gb300 import far
             return far.motion_fit(tt, w, v, t_ref, time_offset_bytes=12)
@@ -364,6 +366,11 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
     recs = []
     prior = Prior(veh, prior_kind, "library", rng)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # Python's cycle collector runs between the steps, outside the timed regions (a collection
+    # that an allocation triggers inside one would pause the host for up to a millisecond);
+    # the objects alive before the run are frozen so that these collections stay short
+    gc.collect()
+    gc.freeze()
     with torch.cuda.stream(stream):
         for t in range(1, n_seq):
             if clk is not None and t == timed_from:
@@ -371,6 +378,7 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
                 clk.__enter__()
             init = prior.init(t, ests)
             tau, kappa = thr.get()
+            gc.collect()
             flush.zero_()
             if e2e:
                 torch.cuda.synchronize()
@@ -398,6 +406,7 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
     if clk is not None:
         torch.cuda.synchronize()
         clk.__exit__(None, None, None)
+    gc.unfreeze()
     return recs
 
 
