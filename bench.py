@@ -276,7 +276,10 @@ def cpu_model() -> str:
 
 # --------------------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms around the timed region. The
+    sampler is started a few steps before the timed region and the first sample is awaited
+    between steps: nvidia-smi's start-up takes driver locks that can stall the CUDA calls of a
+    step running at the same time by tens of milliseconds."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -284,26 +287,44 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.reader = None
         self.out = ""
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
         except (OSError, ValueError):
             self.proc = None
+        self.wait_first()
         return self
+
+    def wait_first(self, timeout: float = 3.0):
+        """Block (between steps) until the first sample has arrived."""
+        t_end = time.perf_counter() + timeout
+        while (self.proc is not None and self.proc.poll() is None and not self.lines
+               and time.perf_counter() < t_end):
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
+            if self.reader is not None:
+                self.reader.join(timeout=5)
+            self.out = "".join(self.lines)
 
     def summary(self):
         rows = [r for r in csv.reader(io.StringIO(self.out)) if len(r) >= 9]
@@ -372,8 +393,9 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
     gc.collect()
     gc.freeze()
     with torch.cuda.stream(stream):
+        clk_from = max(1, timed_from - 5)
         for t in range(1, n_seq):
-            if clk is not None and t == timed_from:
+            if clk is not None and t == clk_from:
                 torch.cuda.synchronize()
                 clk.__enter__()
             init = prior.init(t, ests)

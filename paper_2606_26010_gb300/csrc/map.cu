@@ -200,12 +200,17 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
     find_or_insert_slot(key, i, n, slots, mask, out_slot, out_rank, ctr, slot_cnt);
 }
 
+// Groups of more members than this are sorted by a whole block of k_group_sort (one pass over
+// a bitmap of up to 262144 input indices in the block's shared memory) instead of one warp.
+constexpr u32 GS_BLOCK_MIN = 1024;
+
 // Groups: the first point of each slot (rank 0) opens the slot's group, a contiguous range
 // of its size taken from the running total, and records it under a group index. The heads of
 // a warp take their group indices and ranges with one atomic each.
 __global__ void k_group_alloc(const u32* __restrict__ slot_of, const u32* __restrict__ rank, u32 n, u32 sentinel,
                               const u32* __restrict__ slot_cnt, u32* __restrict__ slot_base, u32* __restrict__ scal,
-                              u32* __restrict__ gstart, u32* __restrict__ gsize, u32* __restrict__ gslot) {
+                              u32* __restrict__ gstart, u32* __restrict__ gsize, u32* __restrict__ gslot,
+                              u32* __restrict__ huge_list) {
     pdl_wait();
     pdl_trigger();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,6 +245,7 @@ __global__ void k_group_alloc(const u32* __restrict__ slot_of, const u32* __rest
     gstart[g] = base;
     gsize[g] = size;
     gslot[g] = h;
+    if (size > GS_BLOCK_MIN) huge_list[atomicAdd(&scal[SCAL_NHUGE], 1u)] = g;
 }
 
 // Every point to its place in its group (arrival order for now).
@@ -261,11 +267,11 @@ __device__ __forceinline__ double centre_dist2(int kx, int ky, int kz, double v,
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Sort of one group's input indices by one warp (values are distinct). Groups of up to 128 are
-// sorted in registers (bitonic network over 32 lanes x R values). Larger ones take the cheaper
-// of a bitmap of their index range (sort_group_bitmap; its cost grows with the range) and a
-// comparison sort: up to 1024 in the warp's shared buffer (bitonic over compare pairs), else
-// chunks of GS_SMEM sorted in shared memory and merged through `tmp` (at most 32 chunks).
+// Sort of one group's input indices by one warp (values are distinct; at most GS_BLOCK_MIN of
+// them, larger groups go to whole blocks). Groups of up to 128 are sorted in registers (bitonic
+// network over 32 lanes x R values). Larger ones take the cheaper of a bitmap of their index
+// range (sort_group_bitmap; its cost grows with the range) and a bitonic network over compare
+// pairs in the warp's shared buffer of GS_SMEM values.
 constexpr int GS_SMEM = 1024;
 constexpr int GS_WARPS = TPB / 32;
 
@@ -398,6 +404,107 @@ __device__ __forceinline__ void sort_group_bitmap(u32* a, u32 size, u32 lo, u32 
     }
 }
 
+// Sort of one group's distinct input indices by the whole block, through a bitmap of their range
+// [lo, hi] in windows of 262144 values (8192 words of shared memory, `buf`): all members are
+// marked, then the words are read back in rows of 32 consecutive words (one per lane, the
+// block's warps taking the rows in turn). A first read gives each row's count, one warp turns
+// the counts into row offsets, and a second read writes every member at its row offset plus its
+// lane prefix. With one window the output goes to `a` in place (every member is marked before
+// any is written), else through `tmp`. Every thread of the block must call this; it ends with a
+// barrier. s_rows holds 256 words, s_red 2 * GS_WARPS.
+constexpr u32 GSB_WORDS = GS_WARPS * GS_SMEM;        // 8192
+constexpr u32 GSB_SPAN = GSB_WORDS * 32u;             // 262144 values per window
+__device__ __forceinline__ void sort_group_block(u32* a, u32 size, u32* tmp, u32* buf, u32* s_rows, u32* s_red) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    u32 lo = 0xFFFFFFFFu, hi = 0u;
+    for (u32 i = t; i < size; i += TPB) {
+        const u32 x = a[i];
+        lo = min(lo, x);
+        hi = max(hi, x);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        s_red[warp] = lo;
+        s_red[GS_WARPS + warp] = hi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w2 = 0; w2 < GS_WARPS; ++w2) {
+        lo = min(lo, s_red[w2]);
+        hi = max(hi, s_red[GS_WARPS + w2]);
+    }
+    const u32 passes = ((hi - lo) / GSB_SPAN) + 1u;
+    u32* out = passes == 1u ? a : tmp;
+    u32 pos = 0;   // members written by the windows before (the same in every thread)
+    for (u32 p = 0; p < passes; ++p) {
+        const u32 w0 = lo + p * GSB_SPAN;
+        const u32 span = min(hi - w0, GSB_SPAN - 1u);   // the window's last offset that can hold a member
+        const u32 rows = (span >> 10) + 1u;             // rows of 32 words (1024 values)
+        __syncthreads();   // the previous window's readers (and s_red's) are done
+        for (u32 i = t; i < rows * 32u; i += TPB) buf[i] = 0u;
+        __syncthreads();
+        for (u32 i = t; i < size; i += TPB) {
+            const u32 d = a[i] - w0;
+            if (d <= span) atomicOr(&buf[d >> 5], 1u << (d & 31u));
+        }
+        __syncthreads();
+        for (u32 r = warp; r < rows; r += GS_WARPS) {
+            const u32 c = __reduce_add_sync(0xffffffffu, (u32)__popc(buf[r * 32u + lane]));
+            if (lane == 0) s_rows[r] = c;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive offsets of the rows (at most 256: 8 per lane), the window's total last
+            u32 v[8];
+            u32 sum = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const u32 r = (u32)lane * 8u + (u32)k;
+                v[k] = r < rows ? s_rows[r] : 0u;
+                sum += v[k];
+            }
+            u32 incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            u32 run = incl - sum;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const u32 r = (u32)lane * 8u + (u32)k;
+                if (r < rows) s_rows[r] = run;
+                run += v[k];
+            }
+            if (lane == 31) s_red[0] = incl;
+        }
+        __syncthreads();
+        for (u32 r = warp; r < rows; r += GS_WARPS) {
+            u32 word = buf[r * 32u + lane];
+            const u32 c = __popc(word);
+            u32 incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            u32 q = pos + s_rows[r] + incl - c;
+            const u32 base = w0 + ((r * 32u + (u32)lane) << 5);
+            while (word) {
+                out[q++] = base + (u32)(__ffs(word) - 1);
+                word &= word - 1u;
+            }
+        }
+        pos += s_red[0];
+    }
+    __syncthreads();
+    if (passes > 1u) {
+        for (u32 i = t; i < size; i += TPB) a[i] = tmp[i];
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ void sort_group(u32* a, u32 size, u32* tmp, u32* buf, int lane) {
     if (size <= 1) return;
     if (size <= 32) {
@@ -420,49 +527,19 @@ __device__ __forceinline__ void sort_group(u32* a, u32 size, u32* tmp, u32* buf,
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     // estimated instructions per lane of each way: the bitmap ~512 per 32768 values of range
-    // plus ~8 per 32 members and pass; the shared-memory network ~3300 per 1024 values and the
-    // serial merge of its chunks ~15 per member
-    const unsigned long long chunks = (size + GS_SMEM - 1) / GS_SMEM;
+    // plus ~8 per 32 members and pass; the shared-memory network ~3300 (up to 1024 values;
+    // larger groups are sorted by whole blocks, see sort_group_block)
     const unsigned long long bitmap_cost = (unsigned long long)(((hi - lo) >> 15) + 1u) * (512ull + size / 4u);
-    const unsigned long long other_cost = size <= 1024 ? 3300ull
-                                        : chunks > 32 ? ~0ull : chunks * 3300ull + 15ull * size;
-    if (bitmap_cost <= other_cost) {
+    if (bitmap_cost <= 3300ull) {
         sort_group_bitmap(a, size, lo, hi, tmp, buf, lane);
         return;
     }
-    if (size <= 1024) {
-        // in the warp's shared buffer, padded to 1024: a bitonic network over compare pairs,
-        // each lane taking 16 of a stage's 512 pairs, their loads issued in batches of 8
-        for (u32 i = lane; i < 1024; i += 32) buf[i] = i < size ? a[i] : 0xFFFFFFFFu;
-        __syncwarp();
-        bitonic_smem_pairs(buf, lane);
-        for (u32 i = lane; i < size; i += 32) a[i] = buf[i];
-        __syncwarp();
-        return;
-    }
-    for (u32 c = 0; c < chunks; ++c) {
-        const u32 c0 = c * GS_SMEM, len = min((u32)GS_SMEM, size - c0);
-        for (u32 i = lane; i < (u32)GS_SMEM; i += 32) buf[i] = i < len ? a[c0 + i] : 0xFFFFFFFFu;
-        __syncwarp();
-        bitonic_smem_pairs(buf, lane);
-        for (u32 i = lane; i < len; i += 32) a[c0 + i] = buf[i];
-        __syncwarp();
-    }
-    // merge: lane c follows chunk c; the warp takes the smallest head each step
-    u32 pc = (u32)lane < chunks ? (u32)lane * GS_SMEM : 0u;
-    const u32 ec = (u32)lane < chunks ? min((u32)(lane + 1) * GS_SMEM, size) : 0u;
-    for (u32 o = 0; o < size; ++o) {
-        const u32 head = pc < ec ? a[pc] : 0xFFFFFFFFu;
-        u32 m = head;
-#pragma unroll
-        for (int s2 = 16; s2 > 0; s2 >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, s2));
-        if (head == m && pc < ec) {
-            tmp[o] = m;
-            ++pc;
-        }
-    }
+    // in the warp's shared buffer, padded to 1024: a bitonic network over compare pairs, each
+    // lane taking 16 of a stage's 512 pairs, their loads issued in batches of 8
+    for (u32 i = lane; i < 1024; i += 32) buf[i] = i < size ? a[i] : 0xFFFFFFFFu;
     __syncwarp();
-    for (u32 i = lane; i < size; i += 32) a[i] = tmp[i];
+    bitonic_smem_pairs(buf, lane);
+    for (u32 i = lane; i < size; i += 32) a[i] = buf[i];
     __syncwarp();
 }
 
@@ -502,14 +579,16 @@ __device__ __forceinline__ void sort_lane(u32* a, u32 size, u32& head) {
 // clear the slot's counter for the next insert and, with ASMD (a10), add the group to the
 // near-voxel sums when its voxel centre lies within r_c of the sensor. Groups larger than
 // GS_LANE_MAX are sorted afterwards by the whole warp, one at a time; groups larger than
-// ADMIT_BIG are listed in big_list for the admission.
+// GS_BLOCK_MIN (listed by k_group_alloc in huge_list) by whole blocks once their warps are
+// done; groups larger than ADMIT_BIG are listed in big_list for the admission.
 __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u32* __restrict__ tmp,
                                                     u32* __restrict__ scal, u32* __restrict__ big_list,
                                                     const u32* __restrict__ gstart,
                                                     const u32* __restrict__ gsize, const u32* __restrict__ gslot,
                                                     u32* __restrict__ slot_cnt, u32* __restrict__ flags,
                                                     const Slot* __restrict__ slots, double v, InsertCfg cfg,
-                                                    const double* __restrict__ dev_T, MapCounters* ctr) {
+                                                    const double* __restrict__ dev_T, MapCounters* ctr,
+                                                    const u32* __restrict__ huge_list) {
     pdl_wait();
     pdl_trigger();
     __shared__ u32 sbuf[GS_WARPS][GS_SMEM];
@@ -527,13 +606,15 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
         const u32 g = w + (j0 + lane) * warps_total;
         const bool gv = g < ng;
         u32 base = 0, size = 0, h = 0, head = 0;
+        bool mine = false;   // sorted here (groups above GS_BLOCK_MIN go to whole blocks below)
         if (gv) {
             base = gstart[g];
             size = gsize[g];
             h = gslot[g];
+            mine = size <= GS_BLOCK_MIN;
             if (size <= GS_LANE_MAX) sort_lane(members + base, size, head);
         }
-        u32 big = __ballot_sync(0xffffffffu, gv && size > GS_LANE_MAX);
+        u32 big = __ballot_sync(0xffffffffu, mine && size > GS_LANE_MAX);
         while (big) {
             const int f = __ffs(big) - 1;
             big &= big - 1u;
@@ -542,7 +623,7 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
             __syncwarp();
             if (lane == f) head = members[fb];
         }
-        if (gv) {
+        if (mine) {
             flags[head] = 1u;
             slot_cnt[h] = 0u;
             if (size > ADMIT_BIG) big_list[atomicAdd(&scal[SCAL_NBIG], 1u)] = g;
@@ -564,6 +645,35 @@ __global__ void __launch_bounds__(TPB) k_group_sort(u32* __restrict__ members, u
     if (lane == 0 && near_cnt) {
         atomicAdd(&ctr->near_sum, near_sum);
         atomicAdd(&ctr->near_cnt, near_cnt);
+    }
+    // groups above GS_BLOCK_MIN, each sorted by a whole block, claimed after the block's warp
+    // work; the same bookkeeping as a lane's
+    const u32 nhuge = scal[SCAL_NHUGE];
+    if (nhuge) {
+        __shared__ u32 s_claim, s_rows[256], s_red[2 * GS_WARPS];
+        for (;;) {
+            __syncthreads();   // sbuf, s_claim and s_red are free
+            if (threadIdx.x == 0) s_claim = atomicAdd(&scal[SCAL_HUGENEXT], 1u);
+            __syncthreads();
+            const u32 b = s_claim;
+            if (b >= nhuge) break;
+            const u32 g = huge_list[b];
+            const u32 base = gstart[g], size = gsize[g], h = gslot[g];
+            sort_group_block(members + base, size, tmp + base, &sbuf[0][0], s_rows, s_red);
+            if (threadIdx.x == 0) {
+                flags[members[base]] = 1u;
+                slot_cnt[h] = 0u;
+                if (size > ADMIT_BIG) big_list[atomicAdd(&scal[SCAL_NBIG], 1u)] = g;
+                if (cfg.asmd) {
+                    int kx, ky, kz;
+                    unpack_key(slots[h].key, kx, ky, kz);
+                    if (centre_dist2(kx, ky, kz, v, cfg.sx, cfg.sy, cfg.sz) <= cfg.rc2) {
+                        atomicAdd(&ctr->near_sum, (unsigned long long)size);
+                        atomicAdd(&ctr->near_cnt, 1ull);
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -610,6 +720,11 @@ struct AdmitArgs {
     int* grp_exp0;
     const u32* big_list;  // groups above ADMIT_BIG members (SCAL_NBIG of them)
     u32* big_next;        // the claim counter over big_list
+    // the map was emptied just before this insert (the scan-local map): its bucket ring is the
+    // identity with head 0, every group opens a new voxel, and the group of ordinal o takes
+    // bucket o with no atomic on the ring head (every warp's atomic on that one address
+    // serialised the header phase)
+    int fresh;
 };
 
 // a11 admission. A warp takes 32 voxel groups at a time (strided over the group range): each
@@ -645,13 +760,13 @@ __device__ __forceinline__ void admit_big_group(const AdmitArgs& a, u32 g, doubl
         const u32 cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
         u32 cap = 0;
         if (bucket == NO_BUCKET) {
-            const u32 h = atomicAdd(&a.ctr->ring_head, 1u);
+            const u32 h = a.fresh ? ord : atomicAdd(&a.ctr->ring_head, 1u);
             if (h < ring_tail) {
                 bucket = a.ring[h % a.max_buckets];
                 sp->bucket = bucket;
                 sp->count = 0;
                 if (a.cexp) a.cexp[bucket] = EXP_NONE;
-                atomicAdd(&a.ctr->n_voxels, 1u);
+                if (!a.fresh) atomicAdd(&a.ctr->n_voxels, 1u);
             } else {
                 atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
                 atomicAdd(&a.ctr->n_dropped, size);
@@ -783,6 +898,12 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
     __syncthreads();
     const double n_near = s_near;
     const u32 ring_tail = a.ctr->ring_tail;
+    if (a.fresh && blockIdx.x == 0 && threadIdx.x == 0) {
+        // every group of a fresh map opens a voxel (those beyond the pool are dropped in their headers)
+        const u32 opened = min(ng, ring_tail);
+        a.ctr->ring_head = opened;
+        a.ctr->n_voxels = opened;
+    }
     const float4 far4 = make_float4(F_INF, F_INF, F_INF, 0.f);
     const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     for (u32 j0 = 0; w + j0 * warps_total < ng; j0 += 32) {
@@ -800,10 +921,22 @@ __global__ void __launch_bounds__(TPB) k_admit(AdmitArgs a) {
             bucket = sp->bucket;
             cnt = (bucket == NO_BUCKET) ? 0u : sp->count;
         }
-        // new voxels take buckets from the ring: one atomic per warp
+        // new voxels take buckets from the ring: by ordinal on a fresh map, else one atomic per warp
         const bool need = gv && bucket == NO_BUCKET;
         const u32 need_mask = __ballot_sync(0xffffffffu, need);
-        if (need_mask) {
+        if (a.fresh) {
+            if (need) {
+                if (ord < ring_tail) {
+                    bucket = a.ring[ord];
+                    sp->bucket = bucket;
+                    sp->count = 0;
+                    if (a.cexp) a.cexp[bucket] = EXP_NONE;
+                } else {
+                    atomicOr(&a.ctr->err, (u32)ERR_BUCKETS_FULL);
+                    atomicAdd(&a.ctr->n_dropped, end - start);
+                }
+            }
+        } else if (need_mask) {
             u32 h0 = 0;
             if (lane == __ffs(need_mask) - 1) h0 = atomicAdd(&a.ctr->ring_head, (u32)__popc(need_mask));
             h0 = __shfl_sync(0xffffffffu, h0, __ffs(need_mask) - 1);
@@ -1459,8 +1592,9 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
                s.slot_cnt);
     mark(0);
     // groups by slot: contiguous ranges of s.sv_alt, each sorted by input index
+    // groups above GS_BLOCK_MIN members are listed in s.pos (free until the admission)
     FAR_LAUNCH(k_group_alloc, blocks_for(n), TPB, 0, st, s.sk, s.sv, n, sentinel, s.slot_cnt, s.slot_base, s.scal,
-               s.gstart, s.gsize, s.gslot);
+               s.gstart, s.gsize, s.gslot, s.pos);
     FAR_LAUNCH(k_group_scatter, blocks_for(n), TPB, 0, st, s.sk, s.sv, n, sentinel, s.slot_base, s.sv_alt);
     mark(1);
     {
@@ -1468,7 +1602,7 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
         const u32 warps = min(n, 152u * 24u);
         FAR_LAUNCH(k_group_sort, blocks_for(warps * 32u), TPB, 0, st, s.sv_alt, s.sk_alt, s.scal, s.rank, s.gstart,
                    s.gsize,
-                   s.gslot, s.slot_cnt, s.flags, m.slots, (double)m.v, cfg, dpose.T, m.ctr);
+                   s.gslot, s.slot_cnt, s.flags, m.slots, (double)m.v, cfg, dpose.T, m.ctr, s.pos);
     }
     // voxel ordinals in first-input-index order (k_world_keys cleared the flags)
     FAR_TRY(scan_exclusive(s.flags, s.head_ord, n, nullptr, nullptr, s.partials, st));
@@ -1503,6 +1637,9 @@ cudaError_t map_insert_batch(DeviceMap& m, Scratch& s, u32 n, const Pose12* pose
     a.grp_exp0 = s.grp_exp0;
     a.big_list = s.rank;   // listed by k_group_sort; the ranks are written after the admission
     a.big_next = s.scal + SCAL_BIGNEXT;
+    // the scan-local insert (the one that emits the sources) always runs on a map emptied just
+    // before (map_clear, or k_local_reset after the previous scan)
+    a.fresh = emit_sources ? 1 : 0;
     // groups <= n, up to 32 per warp and pass; one resident wave (4 blocks of 8 warps per SM at
     // 64 registers)
     const u32 warps = min(n, 152u * 32u);

@@ -92,8 +92,10 @@ struct Scratch {
 // SCAL_IDBASE: the map's next point id when the insert began (the first id it assigns)
 // SCAL_NBIG: groups above ADMIT_BIG members (listed by k_group_sort, admitted by whole blocks);
 // SCAL_BIGNEXT: the next of them a block of k_admit claims
+// SCAL_NHUGE: groups above GS_BLOCK_MIN members (listed by k_group_alloc, sorted by whole blocks
+// of k_group_sort); SCAL_HUGENEXT: the next of them a block claims
 enum { SCAL_NGROUPS = 0, SCAL_NADMIT = 1, SCAL_NVALID = 2, SCAL_IDBASE = 3, SCAL_NBIG = 4, SCAL_BIGNEXT = 5,
-       SCAL_COUNT = 8 };
+       SCAL_NHUGE = 6, SCAL_HUGENEXT = 7, SCAL_COUNT = 8 };
 
 struct InsertCfg {
     int asmd = 0;
