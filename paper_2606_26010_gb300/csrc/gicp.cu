@@ -76,46 +76,6 @@ __device__ __forceinline__ bool chol6_solve(const double (&H)[6][6], const doubl
     return true;
 }
 
-// SE(3) exponential, xi = [phi; rho]: R = I + A K + B K^2, V = I + B K + C K^2 with
-// A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3. Below t = 0.1 the three are
-// evaluated from their Taylor series in t^2 (terms through t^10; the first omitted term is
-// below 1e-21), which needs neither sqrt nor sincos; above, from sincos.
-__device__ __forceinline__ void se3_exp_dev(const double (&xi)[6], double (&E)[12]) {
-    const double px = xi[0], py = xi[1], pz = xi[2];
-    const double t2 = px * px + py * py + pz * pz;
-    double A, B, C;
-    if (t2 < 1e-2) {
-        A = 1.0 - t2 * (1.0 / 6.0) * (1.0 - t2 * (1.0 / 20.0) * (1.0 - t2 * (1.0 / 42.0) *
-                                                                     (1.0 - t2 * (1.0 / 72.0) * (1.0 - t2 * (1.0 / 110.0)))));
-        B = 0.5 * (1.0 - t2 * (1.0 / 12.0) * (1.0 - t2 * (1.0 / 30.0) * (1.0 - t2 * (1.0 / 56.0) *
-                                                                         (1.0 - t2 * (1.0 / 90.0) * (1.0 - t2 * (1.0 / 132.0))))));
-        C = (1.0 / 6.0) * (1.0 - t2 * (1.0 / 20.0) * (1.0 - t2 * (1.0 / 42.0) * (1.0 - t2 * (1.0 / 72.0) *
-                                                                                 (1.0 - t2 * (1.0 / 110.0) * (1.0 - t2 * (1.0 / 156.0))))));
-    } else {
-        const double th = sqrt(t2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        A = sn / th;
-        B = (1.0 - cs) / t2;
-        C = (th - sn) / (t2 * th);
-    }
-    // K^2 = phi phi^T - t2 I
-    const double K[3][3] = {{0.0, -pz, py}, {pz, 0.0, -px}, {-py, px, 0.0}};
-    const double ph[3] = {px, py, pz};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        double t = 0.0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const double k2 = ph[i] * ph[j] - ((i == j) ? t2 : 0.0);
-            const double id = (i == j) ? 1.0 : 0.0;
-            E[4 * i + j] = id + A * K[i][j] + B * k2;
-            t += (id + B * K[i][j] + C * k2) * xi[3 + j];
-        }
-        E[4 * i + 3] = t;
-    }
-}
-
 __device__ __forceinline__ u32 warp_sum_u(u32 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -446,77 +406,181 @@ __global__ void __launch_bounds__(GN_THREADS, FAR_GN_MIN_BLOCKS) k_gn_lin_batch(
     gn_lin_block<TPP, PREC>(p.args, blockIdx.x - p.block_begin, p.nblocks);
 }
 
-// The single solving thread: H and g from the reduced values, Cholesky, SE(3) update (Eq. 6),
-// convergence and time checks, bookkeeping. T: the pose at the start of the launch.
-__device__ __forceinline__ void gn_solve_serial(const GnArgs& a, const double* tot, const double (&T)[12]) {
+// Upper-triangle index of H[r][c] (r <= c) in the reduced values: row-major, 21 entries.
+__device__ __forceinline__ int tri_upper(int r, int c) { return r * 6 - (r * (r - 1)) / 2 + (c - r); }
+
+// The solving warp: H and g from the reduced values, FP64 Cholesky, SE(3) update (Eq. 6),
+// convergence and time checks, bookkeeping. The FP64 work is spread over the lanes (on this
+// GPU an FP64 instruction costs the warp the same whether one lane or all take part): lane
+// l < 21 holds the lower-triangle entry (i, j) with l = i (i + 1) / 2 + j and the Cholesky is
+// right-looking (each column scaled by its r_k = 1 / sqrt(pivot), then the trailing entries
+// updated, one fma per entry and column, in the same order as a row-by-row factorisation);
+// the substitutions run on lanes 0-5, the exponential's 12 entries and the pose update on
+// lanes 0-11. Every lane of the warp must call this.
+__device__ __forceinline__ void gn_solve_warp(const GnArgs& a, const double* tot, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
     RegState* st = a.st;
-    double H[6][6], g[6];
+    const u32 n_corr_tot = (u32)tot[28];
+    // lane -> (i, j), i >= j, for the 21 entries of the lower triangle
+    int li = 0, lj = lane;
+    while (li < 6 && lj > li) {
+        lj -= li + 1;
+        ++li;
+    }
+    const bool tri = lane < 21;
+    if (!tri) li = lj = 0;
+    if (a.update) {
+        const double Tl = lane < 12 ? st->T[lane] : 0.0;     // the pose (loaded while the solve runs)
+        double e = tri ? tot[tri_upper(lj, li)] : 0.0;      // H[i][j], becomes L[i][j]
+        double bv = lane < 6 ? -tot[21 + lane] : 0.0;        // -g, becomes y, then xi
+        bool ok = n_corr_tot >= 6;
+        double rk[6];
 #pragma unroll
-    for (int r = 0, idx = 0; r < 6; ++r)
+        for (int k = 0; k < 6; ++k) {
+            const double d = __shfl_sync(FULL, e, k * (k + 1) / 2 + k);   // the pivot after k updates
+            if (!(d > 0.0)) ok = false;
+            const double r = ok ? rsqrt(d) : 0.0;
+            rk[k] = r;
+            if (tri && lj == k) e = (li == k) ? d * r : e * r;
+            const double lik = __shfl_sync(FULL, e, li >= k ? li * (li + 1) / 2 + k : 0);
+            const double ljk = __shfl_sync(FULL, e, lj >= k ? lj * (lj + 1) / 2 + k : 0);
+            if (tri && lj > k) e = fma(-lik, ljk, e);
+        }
+        // L y = -g, then L^T xi = y
 #pragma unroll
-        for (int c = r; c < 6; ++c, ++idx) {
-            H[r][c] = tot[idx];
-            H[c][r] = tot[idx];
+        for (int k = 0; k < 6; ++k) {
+            const double yk = __shfl_sync(FULL, bv, k) * rk[k];
+            const double lik = __shfl_sync(FULL, e, (lane > k && lane < 6) ? lane * (lane + 1) / 2 + k : 0);
+            if (lane == k) bv = yk;
+            else if (lane > k && lane < 6) bv = fma(-lik, yk, bv);
         }
 #pragma unroll
-    for (int r = 0; r < 6; ++r) g[r] = tot[21 + r];
-    const u32 n_corr_tot = (u32)tot[28];
-    if (a.update) {
-        bool ok = n_corr_tot >= 6;
-        double mg[6], xi[6];
+        for (int k = 5; k >= 0; --k) {
+            const double xk = __shfl_sync(FULL, bv, k) * rk[k];
+            const double lki = __shfl_sync(FULL, e, lane < k ? k * (k + 1) / 2 + lane : 0);
+            if (lane == k) bv = xk;
+            else if (lane < k) bv = fma(-lki, xk, bv);
+        }
+        double xi[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) mg[j] = -g[j];
-        if (ok) ok = chol6_solve(H, mg, xi);
+        for (int j = 0; j < 6; ++j) xi[j] = __shfl_sync(FULL, bv, j);
         if (ok) {
+            // SE(3) exponential, xi = [phi; rho]: R = I + A K + B K^2, V = I + B K + C K^2 with
+            // A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3. Below t = 0.1 the three
+            // are evaluated from their Taylor series in t^2 (terms through t^10; the first omitted
+            // term is below 1e-21), which needs neither sqrt nor sincos; above, from sincos.
+            const double px = xi[0], py = xi[1], pz = xi[2];
+            const double t2 = px * px + py * py + pz * pz;
+            double A, B, C;
+            if (t2 < 1e-2) {
+                // the three series are one nested form s0 (1 - t2 d1 (1 - t2 d2 (... (1 - t2 d5)))),
+                // lane 0 evaluating A, lane 1 B and lane 2 C (one FP64 sequence for all three)
+                const int f = lane < 3 ? lane : 0;
+                const double s0 = f == 0 ? 1.0 : (f == 1 ? 0.5 : 1.0 / 6.0);
+                const double d1 = f == 0 ? 1.0 / 6.0 : (f == 1 ? 1.0 / 12.0 : 1.0 / 20.0);
+                const double d2 = f == 0 ? 1.0 / 20.0 : (f == 1 ? 1.0 / 30.0 : 1.0 / 42.0);
+                const double d3 = f == 0 ? 1.0 / 42.0 : (f == 1 ? 1.0 / 56.0 : 1.0 / 72.0);
+                const double d4 = f == 0 ? 1.0 / 72.0 : (f == 1 ? 1.0 / 90.0 : 1.0 / 110.0);
+                const double d5 = f == 0 ? 1.0 / 110.0 : (f == 1 ? 1.0 / 132.0 : 1.0 / 156.0);
+                const double v = s0 * (1.0 - t2 * d1 * (1.0 - t2 * d2 * (1.0 - t2 * d3 * (1.0 - t2 * d4 *
+                                                                                     (1.0 - t2 * d5)))));
+                A = __shfl_sync(FULL, v, 0);
+                B = __shfl_sync(FULL, v, 1);
+                C = __shfl_sync(FULL, v, 2);
+            } else {
+                const double th = sqrt(t2);
+                double sn, cs;
+                sincos(th, &sn, &cs);
+                A = sn / th;
+                B = (1.0 - cs) / t2;
+                C = (th - sn) / (t2 * th);
+            }
+            // entry (row, col) of [R | V rho] on lane 4 row + col, lanes 0-11; K^2 = phi phi^T - t2 I
+            const int row = (lane >> 2) % 3, col = lane & 3;
+            const double phr = row == 0 ? px : (row == 1 ? py : pz);
+            auto kmat = [&](int i, int j) {   // K = [phi]x
+                if (i == j) return 0.0;
+                const int o = 3 - i - j;       // the third axis
+                const double ph = o == 0 ? px : (o == 1 ? py : pz);
+                return ((j - i + 3) % 3 == 1) ? -ph : ph;
+            };
+            // R and V entry (row, c) on lanes with col = c < 3; the translation V rho of a row on its
+            // lane with col = 3, summed over the row's V entries in column order
+            const int cc = col < 3 ? col : 0;
+            const double phc = cc == 0 ? px : (cc == 1 ? py : pz);
+            const double k2 = phr * phc - ((row == cc) ? t2 : 0.0);
+            const double id = (row == cc) ? 1.0 : 0.0;
+            const double kk = kmat(row, cc);
+            const double Rv = id + A * kk + B * k2;
+            const double Vv = id + B * kk + C * k2;
+            const double v0 = __shfl_sync(FULL, Vv, 4 * row), v1 = __shfl_sync(FULL, Vv, 4 * row + 1);
+            const double v2 = __shfl_sync(FULL, Vv, 4 * row + 2);
+            double Ev = Rv;
+            if (col == 3) {
+                double t = 0.0;
+                t += v0 * xi[3];
+                t += v1 * xi[4];
+                t += v2 * xi[5];
+                Ev = t;
+            }
             // Eq. 6: T <- exp(xi) T about the anchor A (t - A is updated, then A is added back),
             // written before the bookkeeping (the next launch waits on it)
-            double E[12];
-            se3_exp_dev(xi, E);
-            const double tr[3] = {T[3] - a.anchor[0], T[7] - a.anchor[1], T[11] - a.anchor[2]};
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    st->T[4 * r + c] = E[4 * r + 0] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c];
-                st->T[4 * r + 3] =
-                    (E[4 * r + 0] * tr[0] + E[4 * r + 1] * tr[1] + E[4 * r + 2] * tr[2] + E[4 * r + 3]) + a.anchor[r];
+            const double e0 = __shfl_sync(FULL, Ev, 4 * row), e1 = __shfl_sync(FULL, Ev, 4 * row + 1);
+            const double e2 = __shfl_sync(FULL, Ev, 4 * row + 2), e3 = __shfl_sync(FULL, Ev, 4 * row + 3);
+            const double ta = __shfl_sync(FULL, Tl, col), tb = __shfl_sync(FULL, Tl, 4 + col);
+            const double tc = __shfl_sync(FULL, Tl, 8 + col);
+            if (lane < 12) {
+                if (col < 3) {
+                    st->T[lane] = e0 * ta + e1 * tb + e2 * tc;
+                } else {
+                    const double tr0 = ta - a.anchor[0], tr1 = tb - a.anchor[1], tr2 = tc - a.anchor[2];
+                    const double ar = row == 0 ? a.anchor[0] : (row == 1 ? a.anchor[1] : a.anchor[2]);
+                    st->T[lane] = (e0 * tr0 + e1 * tr1 + e2 * tr2 + e3) + ar;
+                }
             }
-            // termination: the increment expressed at the initial sensor position c (relative to
-            // the anchor), [phi; rho + phi x c], so the test does not depend on where the world
-            // origin lies
-            const double* c = a.conv_center;
-            const double r0 = xi[3] + (xi[1] * c[2] - xi[2] * c[1]);
-            const double r1 = xi[4] + (xi[2] * c[0] - xi[0] * c[2]);
-            const double r2 = xi[5] + (xi[0] * c[1] - xi[1] * c[0]);
-            const double nx = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] + r0 * r0 + r1 * r1 + r2 * r2;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) st->xi[j] = xi[j];
-            st->xi_norm2 = nx;
-            st->iters += 1;
-            if (nx <= a.conv_eps * a.conv_eps) {
-                st->converged = 1;
-                st->done = 1;
+            if (lane < 6) st->xi[lane] = bv;   // lane j holds xi[j]
+            if (lane == 0) {
+                // termination: the increment expressed at the initial sensor position c (relative to
+                // the anchor), [phi; rho + phi x c], so the test does not depend on where the world
+                // origin lies
+                const double* c = a.conv_center;
+                const double r0 = xi[3] + (xi[1] * c[2] - xi[2] * c[1]);
+                const double r1 = xi[4] + (xi[2] * c[0] - xi[0] * c[2]);
+                const double r2 = xi[5] + (xi[0] * c[1] - xi[1] * c[0]);
+                const double nx = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] + r0 * r0 + r1 * r1 + r2 * r2;
+                st->xi_norm2 = nx;
+                st->iters += 1;
+                if (nx <= a.conv_eps * a.conv_eps) {
+                    st->converged = 1;
+                    st->done = 1;
+                }
+                if (a.budget_ns > 0 && globaltimer_ns() - st->t_start_ns > a.budget_ns) {
+                    st->status = 6;
+                    st->done = 1;
+                }
             }
-            if (a.budget_ns > 0 && globaltimer_ns() - st->t_start_ns > a.budget_ns) {
-                st->status = 6;
-                st->done = 1;
-            }
-        } else {
+        } else if (lane == 0) {
             st->status = 5;
             st->done = 1;
         }
-    } else {
+    } else if (lane == 0) {
         st->done = 1;
     }
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) st->H[6 * r + c] = H[r][c];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) st->g[j] = g[j];
-    st->chi2 = tot[27];
-    st->n_corr = n_corr_tot;
-    st->n_p2p = (u32)tot[29];
+    // the linearisation's H (full), g, chi2 and counts
+    {
+        const int r = lane / 6, c = lane % 6;
+        st->H[lane] = tot[r <= c ? tri_upper(r, c) : tri_upper(c, r)];
+        if (lane < 4) {
+            const int r2 = (32 + lane) / 6, c2 = (32 + lane) % 6;
+            st->H[32 + lane] = tot[r2 <= c2 ? tri_upper(r2, c2) : tri_upper(c2, r2)];
+        }
+        if (lane < 6) st->g[lane] = tot[21 + lane];
+        if (lane == 0) {
+            st->chi2 = tot[27];
+            st->n_corr = n_corr_tot;
+            st->n_p2p = (u32)tot[29];
+        }
+    }
 }
 
 // Solve half of a Gauss-Newton iteration. Value v of the block partials (col = partials +
@@ -564,12 +628,7 @@ __device__ __forceinline__ bool gn_solve_wide(const GnArgs& a, u32 nblocks) {
     __threadfence();
     tot[lane] = __ldcg(&st->red[lane]);
     __syncwarp();
-    if (lane == 0 && *reinterpret_cast<volatile u32*>(&st->done) == 0u) {
-        double T[12];
-#pragma unroll
-        for (int j = 0; j < 12; ++j) T[j] = st->T[j];
-        gn_solve_serial(a, tot, T);
-    }
+    if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile u32*>(&st->done), 0) == 0u) gn_solve_warp(a, tot, lane);
     return true;
 }
 
