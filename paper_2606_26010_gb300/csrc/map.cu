@@ -1133,10 +1133,10 @@ __global__ void __launch_bounds__(TPB, K <= 6 ? 3 : 2) k_knn_cov(MapView m, cons
         const float4 p = active ? (q ? q[r] : m.pts[qpos[r]]) : make_float4(0.f, 0.f, 0.f, 0.f);
         QFrame<false> f;
         const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
-        float bd[K];
-        u32 bid[K], bpos[K];
+        unsigned long long bk[K];
+        u32 bpos[K];
         const int found =
-            group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid, bpos);
+            group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bk, bpos);
         if (!active || sl != 0) continue;
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (found >= K) covariance_from_neighbours<K>(m.pts, bpos, p.x, p.y, p.z, c0, c1);
@@ -1146,7 +1146,7 @@ __global__ void __launch_bounds__(TPB, K <= 6 ? 3 : 2) k_knn_cov(MapView m, cons
         if (knn_ids) {
             const size_t row = __float_as_uint(p.w);
 #pragma unroll
-            for (int j = 0; j < K; ++j) knn_ids[row * K + j] = (j < found) ? bid[j] : NO_ID;
+            for (int j = 0; j < K; ++j) knn_ids[row * K + j] = (j < found) ? (u32)bk[j] : NO_ID;
         }
     }
 }
@@ -1176,10 +1176,10 @@ __global__ void __launch_bounds__(TPB, K <= 6 ? 3 : 2) k_knn_cov_tile(MapView m,
         if (active) unpack_key(qkey[r], kx, ky, kz);
         QFrame<true> f;
         own_qframe(m, p.x, p.y, p.z, kx, ky, kz, f);
-        float bd[K];
-        u32 bid[K], bpos[K];
+        unsigned long long bk[K];
+        u32 bpos[K];
         const int found =
-            group_knn<K, KNN_TPP, true>(m, max_probe, f, active, sl, vlist[threadIdx.x / KNN_TPP], bd, bid, bpos);
+            group_knn<K, KNN_TPP, true>(m, max_probe, f, active, sl, vlist[threadIdx.x / KNN_TPP], bk, bpos);
         if (!active || sl != 0) continue;
         float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool valid = false;
@@ -1440,24 +1440,24 @@ __global__ void __launch_bounds__(TPB) k_knn_stage(MapView m, const float4* __re
         const u32 r = base + (threadIdx.x & 31u) / KNN_TPP;
         const bool active = r < n;
         const float4 p = active ? q[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float bd[K];
-        u32 bid[K], bpos[K];
+        unsigned long long bk[K];
+        u32 bpos[K];
         int found;
         if (m.tv > 0) {
             QFrame<true> f;
             const bool keyed = active && world_query_frame(m, p.x, p.y, p.z, f);
-            found = group_knn<K, KNN_TPP, true>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid,
+            found = group_knn<K, KNN_TPP, true>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bk,
                                                 bpos);
         } else {
             QFrame<false> f;
             const bool keyed = active && make_qframe<false>(m, p.x, p.y, p.z, zero, f);
-            found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bd, bid,
+            found = group_knn<K, KNN_TPP, false>(m, max_probe, f, keyed, sl, vlist[threadIdx.x / KNN_TPP], bk,
                                                  bpos);
         }
         if (!active || sl != 0) continue;
         found_out[r] = found;
 #pragma unroll
-        for (int j = 0; j < K; ++j) ids[(size_t)r * K + j] = (j < found) ? bid[j] : NO_ID;
+        for (int j = 0; j < K; ++j) ids[(size_t)r * K + j] = (j < found) ? (u32)bk[j] : NO_ID;
     }
 }
 

@@ -119,10 +119,17 @@ __device__ __forceinline__ void own_qframe(const MapView& m, float qx, float qy,
     }
 }
 
+// A k-NN list entry: the packed key (d2 bits << 32 | id), whose integer order is the (d2, id)
+// order for d2 >= 0, and the candidate's position in the map's point array. An empty entry
+// holds KNN_EMPTY (+inf, no id), which every candidate precedes.
+constexpr unsigned long long KNN_EMPTY = (0x7F800000ull << 32) | 0xFFFFFFFFull;
+
+__device__ __forceinline__ float knn_d2(unsigned long long key) { return __uint_as_float((u32)(key >> 32)); }
+
 // Merge the points of voxel (nx, ny, nz) into the sorted K best of q.
 template <int K, bool PREC = false>
 __device__ __forceinline__ void knn_scan_voxel(const MapView& m, u32 max_probe, int nx, int ny, int nz, float qx,
-                                               float qy, float qz, int& found, float (&bd)[K], u32 (&bid)[K],
+                                               float qy, float qz, int& found, unsigned long long (&bk)[K],
                                                u32 (&bpos)[K], float ox = 0.f, float oy = 0.f, float oz = 0.f) {
     u32 bucket, count;
     if (!find_slot(m.slots, m.mask, max_probe, nx, ny, nz, bucket, count)) return;
@@ -144,21 +151,18 @@ __device__ __forceinline__ void knn_scan_voxel(const MapView& m, u32 max_probe, 
         for (int u = 0; u < 4; ++u) {
             if (j0 + u >= count) continue;
             const float d2 = dist2_rn(qx, qy, qz, c[u].x, c[u].y, c[u].z);
-            const u32 id = __float_as_uint(c[u].w);
-            if (!better(d2, id, bd[K - 1], bid[K - 1])) continue;
+            unsigned long long ck = ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c[u].w);
+            if (!(ck < bk[K - 1])) continue;
             // sorted insert: the candidate bubbles up past every worse entry
-            float cd = d2;
-            u32 ci = id, cp = base + j0 + u;
+            u32 cp = base + j0 + u;
 #pragma unroll
-            for (int s = 0; s < K; ++s) {
-                const bool sw = better(cd, ci, bd[s], bid[s]);
-                const float td = bd[s];
-                const u32 ti = bid[s], tp = bpos[s];
-                bd[s] = sw ? cd : td;
-                bid[s] = sw ? ci : ti;
-                bpos[s] = sw ? cp : tp;
-                cd = sw ? td : cd;
-                ci = sw ? ti : ci;
+            for (int s2 = 0; s2 < K; ++s2) {
+                const bool sw = ck < bk[s2];
+                const unsigned long long tk = bk[s2];
+                const u32 tp = bpos[s2];
+                bk[s2] = sw ? ck : tk;
+                bpos[s2] = sw ? cp : tp;
+                ck = sw ? tk : ck;
                 cp = sw ? tp : cp;
             }
         }
@@ -207,63 +211,26 @@ __device__ __forceinline__ float nn_bound(unsigned long long best_key, float lim
     return fminf(b, limit2);
 }
 
-// K nearest of the query (K is the exact k: a run-time k would push the arrays to local
-// memory); arrays sorted ascending by (d2, id). Returns the number found (<= K).
-template <int K, bool PREC>
-__device__ __forceinline__ int knn27q(const MapView& m, u32 max_probe, const QFrame<PREC>& f, float (&bd)[K],
-                                      u32 (&bid)[K], u32 (&bpos)[K]) {
-    const float qx = f.q[0], qy = f.q[1], qz = f.q[2];
-    const int kx = f.k[0], ky = f.k[1], kz = f.k[2];
-    int found = 0;
-    const FaceDist fd = face_distances(qx, qy, qz, f.lk[0], f.lk[1], f.lk[2], m.v);
-    // own voxel first, then only the neighbours on the sides within reach of the k-th distance
-    knn_scan_voxel<K, PREC>(m, max_probe, kx, ky, kz, qx, qy, qz, found, bd, bid, bpos, f.off(0, 0), f.off(1, 0),
-                            f.off(2, 0));
-    const float b0 = (found >= K) ? bd[K - 1] : F_INF;
-    bool reach[3][2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        reach[a][0] = fd.lo[a] * fd.lo[a] <= b0;
-        reach[a][1] = fd.hi[a] * fd.hi[a] <= b0;
-    }
-    for (int dx = -1; dx <= 1; ++dx) {
-        if ((dx < 0 && !reach[0][0]) || (dx > 0 && !reach[0][1]) || !key_in_range(kx + dx)) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            if ((dy < 0 && !reach[1][0]) || (dy > 0 && !reach[1][1]) || !key_in_range(ky + dy)) continue;
-            for (int dz = -1; dz <= 1; ++dz) {
-                if ((dz < 0 && !reach[2][0]) || (dz > 0 && !reach[2][1]) || !key_in_range(kz + dz)) continue;
-                if (dx == 0 && dy == 0 && dz == 0) continue;
-                if (found >= K && box_lb2(fd, dx, dy, dz) > bd[K - 1]) continue;
-                knn_scan_voxel<K, PREC>(m, max_probe, kx + dx, ky + dy, kz + dz, qx, qy, qz, found, bd, bid, bpos,
-                                        f.off(0, dx), f.off(1, dy), f.off(2, dz));
-            }
-        }
-    }
-    return found < K ? found : K;
-}
-
 template <int K>
-__device__ __forceinline__ void knn_init(float (&bd)[K], u32 (&bid)[K], u32 (&bpos)[K]) {
+__device__ __forceinline__ void knn_init(unsigned long long (&bk)[K], u32 (&bpos)[K]) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        bd[j] = F_INF;
-        bid[j] = NO_ID;
+        bk[j] = KNN_EMPTY;
         bpos[j] = 0;
     }
 }
 
-// The K best of two sorted lists (ascending (d2, id), disjoint candidates) into the first: the
-// K smallest of the union are min(a_i, b_{K-1-i}) (a bitonic sequence), which an odd-even
+// The K best of two sorted lists (ascending keys, disjoint candidates) into the second: the K
+// smallest of the union are min(a_i, b_{K-1-i}) (a bitonic sequence), which an odd-even
 // transposition sort puts back in order. Registers only.
 template <int K>
-__device__ __forceinline__ void knn_merge(const float (&od)[K], const u32 (&oi)[K], const u32 (&op)[K], float (&bd)[K],
-                                          u32 (&bid)[K], u32 (&bpos)[K]) {
+__device__ __forceinline__ void knn_merge(const unsigned long long (&ok)[K], const u32 (&op)[K],
+                                          unsigned long long (&bk)[K], u32 (&bpos)[K]) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const int j = K - 1 - i;
-        if (better(od[j], oi[j], bd[i], bid[i])) {
-            bd[i] = od[j];
-            bid[i] = oi[j];
+        if (ok[j] < bk[i]) {
+            bk[i] = ok[j];
             bpos[i] = op[j];
         }
     }
@@ -271,13 +238,11 @@ __device__ __forceinline__ void knn_merge(const float (&od)[K], const u32 (&oi)[
     for (int pass = 0; pass < K; ++pass)
 #pragma unroll
         for (int i = pass & 1; i + 1 < K; i += 2) {
-            const bool sw = better(bd[i + 1], bid[i + 1], bd[i], bid[i]);
-            const float d0 = bd[i], d1 = bd[i + 1];
-            const u32 i0 = bid[i], i1 = bid[i + 1], p0 = bpos[i], p1 = bpos[i + 1];
-            bd[i] = sw ? d1 : d0;
-            bd[i + 1] = sw ? d0 : d1;
-            bid[i] = sw ? i1 : i0;
-            bid[i + 1] = sw ? i0 : i1;
+            const bool sw = bk[i + 1] < bk[i];
+            const unsigned long long k0 = bk[i], k1 = bk[i + 1];
+            const u32 p0 = bpos[i], p1 = bpos[i + 1];
+            bk[i] = sw ? k1 : k0;
+            bk[i + 1] = sw ? k0 : k1;
             bpos[i] = sw ? p1 : p0;
             bpos[i + 1] = sw ? p0 : p1;
         }
@@ -287,10 +252,10 @@ __device__ __forceinline__ void knn_merge(const float (&od)[K], const u32 (&oi)[
 // lane of the group ends with it): a butterfly over the lanes keeps the K smallest of each pair,
 // min(a_i, b_{K-1-i}), sorted again by an odd-even transposition sort.
 template <int K, int TPP>
-__device__ __forceinline__ float group_union_kth(const float (&bd)[K]) {
+__device__ __forceinline__ float group_union_kth(const unsigned long long (&bk)[K]) {
     float c[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) c[i] = bd[i];
+    for (int i = 0; i < K; ++i) c[i] = knn_d2(bk[i]);
 #pragma unroll
     for (int o = 1; o < TPP; o <<= 1) {
         float p[K];
@@ -322,20 +287,20 @@ __device__ __forceinline__ float group_union_kth(const float (&bd)[K]) {
 // saw, capped at K. Every lane of the warp must call this.
 template <int K, int TPP, bool PREC>
 __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const QFrame<PREC>& f, bool keyed,
-                                         int sl, unsigned char* list, float (&bd)[K], u32 (&bid)[K],
+                                         int sl, unsigned char* list, unsigned long long (&bk)[K],
                                          u32 (&bpos)[K]) {
-    knn_init<K>(bd, bid, bpos);
+    knn_init<K>(bk, bpos);
     int found = 0;
     const FaceDist fd = face_distances(f.q[0], f.q[1], f.q[2], f.lk[0], f.lk[1], f.lk[2], m.v);
     auto scan = [&](int v) {
         const int dx = c_nb_order[v][0], dy = c_nb_order[v][1], dz = c_nb_order[v][2];
         const int nx = f.k[0] + dx, ny = f.k[1] + dy, nz = f.k[2] + dz;
         if (key_in_range(nx) && key_in_range(ny) && key_in_range(nz))
-            knn_scan_voxel<K, PREC>(m, max_probe, nx, ny, nz, f.q[0], f.q[1], f.q[2], found, bd, bid, bpos,
+            knn_scan_voxel<K, PREC>(m, max_probe, nx, ny, nz, f.q[0], f.q[1], f.q[2], found, bk, bpos,
                                     f.off(0, dx), f.off(1, dy), f.off(2, dz));
     };
     auto group_bound = [&]() {
-        float kth = bd[K - 1];
+        float kth = knn_d2(bk[K - 1]);
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) kth = fminf(kth, __shfl_xor_sync(0xffffffffu, kth, o));
         return kth;
@@ -343,7 +308,7 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
     if (keyed && sl < 27) scan(sl);
     // the K best of the union are at least as close as the union's K-th distance, which is finite
     // once the first round's voxels hold K points together (sparse regions)
-    float bound = group_union_kth<K, TPP>(bd);
+    float bound = group_union_kth<K, TPP>(bk);
     // survivors of the remaining voxels under the group's bound, compacted in voxel order
     u32 mine = 0;
     int k = 0;
@@ -375,15 +340,14 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
 #pragma unroll
     for (int o = TPP / 2; o > 0; o >>= 1) {
         found += __shfl_xor_sync(0xffffffffu, found, o);
-        float od[K];
-        u32 oi[K], op[K];
+        unsigned long long ok[K];
+        u32 op[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            od[j] = __shfl_xor_sync(0xffffffffu, bd[j], o);
-            oi[j] = __shfl_xor_sync(0xffffffffu, bid[j], o);
+            ok[j] = __shfl_xor_sync(0xffffffffu, bk[j], o);
             op[j] = __shfl_xor_sync(0xffffffffu, bpos[j], o);
         }
-        knn_merge<K>(od, oi, op, bd, bid, bpos);
+        knn_merge<K>(ok, op, bk, bpos);
     }
     return found < K ? found : K;
 }
