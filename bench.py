@@ -408,11 +408,17 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
             else:
                 ev0.record(stream)
             mo = prior.motion(t) if skew else None
-            if e2e and t + 1 < n_seq:
-                m.prefetch(dev[t + 1])     # the next scan's copy overlaps this scan's kernels
-            pose, _, res = m.process_scan(dev[t], init, max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau,
-                                          kappa=kappa, asmd=True, r_near=R_NEAR, r_max=R_MAX, evict_radius=EVICT_R,
-                                          motion=mo)
+            step_kw = dict(max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau, kappa=kappa, asmd=True, r_near=R_NEAR,
+                           r_max=R_MAX, evict_radius=EVICT_R, motion=mo)
+            if e2e:
+                # the step is enqueued, the next scan's copy is started while it runs, then the step
+                # is collected (far_process_scan_async / far_prefetch_points / far_process_scan_wait)
+                m.process_scan_async(dev[t], init, **step_kw)
+                if t + 1 < n_seq:
+                    m.prefetch(dev[t + 1])
+                pose, _, res = m.process_scan_wait()
+            else:
+                pose, _, res = m.process_scan(dev[t], init, **step_kw)
             thr.update(init, pose)
             if e2e:
                 ms = 1e3 * (time.perf_counter() - w0)
@@ -588,8 +594,8 @@ def run_ours(args):
         d2h = 128 + 704 + 96
         e2e = {"value": round(pts_all / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": round(h2d),
                "d2h_bytes_per_step": d2h, "ms_per_step": round(1e3 * e2e_s / args.steps, 4),
-               "api": "far_process_scan_motion with pinned host points, the next scan's copy started by "
-                      "far_prefetch_points before each call"}
+               "api": "far_process_scan_async with pinned host points, the next scan's copy started by "
+                      "far_prefetch_points while the step runs, then far_process_scan_wait"}
 
     # ---- the other priors, as labelled secondary lines
     secondary = []

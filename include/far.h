@@ -286,6 +286,22 @@ far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, u
                                    const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
                                    const far_insert_params* ins, double evict_radius, double out_pose[16],
                                    double out_cov[36], far_step_result* result);
+/*
+ * far_process_scan_motion in two halves, so that the caller's host work that does not depend on
+ * this scan's result (e.g. far_prefetch_points of the next scan) overlaps the device work.
+ * far_process_scan_async checks its arguments and enqueues the whole step on the map's stream
+ * (the pose covariance too when want_cov is non-zero), then returns without waiting;
+ * far_process_scan_wait waits for it and fills the outputs exactly as far_process_scan_motion
+ * does (which is async followed by wait). One step may be pending per map: a second async call
+ * before the wait, or a wait without a pending step, is FAR_ERR_INVALID (a wait whose outputs
+ * are invalid leaves the step pending). Between the two calls the map must not be used
+ * otherwise, and host points that were not prefetched must stay valid and unchanged (their copy
+ * may still be in flight). The wait returns the step's status as far_process_scan_motion would.
+ */
+far_status far_process_scan_async(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                                  const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
+                                  const far_insert_params* ins, double evict_radius, int32_t want_cov);
+far_status far_process_scan_wait(far_map* map, double out_pose[16], double out_cov[36], far_step_result* result);
 
 /*
  * Batched registration: many independent problems (each scan against its own map) run

@@ -104,6 +104,8 @@ struct far_map {
     bool ins_used[2] = {false, false};
     far_insert_times ins_last[2] = {};
     bool local_dirty = false;        // the scan-local map may hold a scan (see build_sources)
+    bool step_pending = false;       // far_process_scan_async launched a step that no wait has collected
+    bool step_want_cov = false;      // ... and computed the pose covariance
     // prefetch of the next host scan (far_prefetch_points): two staging buffers filled on a copy
     // stream; a buffer is reused only after the map's stream has packed what it held
     cudaStream_t copy_stream = nullptr;
@@ -1031,14 +1033,14 @@ far_status far_process_scan(far_map* map, const float* xyz, uint64_t n, uint32_t
                                    out_cov, result);
 }
 
-far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
-                                   const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
-                                   const far_insert_params* ins, double evict_radius, double out_pose[16],
-                                   double out_cov[36], far_step_result* result) {
+far_status far_process_scan_async(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                                  const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
+                                  const far_insert_params* ins, double evict_radius, int32_t want_cov) {
     far_status st = check_points(map, xyz, n, stride_bytes);
     if (st != FAR_OK) return st;
-    if (!reg || !init_pose || !finite_pose(init_pose) || !out_pose)
-        return fail(FAR_ERR_INVALID, "reg params, init_pose or out_pose invalid");
+    if (map->step_pending) return fail(FAR_ERR_INVALID, "a step is pending: call far_process_scan_wait first");
+    if (!reg || !init_pose || !finite_pose(init_pose))
+        return fail(FAR_ERR_INVALID, "reg params or init_pose invalid");
     if (!(reg->kappa > 0.0f) || !(reg->tau >= 0.0f) || reg->max_iters > 1000)
         return fail(FAR_ERR_INVALID, "kappa must be > 0, tau >= 0, max_iters <= 1000");
     if (!(evict_radius >= 0.0) || std::isnan(evict_radius)) return fail(FAR_ERR_INVALID, "evict_radius must be >= 0");
@@ -1064,7 +1066,7 @@ far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, u
     GnArgs a = gn_args(map, init_pose, std::max(nn, 1u), reg->tau, reg->kappa, reg->conv_eps, 1, nullptr,
                        reg->time_budget_s, (int)reg->threads_per_point);
     if ((st = run_gn(map, a, std::max(nn, 1u), reg->max_iters)) != FAR_OK) return st;
-    if (out_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
+    if (want_cov) CK(gn_covariance(map->s.st, map->d_cov36, map->stream));
     mark(map, EV_INSERT);
     // Sec. III-A.3 submap update at the registered pose, read from the device (skipped unless status == 0)
     DevicePose dp;
@@ -1079,7 +1081,18 @@ far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, u
     mark(map, EV_END);
     CK(cudaMemcpyAsync(map->h_st, map->s.st, sizeof(RegState), cudaMemcpyDeviceToHost, map->stream));
     CK(cudaMemcpyAsync(map->h_ctr, map->map.ctr, sizeof(MapCounters), cudaMemcpyDeviceToHost, map->stream));
-    if (out_cov) CK(cudaMemcpyAsync(map->h_cov36, map->d_cov36, 36 * sizeof(double), cudaMemcpyDeviceToHost, map->stream));
+    if (want_cov) CK(cudaMemcpyAsync(map->h_cov36, map->d_cov36, 36 * sizeof(double), cudaMemcpyDeviceToHost, map->stream));
+    map->step_pending = true;
+    map->step_want_cov = want_cov != 0;
+    return FAR_OK;
+}
+
+far_status far_process_scan_wait(far_map* map, double out_pose[16], double out_cov[36], far_step_result* result) {
+    if (!map) return fail(FAR_ERR_INVALID, "map is NULL");
+    if (!map->step_pending) return fail(FAR_ERR_INVALID, "no step is pending (far_process_scan_async first)");
+    if (!out_pose) return fail(FAR_ERR_INVALID, "out_pose is NULL");
+    if (out_cov && !map->step_want_cov) return fail(FAR_ERR_INVALID, "out_cov given but the step did not ask for it");
+    map->step_pending = false;
     CK(cudaStreamSynchronize(map->stream));
     if (map->h_ctr->n_tomb > map->map.cap / 4) {
         CK(map_rebuild(map->map, map->stream));
@@ -1111,6 +1124,18 @@ far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, u
     }
     if (res == FAR_OK) return check_device_errors(map, "far_process_scan");
     return res;
+}
+
+
+far_status far_process_scan_motion(far_map* map, const float* xyz, uint64_t n, uint32_t stride_bytes,
+                                   const far_motion* motion, const double init_pose[16], const far_reg_params* reg,
+                                   const far_insert_params* ins, double evict_radius, double out_pose[16],
+                                   double out_cov[36], far_step_result* result) {
+    if (map && !out_pose) return fail(FAR_ERR_INVALID, "reg params, init_pose or out_pose invalid");
+    const far_status st = far_process_scan_async(map, xyz, n, stride_bytes, motion, init_pose, reg, ins, evict_radius,
+                                                 out_cov != nullptr);
+    if (st != FAR_OK) return st;
+    return far_process_scan_wait(map, out_pose, out_cov, result);
 }
 
 // ---------------------------------------------------------------- motion undistortion (Sec. III-A.1)

@@ -202,7 +202,10 @@ __global__ void k_world_keys(const float4* __restrict__ in, u32 n, Pose12 T, int
 
 // Groups of more members than this are sorted by a whole block of k_group_sort (one pass over
 // a bitmap of up to 262144 input indices in the block's shared memory) instead of one warp.
-constexpr u32 GS_BLOCK_MIN = 1024;
+#ifndef FAR_GS_BLOCK_MIN
+#define FAR_GS_BLOCK_MIN 1024
+#endif
+constexpr u32 GS_BLOCK_MIN = FAR_GS_BLOCK_MIN;
 
 // Groups: the first point of each slot (rank 0) opens the slot's group, a contiguous range
 // of its size taken from the running total, and records it under a group index. The heads of

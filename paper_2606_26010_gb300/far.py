@@ -159,6 +159,9 @@ _SIGS = {
     "far_undistort": (ctypes.c_int, [_vp, _u64, _u32, _vp, _vp, _vp]),
     "far_process_scan_motion": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, ctypes.c_double, _vp,
                                                _vp, _vp]),
+    "far_process_scan_async": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                              ctypes.c_int32]),
+    "far_process_scan_wait": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "far_prefetch_points": (ctypes.c_int, [_vp, _vp, _u64, _u32]),
 }
 EXPORTED = tuple(_SIGS)
@@ -384,6 +387,30 @@ class VoxelMap:
                                                    ctypes.byref(prm), ctypes.byref(ins), float(evict_radius),
                                                    _p(pose), _p(cov), ctypes.byref(res)),
                    allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
+        return pose.reshape(4, 4), (cov.reshape(6, 6) if want_cov else None), res.as_dict()
+
+    def process_scan_async(self, xyz, init, max_iters=10, conv_eps=0.0, tau=2.0, kappa=2.0 / 9.0,
+                           time_budget_s=0.0, asmd=True, r_near=10.0, r_max=100.0, evict_radius=0.0, want_cov=False,
+                           threads_per_point=0, motion=None):
+        """far_process_scan_async: enqueue the step and return; collect it with process_scan_wait.
+        The points must stay alive and unchanged until then."""
+        ptr, n, stride, keep = _points(xyz)
+        prm = RegParams(max_iters, conv_eps, tau, kappa, time_budget_s, threads_per_point)
+        ins = InsertParams(int(asmd), r_near, r_max)
+        _check(self._L.far_process_scan_async(self._h, ptr, n, stride, ctypes.byref(motion) if motion is not None
+                                              else None, _p(_pose(init)), ctypes.byref(prm), ctypes.byref(ins),
+                                              float(evict_radius), int(bool(want_cov))))
+        self._pending = (keep, bool(want_cov))
+
+    def process_scan_wait(self):
+        """far_process_scan_wait: (pose 4x4, cov 6x6 or None, result dict) of the pending step."""
+        keep, want_cov = self._pending if getattr(self, "_pending", None) else (None, False)
+        pose = np.zeros(16)
+        cov = np.zeros(36) if want_cov else None
+        res = StepResult()
+        status = self._L.far_process_scan_wait(self._h, _p(pose), _p(cov), ctypes.byref(res))
+        self._pending = None
+        _check(status, allow=(FAR_ERR_DEGENERATE, FAR_ERR_TIMEOUT))
         return pose.reshape(4, 4), (cov.reshape(6, 6) if want_cov else None), res.as_dict()
 
     def prefetch(self, xyz):

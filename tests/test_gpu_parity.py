@@ -445,6 +445,41 @@ def test_prefetched_host_scans_give_the_same_results(far, problem1):
         assert np.array_equal(out[0][1][key], out[1][1][key]), key
 
 
+def test_async_step_equals_the_blocking_step(far, problem1):
+    """far_process_scan_async + far_process_scan_wait, with the next scan's prefetch issued while
+    the step runs, gives bitwise the poses, covariances, results and map of far_process_scan; a
+    second async call before the wait and a wait with no step pending are rejected."""
+    import torch
+    scans = [torch.from_numpy(np.ascontiguousarray(s)).pin_memory() for s in problem1.map_scans[:4]]
+    kw = dict(max_iters=10, conv_eps=5e-3, tau=2.0, kappa=2.0 / 9, asmd=True, r_near=10.0, r_max=100.0,
+              evict_radius=60.0, want_cov=True)
+    out = []
+    for use_async in (False, True):
+        g = far.VoxelMap(0.5, 20, 5, max_voxels=1 << 17, max_scan_points=40_000)
+        g.insert(scans[0], problem1.map_poses[0])
+        steps = []
+        for i in range(1, 4):
+            if use_async:
+                g.process_scan_async(scans[i], problem1.map_poses[i], **kw)
+                if i == 1:
+                    with pytest.raises(far.FarError):
+                        g.process_scan_async(scans[i], problem1.map_poses[i], **kw)
+                if i + 1 < 4:
+                    g.prefetch(scans[i + 1])
+                steps.append(g.process_scan_wait())
+            else:
+                steps.append(g.process_scan(scans[i], problem1.map_poses[i], **kw))
+        if use_async:
+            with pytest.raises(far.FarError):
+                g.process_scan_wait()
+        out.append((steps, g.export()))
+        g.close()
+    for (Ta, Ca, ra), (Tb, Cb, rb) in zip(out[0][0], out[1][0]):
+        assert np.array_equal(Ta, Tb) and np.array_equal(Ca, Cb) and ra == rb
+    for key in out[0][1]:
+        assert np.array_equal(out[0][1][key], out[1][1][key]), key
+
+
 def test_graph_loop_equals_explicit_launches(far, problem1, maps1):
     """With conv_eps > 0 the loop runs as a graph with a device-side while loop; with profiling it
     runs as explicit launches. Both apply the same kernels in the same order: identical results."""
