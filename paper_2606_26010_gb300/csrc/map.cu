@@ -1285,10 +1285,24 @@ __global__ void k_iota(u32* a, u32 n) {
     for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
 
+// Slots per thread of the eviction scan: all of a thread's slot loads are issued before any is
+// tested (the table is mostly empty slots, so the scan is bound by the loads' latency).
+constexpr u32 EVICT_PER_THREAD = 4;
+
 __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, double cz, double r2, u32* ring,
                         u32 max_buckets, MapCounters* ctr, const double* __restrict__ dev_T) {
     pdl_wait();
     pdl_trigger();
+    // thread t takes slots t, t + T, t + 2 T, t + 3 T (T = threads in the grid): the whole slot
+    // (key, bucket, count) in one 16 B load each
+    const u32 nthreads = gridDim.x * blockDim.x;
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 raw[EVICT_PER_THREAD];
+#pragma unroll
+    for (u32 k = 0; k < EVICT_PER_THREAD; ++k) {
+        const u32 h = t + k * nthreads;
+        raw[k] = h < cap ? *reinterpret_cast<const uint4*>(slots + h) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+    }
     if (dev_T) {
         cx = dev_T[3];
         cy = dev_T[7];
@@ -1304,9 +1318,11 @@ __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, do
     const float Mf = fabsf(fcx) + fabsf(fcy) + fabsf(fcz) + fr + fv;
     const float band = 2e-5f + 2e-6f * Mf / fmaxf(fr, 1e-3f);
     const float lo2 = fr2 * (1.0f - band), hi2 = fr2 * (1.0f + band);
-    for (u32 h = blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += gridDim.x * blockDim.x) {
-        const u64 key = slots[h].key;
-        if (key >> 63) continue;  // empty or tombstone
+#pragma unroll
+    for (u32 k = 0; k < EVICT_PER_THREAD; ++k) {
+        const u64 key = ((u64)raw[k].y << 32) | raw[k].x;
+        if (key >> 63) continue;  // empty, tombstone or beyond the table
+        const u32 h = t + k * nthreads;
         int kx, ky, kz;
         unpack_key(key, kx, ky, kz);
         // FP32 estimate first; only distances near the radius take the exact FP64 test
@@ -1318,15 +1334,15 @@ __global__ void k_evict(Slot* slots, u32 cap, double v, double cx, double cy, do
         else if (e2 > hi2) far_away = true;
         else far_away = centre_dist2(kx, ky, kz, v, cx, cy, cz) > r2;
         if (!far_away) continue;
-        const u32 b = slots[h].bucket;
-        const u32 c = slots[h].count;
+        const u32 b = raw[k].z;
+        const u32 c = raw[k].w;
         slots[h].key = KEY_TOMB;
         slots[h].bucket = NO_BUCKET;
         slots[h].count = 0;
         atomicAdd(&ctr->n_tomb, 1u);
         if (b != NO_BUCKET) {
-            const u32 t = atomicAdd(&ctr->ring_tail, 1u);
-            ring[t % max_buckets] = b;
+            const u32 tt = atomicAdd(&ctr->ring_tail, 1u);
+            ring[tt % max_buckets] = b;
             atomicSub(&ctr->n_voxels, 1u);
             atomicAdd(&ctr->removed, (unsigned long long)c);
             atomicAdd(&ctr->n_points, (unsigned long long)(0ull - (unsigned long long)c));
@@ -1727,7 +1743,7 @@ cudaError_t map_local_reset(DeviceMap& m, const Scratch& s, u32 n, cudaStream_t 
 
 cudaError_t map_evict(DeviceMap& m, const double center[3], double radius, cudaStream_t st, const double* dev_pose) {
     FAR_TRY(cudaMemsetAsync(&m.ctr->removed, 0, sizeof(unsigned long long), st));
-    const u32 blocks = min(blocks_for(m.cap), 152u * 16u);
+    const u32 blocks = max(1u, (u32)(((u64)m.cap + (u64)TPB * EVICT_PER_THREAD - 1) / ((u64)TPB * EVICT_PER_THREAD)));
     const double c0 = center ? center[0] : 0.0, c1 = center ? center[1] : 0.0, c2 = center ? center[2] : 0.0;
     FAR_LAUNCH(k_evict, blocks, TPB, 0, st, m.slots, m.cap, (double)m.v, c0, c1, c2, radius * radius, m.ring, m.max_buckets,
                                     m.ctr, dev_pose);
