@@ -275,8 +275,9 @@ __device__ __forceinline__ float group_union_kth(const unsigned long long (&bk)[
     return c[K - 1];
 }
 
-// K nearest of the query searched by a group of TPP consecutive lanes. Lane sl first scans
-// voxel sl of the order own, faces, edges, corners into its own sorted K best; the group then
+// K nearest of the query searched by a group of TPP consecutive lanes. Lane 0 first scans the
+// query's own voxel and lanes 1 .. TPP - 1 the faces nearest to the query, each into its own
+// sorted K best; the group then
 // takes the K-th distance of the union of the lanes' lists as its bound (group_union_kth; the K
 // best of all 27 voxels are at least that close), lists the remaining voxels whose box distance
 // does not exceed it
@@ -305,15 +306,32 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
         for (int o = TPP / 2; o > 0; o >>= 1) kth = fminf(kth, __shfl_xor_sync(0xffffffffu, kth, o));
         return kth;
     };
-    if (keyed && sl < 27) scan(sl);
+    static_assert(TPP >= 2 && TPP <= 7, "the first round takes the own voxel and TPP - 1 faces");
+    // first round: lane 0 the own voxel, lanes 1 .. TPP - 1 the faces nearest to the query (face
+    // j = c_nb_order entry 1 + j, at distance lo/hi of its axis; ties to the lower entry), so that
+    // the first bound is as tight as the first round allows
+    const float fdist[6] = {fd.lo[0], fd.hi[0], fd.lo[1], fd.hi[1], fd.lo[2], fd.hi[2]};
+    u32 chosen = 0;   // bit v: entry v scanned in the first round
+    int my_first = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        int rank = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) rank += (fdist[i] < fdist[j] || (fdist[i] == fdist[j] && i < j)) ? 1 : 0;
+        if (rank < TPP - 1) chosen |= 1u << (1 + j);
+        if (rank == sl - 1) my_first = 1 + j;
+    }
+    if (keyed) scan(my_first);
     // the K best of the union are at least as close as the union's K-th distance, which is finite
     // once the first round's voxels hold K points together (sparse regions)
     float bound = group_union_kth<K, TPP>(bk);
-    // survivors of the remaining voxels under the group's bound, compacted in voxel order
+    // survivors of the other voxels under the group's bound, compacted in voxel order
     u32 mine = 0;
     int k = 0;
-    for (int v = TPP + sl; v < 27; v += TPP, ++k)
-        if (keyed && !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound)) mine |= 1u << k;
+    for (int v = 1 + sl; v < 27; v += TPP, ++k)
+        if (keyed && !((chosen >> v) & 1u) &&
+            !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound))
+            mine |= 1u << k;
     const int cnt = __popc(mine);
     int pre = cnt;   // inclusive prefix over the group's lanes
 #pragma unroll
@@ -324,7 +342,7 @@ __device__ __forceinline__ int group_knn(const MapView& m, u32 max_probe, const 
     const int total = __shfl_sync(0xffffffffu, pre, TPP - 1, TPP);
     pre -= cnt;
     k = 0;
-    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+    for (int v = 1 + sl; v < 27; v += TPP, ++k)
         if (mine & (1u << k)) list[pre++] = (unsigned char)v;
     __syncwarp();
     const int rounds = (__reduce_max_sync(0xffffffffu, (u32)total) + TPP - 1) / TPP;   // warp-uniform
