@@ -145,7 +145,8 @@ __device__ __forceinline__ float nn_group_bound(unsigned long long best_key, flo
 }
 
 // Nearest map point of q (smallest (d^2, id)) searched by a group of TPP consecutive
-// lanes. The first TPP voxels of the order own, faces, edges, corners are scanned at once
+// lanes. A first round scans TPP voxels at once: the own voxel and the TPP - 1 faces nearest
+// to the query (TPP <= 6), else entries 0 .. TPP - 1 of the order own, faces, edges, corners
 // (lane sl takes entry sl); the group then keeps only the other voxels whose box distance
 // does not exceed min(best, tau^2), lists them in shared memory (`list`, 27 entries per
 // group) and scans them TPP at a time, sharing the best after each round. A voxel whose box
@@ -160,14 +161,34 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, c
     best_pos = 0;
     best_v = 0;
     const FaceDist fd = face_distances(f.q[0], f.q[1], f.q[2], f.lk[0], f.lk[1], f.lk[2], m.v);
-    if (keyed && sl < 27) nn_try_voxel<PREC>(m, max_probe, f, fd, sl, limit2, best_key, best_pos, best_v);
+    // first round: entries 0 .. TPP - 1 of the order; with fewer than 7 lanes, lane 0 takes the own
+    // voxel and lanes 1 .. TPP - 1 the faces nearest to the query (face j = entry 1 + j, ties to
+    // the lower entry), so that the first bound is as tight as the round allows
+    u32 chosen = 0;   // bit v: entry v scanned in the first round (TPP <= 6)
+    int my_first = sl;
+    if constexpr (TPP <= 6) {
+        const float fdist[6] = {fd.lo[0], fd.hi[0], fd.lo[1], fd.hi[1], fd.lo[2], fd.hi[2]};
+        my_first = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            int rank = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) rank += (fdist[i] < fdist[j] || (fdist[i] == fdist[j] && i < j)) ? 1 : 0;
+            if (rank < TPP - 1) chosen |= 1u << (1 + j);
+            if (rank == sl - 1) my_first = 1 + j;
+        }
+    }
+    if (keyed && my_first < 27) nn_try_voxel<PREC>(m, max_probe, f, fd, my_first, limit2, best_key, best_pos, best_v);
     group_best<TPP, PREC>(best_key, best_pos, best_v);
-    // survivors of the remaining voxels under the group's bound, compacted in input order
+    // survivors of the other voxels under the group's bound, compacted in input order
     const float bound0 = nn_group_bound(best_key, limit2);
+    constexpr int kRest0 = TPP <= 6 ? 1 : TPP;   // first entry of the survivor scan
     u32 mine = 0;
     int k = 0;
-    for (int v = TPP + sl; v < 27; v += TPP, ++k)
-        if (keyed && !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound0)) mine |= 1u << k;
+    for (int v = kRest0 + sl; v < 27; v += TPP, ++k)
+        if (keyed && !((chosen >> v) & 1u) &&
+            !(box_lb2(fd, c_nb_order[v][0], c_nb_order[v][1], c_nb_order[v][2]) > bound0))
+            mine |= 1u << k;
     const int cnt = __popc(mine);
     int pre = cnt;   // inclusive prefix over the group's lanes
 #pragma unroll
@@ -178,7 +199,7 @@ __device__ __forceinline__ void group_nearest(const MapView& m, u32 max_probe, c
     const int total = __shfl_sync(0xffffffffu, pre, TPP - 1, TPP);
     pre -= cnt;
     k = 0;
-    for (int v = TPP + sl; v < 27; v += TPP, ++k)
+    for (int v = kRest0 + sl; v < 27; v += TPP, ++k)
         if (mine & (1u << k)) list[pre++] = (unsigned char)v;
     __syncwarp();
     const int rounds = (__reduce_max_sync(0xffffffffu, (u32)total) + TPP - 1) / TPP;   // warp-uniform
