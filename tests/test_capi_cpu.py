@@ -69,6 +69,8 @@ def test_null_arguments_are_rejected(L):
     assert L.far_map_destroy(None) == far.FAR_ERR_INVALID
     assert L.far_map_insert(None, None, 0, 12, None, None, None) == far.FAR_ERR_INVALID
     assert L.far_register_scan(None, None, 0, 12, None, None, None, None, None) == far.FAR_ERR_INVALID
+    assert L.far_process_scan_async(None, None, 0, 12, None, None, None, None, 0.0, 0) == far.FAR_ERR_INVALID
+    assert L.far_process_scan_wait(None, None, None, None) == far.FAR_ERR_INVALID
 
 
 def test_threshold_matches_oracle_on_random_sequence(L):
