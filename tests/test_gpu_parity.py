@@ -156,9 +156,9 @@ def test_no_spacing_and_single_voxel_cap(far):
 
 @pytest.mark.parametrize("size", [33, 513, 2500, 6000, 9000])
 def test_large_voxel_groups_admit_in_input_order(far, size):
-    """All points of a batch in a few voxels: groups above 32 and 128 points (register sorts; the
-    larger ones through a bitmap of their compact index range, and above 192 admitted by a whole
-    block) still admit in input order."""
+    """All points of a batch in a few voxels: groups above 32 and 128 points (register sorts), up
+    to 1024 (a warp's bitmap of their compact index range) and above (sorted by a whole block;
+    above 192 points admitted by a whole block) still admit in input order."""
     rng = np.random.default_rng(size)
     pts = rng.uniform(0.01, 0.99, size=(size, 3)).astype(np.float32)   # voxels (0|1, 0|1, 0|1) at v = 0.5
     for spacing in (0.0, 0.03):
@@ -171,10 +171,11 @@ def test_large_voxel_groups_admit_in_input_order(far, size):
                                             (1_200_000, 1000)])
 def test_voxel_groups_spread_over_the_input(far, n_total, stride):
     """Every stride-th point falls in one voxel and the rest scatter over a 400 m cube (about one
-    per voxel), so that voxel's group spans the whole input order: 40000 points in one voxel and
-    groups of 9000 and 1500 whose ranges take 3 and 10 bitmap passes; 600 and 1200 points over
-    ranges wide enough that the shared-memory network and the chunk merge are the cheaper sorts.
-    All admit in input order (with ASMD caps for the 9000-point group)."""
+    per voxel), so that voxel's group spans the whole input order: groups of 40000, 9000, 1500
+    and 1200 points sorted by whole blocks (the last two over index ranges that take 2 and 5
+    windows of the block's bitmap), and 600 points over a range wide enough that a warp's
+    shared-memory network is cheaper than its bitmap. All admit in input order (with ASMD caps
+    for the 9000-point group)."""
     rng = np.random.default_rng(n_total + stride)
     pts = rng.uniform(-200.0, 200.0, size=(n_total, 3))
     pts[::stride] = rng.uniform(0.01, 0.49, size=(len(pts[::stride]), 3))
