@@ -403,11 +403,15 @@ def run_sequence(m, veh, thr, dev, prior_kind, stream, flush, n_seq, timed_from,
             gc.collect()
             flush.zero_()
             if e2e:
+                # host-timed step: the de-skew fit (host) is part of it
                 torch.cuda.synchronize()
                 w0 = time.perf_counter()
+                mo = prior.motion(t) if skew else None
             else:
+                # device-timed step: the host's de-skew fit comes before the first event, so that
+                # the device does not sit idle inside the timed region while Python fits the lines
+                mo = prior.motion(t) if skew else None
                 ev0.record(stream)
-            mo = prior.motion(t) if skew else None
             step_kw = dict(max_iters=MAX_ITERS, conv_eps=CONV_EPS, tau=tau, kappa=kappa, asmd=True, r_near=R_NEAR,
                            r_max=R_MAX, evict_radius=EVICT_R, motion=mo)
             if e2e:
