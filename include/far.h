@@ -444,14 +444,20 @@ far_status far_lidar_velocity(const double T_prev[16], const double T_cur[16], d
  *   t += dt R v,  theta += dt E(theta) (omega_m - omega_b),
  *   v += dt (-[omega_m]x v + (a_m - a_b) + R^T (0, 0, -g)),
  * with the analytic Jacobian and Q = diag(q) dt; the state is kept in a history of
- * `history` entries. far_ekf_update takes a registration that refers to time t_meas (the
- * scan's time stamp, possibly in the past): z_s = [t_L, theta_L, v_L] (Eq. 10 without the
- * reference angles), projected to the current time by Eq. 11, z_k = z_s + h(x) - h(x_s)
- * with h the identity and x_s the stored state at or just before t_meas (the oldest one if
- * t_meas precedes the history); then a Kalman update with R = diag(r) (Joseph form), angle
- * innovations wrapped to (-pi, pi]. Biases are fixed parameters (calibrated at standstill,
- * as the paper does). FAR_ERR_INVALID on bad arguments or time going backwards;
- * FAR_ERR_DEGENERATE when P + R is not positive definite.
+ * `history` entries, each with the IMU input of the prediction that produced it.
+ * far_ekf_update takes a registration that refers to time t_meas (the scan's time stamp,
+ * possibly in the past): z_s = [t_L, theta_L, v_L] and, when r_ref is set, the reference roll
+ * and pitch theta_ref (Eq. 10), projected to the current time by Eq. 11,
+ * z_k = z_s + h(x) - h(x_s), with x_s the stored state at or just before t_meas (the oldest one
+ * if t_meas precedes the history) and h selecting the measured states (theta_ref measures the
+ * state's roll and pitch); then a Kalman update with R = diag(r, r_ref) (Joseph form), angle
+ * innovations wrapped to (-pi, pi]. theta_ref comes from x_s's velocity and the IMU input that
+ * produced x_s: gravity in the body frame from Eq. 9's velocity equation taken as steady,
+ * g = [omega_m]x v - (a_m - a_b), solved for roll = atan2(-g_y, -g_z) and
+ * pitch = atan2(g_x, sqrt(g_y^2 + g_z^2)) (an entry with no IMU input yet, e.g. the initial
+ * state, gives no theta_ref rows). Biases are fixed parameters (calibrated at standstill, as
+ * the paper does). FAR_ERR_INVALID on bad arguments or time going backwards;
+ * FAR_ERR_DEGENERATE when H P H^T + R is not positive definite.
  */
 typedef struct far_ekf far_ekf;
 typedef struct far_ekf_params {
@@ -461,6 +467,7 @@ typedef struct far_ekf_params {
     double q[9];          /* process noise density per state: Q = diag(q) dt */
     double r[9];          /* measurement noise variances of [t_L, theta_L, v_L] */
     uint32_t history;     /* stored states for the delay compensation, 2..2^20 */
+    double r_ref[2];      /* variances of the reference roll and pitch; both 0: no theta_ref rows */
 } far_ekf_params;
 far_status far_ekf_create(const far_ekf_params* params, double t0, const double x0[9], const double P0[81],
                           far_ekf** out);

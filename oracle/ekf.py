@@ -14,8 +14,14 @@ far_ekf_* calls) never does and shares no code with it.
                           v += dt (-[omega_m]x v + (a_m - a_b) + g(theta))
                           with R(theta) = Rz(yaw) Ry(pitch) Rx(roll), E the Euler-rate
                           matrix of that convention and g(theta) = R^T (0, 0, -g)
-  measurement ........... Eq. 10 without the reference angles: z = [t_L, theta_L, v_L],
-                          h(x) = x (the reference roll/pitch of the cited filter is not built)
+  measurement ........... Eq. 10: z = [t_L, theta_L, v_L] measured as the states themselves, and,
+                          with r_ref, the reference roll and pitch theta_ref measured as the
+                          state's roll and pitch (H is the 9 x 9 identity with those two rows
+                          below it)
+  reference angles ...... gravity in the body frame from Eq. 9's velocity equation taken as
+                          steady, g = omega_m x v - (a_m - a_b), at the stored state of the
+                          measurement's time and the IMU input that produced it;
+                          roll = atan2(-g_y, -g_z), pitch = atan2(g_x, |(g_y, g_z)|)
   delay compensation .... Eq. 11: z_k = z_s + h(x_{k|k-1}) - h(x_s), x_s the filter's state
                           at the measurement's time stamp
   upsampling ............ Sec. III-B (end), read as: the correction K y of one measurement is
@@ -93,6 +99,12 @@ def transition(x, acc, gyro, dt, gravity, acc_bias, gyro_bias) -> np.ndarray:
     return np.concatenate([t + dt * dt_, th + dt * dth, v + dt * dv])
 
 
+def reference_angles(v, acc, gyro, acc_bias=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """(roll, pitch) whose gravity R^T (0, 0, -g) points along omega x v - (a - a_b)."""
+    g = np.cross(np.asarray(gyro, float), np.asarray(v, float)) - (np.asarray(acc, float) - np.asarray(acc_bias, float))
+    return np.array([math.atan2(-g[1], -g[2]), math.atan2(g[0], math.hypot(g[1], g[2]))])
+
+
 def pose_of(x) -> np.ndarray:
     T = np.eye(4)
     T[:3, :3] = rot_zyx(x[3:6])
@@ -104,15 +116,16 @@ class KinematicEKF:
     """The filter of Sec. III-B: predictions at the IMU rate, delayed LiDAR updates (Eq. 11)."""
 
     def __init__(self, x0, P0, q, r, gravity=9.81, acc_bias=(0.0, 0.0, 0.0), gyro_bias=(0.0, 0.0, 0.0),
-                 t0=0.0, history=256):
+                 t0=0.0, history=256, r_ref=None):
         self.x = np.asarray(x0, float).copy()
         self.P = np.asarray(P0, float).copy()
         self.q = np.asarray(q, float)          # process noise density per state (Q = diag(q) dt)
         self.r = np.asarray(r, float)          # measurement noise variances (9)
         self.gravity = float(gravity)
         self.acc_bias, self.gyro_bias = np.asarray(acc_bias, float), np.asarray(gyro_bias, float)
+        self.r_ref = None if r_ref is None or r_ref[0] <= 0.0 else np.asarray(r_ref, float)
         self.time = float(t0)
-        self.hist = [(self.time, self.x.copy())]
+        self.hist = [(self.time, self.x.copy(), None)]   # (time, state, IMU input that produced it)
         self.history = int(history)
         self.pending = []                      # shares of a spread correction still to add
 
@@ -135,35 +148,46 @@ class KinematicEKF:
         self.time = float(t)
         if self.pending:
             self._add_share()
-        self.hist.append((self.time, self.x.copy()))
+        self.hist.append((self.time, self.x.copy(), (np.asarray(acc, float).copy(), np.asarray(gyro, float).copy())))
         if len(self.hist) > self.history:
             self.hist.pop(0)
 
+    def entry_at(self, t: float):
+        """The stored (state, input) with the latest time stamp not after t (the oldest otherwise)."""
+        best = self.hist[0]
+        for entry in self.hist:
+            if entry[0] <= t + 1e-12:
+                best = entry
+        return best[1], best[2]
+
     def state_at(self, t: float) -> np.ndarray:
-        """The stored state with the latest time stamp not after t (the oldest one otherwise)."""
-        best = self.hist[0][1]
-        for ts, xs in self.hist:
-            if ts <= t + 1e-12:
-                best = xs
-        return best
+        return self.entry_at(t)[0]
 
     def update(self, t_meas: float, T_L, v_L, cycles: int = 1):
         while self.pending:
             self._add_share()
         z_s = np.concatenate([np.asarray(T_L, float)[:3, 3], euler_from_rot(np.asarray(T_L, float)[:3, :3]),
                               np.asarray(v_L, float)])
-        x_s = self.state_at(t_meas)
-        d = self.x - x_s                                    # h(x_k|k-1) - h(x_s), h = identity
-        z_k = z_s + d                                       # Eq. 11
-        y = z_k - self.x
-        for a in (3, 4, 5):
+        x_s, u_s = self.entry_at(t_meas)
+        H = np.eye(9)
+        r = self.r
+        angle_rows = [3, 4, 5]
+        if self.r_ref is not None and u_s is not None:
+            z_s = np.concatenate([z_s, reference_angles(x_s[6:9], u_s[0], u_s[1], self.acc_bias)])
+            H = np.vstack([H, np.eye(9)[[3, 4]]])
+            r = np.concatenate([r, self.r_ref])
+            angle_rows = [3, 4, 5, 9, 10]
+        z_k = z_s + H @ self.x - H @ x_s                    # Eq. 11
+        y = z_k - H @ self.x
+        for a in angle_rows:
             y[a] = wrap(y[a])
-        S = self.P + np.diag(self.r)
-        K = self.P @ np.linalg.inv(S)
-        I_K = np.eye(9) - K
+        R = np.diag(r)
+        S = H @ self.P @ H.T + R
+        K = self.P @ H.T @ np.linalg.inv(S)
+        I_K = np.eye(9) - K @ H
         self.pending = [K @ y / cycles for _ in range(cycles)]
         self._add_share()
-        self.P = I_K @ self.P @ I_K.T + K @ np.diag(self.r) @ K.T
+        self.P = I_K @ self.P @ I_K.T + K @ R @ K.T
         return y
 
     def pose(self) -> np.ndarray:

@@ -69,6 +69,19 @@ void euler_from_rot(const double* T, double th[3]) {
     th[2] = std::atan2(T[4], T[0]);
 }
 
+// Reference roll and pitch from the IMU (Sec. III-B, Eq. 10): gravity in the body frame from the
+// velocity equation of Eq. 9 with the velocity taken as steady, g(theta) = [omega_m]x v - (a_m - a_b),
+// and g(theta) = R(theta)^T (0, 0, -g) = (g sin p, -g cos p sin r, -g cos p cos r) solved for r, p.
+void reference_angles(const double v[3], const double u[6], const double ab[3], double out[2]) {
+    const double* a = u;
+    const double* w = u + 3;
+    const double gx = (w[1] * v[2] - w[2] * v[1]) - (a[0] - ab[0]);
+    const double gy = (w[2] * v[0] - w[0] * v[2]) - (a[1] - ab[1]);
+    const double gz = (w[0] * v[1] - w[1] * v[0]) - (a[2] - ab[2]);
+    out[0] = std::atan2(-gy, -gz);
+    out[1] = std::atan2(gx, std::sqrt(gy * gy + gz * gz));
+}
+
 // In-place Cholesky solve of S X = B for a symmetric positive definite n x n S (row-major);
 // B is n x m. Returns false when S is not positive definite.
 bool chol_solve(int n, std::vector<double>& S, std::vector<double>& B, int m) {
@@ -106,9 +119,13 @@ struct far_ekf {
     double t = 0.0;
     double x[9] = {};
     double P[81] = {};
-    std::vector<double> hist_t;   // ring of (time, state) for delay compensation
-    std::vector<double> hist_x;
+    std::vector<double> hist_t;   // ring of (time, state, the IMU input that produced it) for delay
+    std::vector<double> hist_x;   // compensation and the reference angles
+    std::vector<double> hist_u;   // a_m, omega_m (6 per entry)
+    std::vector<unsigned char> hist_has_u;
     uint32_t hist_n = 0, hist_head = 0;
+    double u_last[6] = {};        // the input of the last prediction (for the next push)
+    bool has_u_last = false;
     // a state correction spread over update cycles: `share` is added after each of the next
     // `shares_left` predictions
     double share[9] = {};
@@ -129,15 +146,17 @@ struct far_ekf {
         const uint32_t slot = (hist_head + hist_n) % cap;
         hist_t[slot] = t;
         std::memcpy(&hist_x[9 * (size_t)slot], x, sizeof(x));
+        std::memcpy(&hist_u[6 * (size_t)slot], u_last, sizeof(u_last));
+        hist_has_u[slot] = has_u_last ? 1 : 0;
         if (hist_n < cap) ++hist_n;
         else hist_head = (hist_head + 1) % cap;
     }
-    // the stored state with the latest time stamp not after t_meas (the oldest one otherwise)
-    const double* state_at(double t_meas) const {
-        const double* best = &hist_x[9 * (size_t)hist_head];
+    // the stored entry with the latest time stamp not after t_meas (the oldest one otherwise)
+    uint32_t entry_at(double t_meas) const {
+        uint32_t best = hist_head;
         for (uint32_t i = 0; i < hist_n; ++i) {
             const uint32_t s = (hist_head + i) % p.history;
-            if (hist_t[s] <= t_meas + 1e-12) best = &hist_x[9 * (size_t)s];
+            if (hist_t[s] <= t_meas + 1e-12) best = s;
         }
         return best;
     }
@@ -165,6 +184,9 @@ far_status far_ekf_create(const far_ekf_params* params, double t0, const double 
     for (int i = 0; i < 9; ++i)
         if (params->q[i] < 0.0 || !(params->r[i] > 0.0))
             return bad("far_ekf_create: q must be >= 0 and r > 0");
+    if (!finite_n(params->r_ref, 2) || params->r_ref[0] < 0.0 || params->r_ref[1] < 0.0 ||
+        ((params->r_ref[0] > 0.0) != (params->r_ref[1] > 0.0)))
+        return bad("far_ekf_create: r_ref must be both 0 (off) or both > 0");
     far_ekf* e = new (std::nothrow) far_ekf();
     if (!e) return FAR_ERR_OOM;
     e->p = *params;
@@ -173,6 +195,8 @@ far_status far_ekf_create(const far_ekf_params* params, double t0, const double 
     std::memcpy(e->P, P0, sizeof(e->P));
     e->hist_t.assign(params->history, 0.0);
     e->hist_x.assign(9 * (size_t)params->history, 0.0);
+    e->hist_u.assign(6 * (size_t)params->history, 0.0);
+    e->hist_has_u.assign(params->history, 0);
     e->push();
     *out = e;
     return FAR_OK;
@@ -251,6 +275,11 @@ far_status far_ekf_predict(far_ekf* e, double t, const double acc[3], const doub
     std::memcpy(e->P, Pn, sizeof(Pn));
     e->t = t;
     if (e->shares_left) e->add_share();   // this cycle's share of a spread correction
+    for (int i = 0; i < 3; ++i) {
+        e->u_last[i] = acc[i];
+        e->u_last[3 + i] = gyro[i];
+    }
+    e->has_u_last = true;
     e->push();
     return FAR_OK;
 }
@@ -266,8 +295,18 @@ far_status far_ekf_update_spread(far_ekf* e, double t_meas, const double pose[16
         return bad("far_ekf_update: non-finite input");
     if (cycles < 1 || cycles > 1000) return bad("far_ekf_update_spread: cycles must be in 1..1000");
     e->flush_shares();
-    // measurement at its own time s: z_s = [t_L, theta_L, v_L]
-    double z[9];
+    // measurement at its own time s: z_s = [t_L, theta_L, v_L], and with r_ref the reference roll and
+    // pitch (rows 9, 10, measuring the state's roll and pitch); row a measures state sel[a]
+    const uint32_t es = e->entry_at(t_meas);
+    const double* xs = &e->hist_x[9 * (size_t)es];
+    const bool ref = e->p.r_ref[0] > 0.0 && e->hist_has_u[es];
+    const int m = ref ? 11 : 9;
+    int sel[11];
+    double z[11], rd[11];
+    for (int a = 0; a < 9; ++a) {
+        sel[a] = a;
+        rd[a] = e->p.r[a];
+    }
     z[0] = pose[3];
     z[1] = pose[7];
     z[2] = pose[11];
@@ -275,31 +314,40 @@ far_status far_ekf_update_spread(far_ekf* e, double t_meas, const double pose[16
     z[6] = v_L[0];
     z[7] = v_L[1];
     z[8] = v_L[2];
-    // Eq. 11: z_k = z_s + h(x_k|k-1) - h(x_s), h = identity
-    const double* xs = e->state_at(t_meas);
-    double y[9];
-    for (int i = 0; i < 9; ++i) y[i] = (z[i] + (e->x[i] - xs[i])) - e->x[i];
-    for (int a = 3; a < 6; ++a) y[a] = wrap_angle(y[a]);
-    // K = P S^-1 with S = P + R (S symmetric): solve S K^T = P (P symmetric)
-    std::vector<double> S(81), Kt(81);
-    for (int i = 0; i < 81; ++i) {
-        S[i] = e->P[i];
-        Kt[i] = e->P[i];
+    if (ref) {
+        reference_angles(xs + 6, &e->hist_u[6 * (size_t)es], e->p.acc_bias, z + 9);
+        sel[9] = 3;
+        sel[10] = 4;
+        rd[9] = e->p.r_ref[0];
+        rd[10] = e->p.r_ref[1];
     }
-    for (int i = 0; i < 9; ++i) S[9 * i + i] += e->p.r[i];
-    if (!chol_solve(9, S, Kt, 9)) {
+    // Eq. 11: z_k = z_s + h(x_k|k-1) - h(x_s), h selecting states; the innovation z_k - h(x_k|k-1)
+    double y[11];
+    for (int a = 0; a < m; ++a) {
+        const int i = sel[a];
+        y[a] = (z[a] + (e->x[i] - xs[i])) - e->x[i];
+        if (i >= 3 && i < 6) y[a] = wrap_angle(y[a]);
+    }
+    // K = P H^T S^-1 with S = H P H^T + R (symmetric): solve S K^T = H P
+    std::vector<double> S((size_t)m * m), Kt((size_t)m * 9);
+    for (int a = 0; a < m; ++a) {
+        for (int b = 0; b < m; ++b) S[(size_t)m * a + b] = e->P[9 * sel[a] + sel[b]];
+        S[(size_t)m * a + a] += rd[a];
+        for (int j = 0; j < 9; ++j) Kt[9 * (size_t)a + j] = e->P[9 * sel[a] + j];
+    }
+    if (!chol_solve(m, S, Kt, 9)) {
         far::set_last_error("far_ekf_update: innovation covariance not positive definite");
         return FAR_ERR_DEGENERATE;
     }
-    double K[81];
+    double K[9 * 11];
     for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) K[9 * i + j] = Kt[9 * j + i];
+        for (int a = 0; a < m; ++a) K[11 * i + a] = Kt[9 * (size_t)a + i];
     // the correction K y, all at once or in equal shares over `cycles` update cycles (this one
     // and the next cycles - 1 predictions); the covariance takes the whole update now
     double dx[9];
     for (int i = 0; i < 9; ++i) {
         double s = 0.0;
-        for (int j = 0; j < 9; ++j) s += K[9 * i + j] * y[j];
+        for (int a = 0; a < m; ++a) s += K[11 * i + a] * y[a];
         dx[i] = s;
     }
     if (cycles == 1) {
@@ -310,10 +358,15 @@ far_status far_ekf_update_spread(far_ekf* e, double t_meas, const double pose[16
         e->shares_left = cycles;
         e->add_share();
     }
-    // Joseph form: P = (I - K) P (I - K)^T + K R K^T
+    // Joseph form: P = (I - K H) P (I - K H)^T + K R K^T
     double IK[81], A[81], Pn[81];
     for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) IK[9 * i + j] = (i == j ? 1.0 : 0.0) - K[9 * i + j];
+        for (int j = 0; j < 9; ++j) {
+            double v = (i == j ? 1.0 : 0.0);
+            for (int a = 0; a < m; ++a)
+                if (sel[a] == j) v -= K[11 * i + a];
+            IK[9 * i + j] = v;
+        }
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j < 9; ++j) {
             double s = 0.0;
@@ -323,10 +376,8 @@ far_status far_ekf_update_spread(far_ekf* e, double t_meas, const double pose[16
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j < 9; ++j) {
             double s = 0.0, r = 0.0;
-            for (int k = 0; k < 9; ++k) {
-                s += A[9 * i + k] * IK[9 * j + k];
-                r += K[9 * i + k] * e->p.r[k] * K[9 * j + k];
-            }
+            for (int k = 0; k < 9; ++k) s += A[9 * i + k] * IK[9 * j + k];
+            for (int a = 0; a < m; ++a) r += K[11 * i + a] * rd[a] * K[11 * j + a];
             Pn[9 * i + j] = s + r;
         }
     std::memcpy(e->P, Pn, sizeof(Pn));

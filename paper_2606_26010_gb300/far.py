@@ -109,7 +109,8 @@ def make_motion(w0=(0, 0, 0), w1=(0, 0, 0), v0=(0, 0, 0), v1=(0, 0, 0), time_off
 
 class EkfParams(ctypes.Structure):
     _fields_ = [("gravity", ctypes.c_double), ("acc_bias", ctypes.c_double * 3), ("gyro_bias", ctypes.c_double * 3),
-                ("q", ctypes.c_double * 9), ("r", ctypes.c_double * 9), ("history", ctypes.c_uint32)]
+                ("q", ctypes.c_double * 9), ("r", ctypes.c_double * 9), ("history", ctypes.c_uint32),
+                ("r_ref", ctypes.c_double * 2)]
 
 
 _vp = ctypes.c_void_p
@@ -572,7 +573,7 @@ class Ekf:
     """The library's kinematic EKF (Sec. III-B); arguments are marshalled only."""
 
     def __init__(self, x0, P0, q, r, gravity=9.81, acc_bias=(0.0, 0.0, 0.0), gyro_bias=(0.0, 0.0, 0.0), t0=0.0,
-                 history=256):
+                 history=256, r_ref=(0.0, 0.0)):
         self._L = lib()
         prm = EkfParams()
         prm.gravity = float(gravity)
@@ -581,6 +582,7 @@ class Ekf:
         prm.q[:] = [float(a) for a in q]
         prm.r[:] = [float(a) for a in r]
         prm.history = int(history)
+        prm.r_ref[:] = [float(a) for a in r_ref]
         h = ctypes.c_void_p()
         x0 = np.ascontiguousarray(x0, np.float64).reshape(9)
         P0 = np.ascontiguousarray(P0, np.float64).reshape(81)

@@ -186,6 +186,47 @@ def test_spread_update_divides_the_jump_of_the_odometry():
     assert np.linalg.norm(jumps[1]) > 0.1
 
 
+def test_reference_angles_closed_forms():
+    """theta_ref (Eq. 10): a resting IMU tilted by (roll, pitch) measures a = R^T (0, 0, g) (R built by
+    scipy from Z-Y-X Euler angles), which gives back roll and pitch for any yaw; a level constant
+    turn (rate w, speed s, centripetal specific force w s) gives zero roll and pitch; an
+    accelerometer bias is removed first."""
+    for roll, pitch, yaw in [(0.02, -0.03, 1.1), (-0.4, 0.25, -2.0), (0.0, 0.0, 0.3)]:
+        R = Rotation.from_euler("ZYX", [yaw, pitch, roll]).as_matrix()
+        acc = R.T @ np.array([0.0, 0.0, G])
+        np.testing.assert_allclose(oe.reference_angles([0, 0, 0], acc, [0, 0, 0]), [roll, pitch], atol=1e-14)
+        bias = np.array([0.05, -0.02, 0.1])
+        np.testing.assert_allclose(oe.reference_angles([0, 0, 0], acc + bias, [0, 0, 0], bias), [roll, pitch],
+                                   atol=1e-14)
+    s_, w = 30.0, 0.4
+    np.testing.assert_allclose(oe.reference_angles([s_, 0, 0], [0.0, w * s_, G], [0.0, 0.0, w]), [0.0, 0.0],
+                               atol=1e-15)
+
+
+def test_reference_rows_combine_with_the_lidar_angles():
+    """With diagonal P and R, roll and pitch are measured twice (theta_L and theta_ref): each posterior
+    is the inverse-variance combination of the prior and the two measurements, the other states
+    take the scalar update."""
+    p = np.array([0.5, 0.2, 0.1, 0.01, 0.02, 0.03, 1.0, 2.0, 0.5])
+    r = np.array([0.1, 0.1, 0.2, 0.001, 0.004, 0.002, 0.5, 0.5, 1.0])
+    r_ref = np.array([0.003, 0.006])
+    x0 = np.array([1.0, 2.0, 3.0, 0.01, -0.02, 0.5, 0.0, 0.0, 0.0])
+    f = oe.KinematicEKF(x0, np.diag(p), np.zeros(9), r, r_ref=r_ref)
+    ref = np.array([0.02, -0.03])
+    acc = Rotation.from_euler("ZYX", [0.7, ref[1], ref[0]]).as_matrix().T @ np.array([0.0, 0.0, G])
+    f.predict(0.0, acc, [0.0, 0.0, 0.0])    # a zero-length cycle: records the resting IMU sample
+    z = np.array([1.3, 1.9, 3.2, 0.015, -0.01, 0.45, 0.5, -0.2, 0.1])
+    f.update(0.0, make_pose(oe.rot_zyx(z[3:6]), z[:3]), z[6:9])
+    expect = x0 + p / (p + r) * (z - x0)
+    var = p * r / (p + r)
+    for a, j in ((3, 0), (4, 1)):
+        info = 1 / p[a] + 1 / r[a] + 1 / r_ref[j]
+        expect[a] = (x0[a] / p[a] + z[a] / r[a] + ref[j] / r_ref[j]) / info
+        var[a] = 1 / info
+    np.testing.assert_allclose(f.x, expect, atol=1e-12)
+    np.testing.assert_allclose(f.P, np.diag(var), atol=1e-14)
+
+
 # ----------------------------------------------------------------------------- library vs oracle
 def test_library_lidar_velocity_matches_oracle():
     from paper_2606_26010_gb300 import far
@@ -196,8 +237,9 @@ def test_library_lidar_velocity_matches_oracle():
                                    atol=1e-12)
 
 
-@pytest.mark.parametrize("t_start,cycles", [(0.0, 1), (10.05, 1), (10.05, 4), (0.0, 15)])
-def test_library_ekf_matches_oracle_on_the_track(t_start, cycles):
+@pytest.mark.parametrize("t_start,cycles,with_ref", [(0.0, 1, False), (10.05, 1, False), (10.05, 4, False),
+                                                    (0.0, 15, False), (10.05, 1, True), (0.0, 4, True)])
+def test_library_ekf_matches_oracle_on_the_track(t_start, cycles, with_ref):
     """Two seconds of noisy 100 Hz IMU along the track (the curve entry included for the second
     start), LiDAR updates every 0.1 s from noisy poses, each applied 30 ms after its time stamp
     (delay compensation), at once or spread over `cycles` IMU cycles (15: shares still pending
@@ -210,8 +252,9 @@ def test_library_ekf_matches_oracle_on_the_track(t_start, cycles):
     P0 = np.diag([0.01] * 3 + [1e-4] * 3 + [0.1] * 3)
     q = np.array([1e-3] * 3 + [1e-5] * 3 + [0.5] * 3)
     r = np.array([1e-4] * 3 + [1e-6] * 3 + [0.05] * 3)
-    lib = far.Ekf(x0, P0, q, r, t0=t_start, history=64)
-    ora = oe.KinematicEKF(x0, P0, q, r, t0=t_start, history=64)
+    r_ref = (2e-5, 2e-5) if with_ref else (0.0, 0.0)
+    lib = far.Ekf(x0, P0, q, r, t0=t_start, history=64, r_ref=r_ref)
+    ora = oe.KinematicEKF(x0, P0, q, r, t0=t_start, history=64, r_ref=r_ref)
     times, acc, gyro = synth.track_imu(seq, t_start, t_start + 2.0, acc_sigma=0.05, gyro_sigma=0.002, seed=7)
     pending = []
     for t, a, g in zip(times, acc, gyro):
@@ -250,3 +293,6 @@ def test_library_ekf_rejects_bad_input():
     for cycles in (0, 1001):
         with pytest.raises(far.FarError):
             e.update(1.0, np.eye(4), [0, 0, 0], cycles=cycles)
+    for r_ref in ((1e-3, 0.0), (-1e-3, -1e-3), (float("nan"), 1e-3)):
+        with pytest.raises(far.FarError):
+            far.Ekf(np.zeros(9), np.eye(9), np.zeros(9), np.ones(9), r_ref=r_ref)
